@@ -1,0 +1,238 @@
+"""Pins of the CPU oracle against facts that do not come from the oracle:
+hand-derived fixtures, closed forms, brute force from the definition,
+Theorem 1's exact work count, and certificate checks that must reject wrong
+answers. All CPU-only."""
+import numpy as np
+import pytest
+
+import graphgen as gg
+import oracle
+from tests import golden_io
+
+
+def _csr(n, s, d):
+    return oracle.build_csr(n, s, d)
+
+
+def _all_three(n, s, d):
+    off, adj = _csr(n, s, d)
+    c_bz = oracle.bz(n, off, adj)
+    c_a1, st = oracle.alg1(n, off, adj)
+    return off, adj, c_bz, c_a1, st
+
+
+# ----------------------------------------------------------------- fixtures
+@pytest.mark.parametrize("name", golden_io.names())
+def test_golden_fixture(name):
+    n, s, d, want = golden_io.load(name)
+    off, adj, c_bz, c_a1, _ = _all_three(n, s, d)
+    np.testing.assert_array_equal(c_bz, want)
+    np.testing.assert_array_equal(c_a1, want)
+    assert oracle.check(n, off, adj, want) == (0, -1)
+    assert oracle.brute_coreness(n, s, d) == want.tolist()
+
+
+# ----------------------------------------------------------------- closed forms
+CLOSED = [
+    ("K1", gg.complete(1), lambda n: [0] * n),
+    ("K2", gg.complete(2), lambda n: [1] * n),
+    ("K7", gg.complete(7), lambda n: [6] * n),
+    ("K40", gg.complete(40), lambda n: [39] * n),
+    ("path2", gg.path(2), lambda n: [1] * n),
+    ("path50", gg.path(50), lambda n: [1] * n),
+    ("star1000", gg.star(1000), lambda n: [1] * n),
+    ("cycle3", gg.cycle(3), lambda n: [2] * n),
+    ("cycle101", gg.cycle(101), lambda n: [2] * n),
+    ("K3_5", gg.complete_bipartite(3, 5), lambda n: [3] * n),
+    ("K9_4", gg.complete_bipartite(9, 4), lambda n: [4] * n),
+    ("grid2x2", gg.grid2d(2, 2), lambda n: [2] * n),
+    ("grid7x13", gg.grid2d(7, 13), lambda n: [2] * n),
+    ("grid1x9", gg.grid2d(1, 9), lambda n: [1] * n),
+    ("cube2", gg.grid3d(2, 2, 2), lambda n: [3] * n),
+    ("cube4x5x6", gg.grid3d(4, 5, 6), lambda n: [3] * n),
+    ("tree300", gg.random_tree(300, 7), lambda n: [1] * n),
+]
+
+
+@pytest.mark.parametrize("name,g,f", CLOSED, ids=[c[0] for c in CLOSED])
+def test_closed_forms(name, g, f):
+    n, s, d = g
+    off, adj, c_bz, c_a1, st = _all_three(n, s, d)
+    want = np.array(f(n), np.int32)
+    np.testing.assert_array_equal(c_bz, want)
+    np.testing.assert_array_equal(c_a1, want)
+    assert oracle.check(n, off, adj, want)[0] == 0
+
+
+def test_isolated_vertices():
+    n = 17
+    off, adj, c_bz, c_a1, st = _all_three(n, np.empty(0, np.int32), np.empty(0, np.int32))
+    assert (c_bz == 0).all() and (c_a1 == 0).all()
+    assert st["rounds"] == 1 and st["kmax"] == 0
+
+
+def test_empty_graph():
+    off, adj, c_bz, c_a1, st = _all_three(0, np.empty(0, np.int32), np.empty(0, np.int32))
+    assert len(c_bz) == 0 and len(c_a1) == 0 and st["rounds"] == 0
+
+
+@pytest.mark.parametrize("K", [2, 3, 10, 57, 200])
+def test_staircase(K):
+    n, s, d = gg.staircase(K)
+    off, adj, c_bz, c_a1, st = _all_three(n, s, d)
+    want = np.array([K] * (K + 1) + list(range(1, K)), np.int32)
+    np.testing.assert_array_equal(c_bz, want)
+    np.testing.assert_array_equal(c_a1, want)
+    assert st["kmax"] == K and st["nonempty_rounds"] == K
+
+
+def test_disjoint_union_is_per_component():
+    parts = [gg.complete(6), gg.cycle(9), gg.star(4), gg.grid3d(2, 3, 2), gg.staircase(8)]
+    n, s, d = gg.disjoint_union(*parts)
+    off, adj = _csr(n, s, d)
+    c = oracle.bz(n, off, adj)
+    base = 0
+    for pn, ps, pd in parts:
+        po, pa = _csr(pn, ps, pd)
+        np.testing.assert_array_equal(c[base:base + pn], oracle.bz(pn, po, pa))
+        base += pn
+
+
+# ----------------------------------------------------------------- brute force
+@pytest.mark.parametrize("seed", range(150))
+def test_brute_force_small_random(seed):
+    rng = np.random.default_rng(seed)
+    n = int(rng.integers(1, 28))
+    m = int(rng.integers(0, 3 * n + 1))
+    n, s, d = gg.small_random(n, m, seed)
+    off, adj, c_bz, c_a1, st = _all_three(n, s, d)
+    want = np.array(oracle.brute_coreness(n, s, d), np.int32)
+    np.testing.assert_array_equal(c_bz, want)
+    np.testing.assert_array_equal(c_a1, want)
+    assert oracle.check(n, off, adj, c_bz)[0] == 0
+
+
+@pytest.mark.parametrize("seed", range(20))
+def test_brute_force_dense_random(seed):
+    rng = np.random.default_rng(1000 + seed)
+    n = int(rng.integers(5, 22))
+    p = rng.random() * 0.8 + 0.1
+    iu, ju = np.triu_indices(n, 1)
+    keep = rng.random(len(iu)) < p
+    s, d = iu[keep].astype(np.int32), ju[keep].astype(np.int32)
+    off, adj, c_bz, c_a1, _ = _all_three(n, s, d)
+    want = np.array(oracle.brute_coreness(n, s, d), np.int32)
+    np.testing.assert_array_equal(c_bz, want)
+    np.testing.assert_array_equal(c_a1, want)
+
+
+# ----------------------------------------------------------------- Theorem 1
+@pytest.mark.parametrize("seed", range(10))
+def test_theorem1_work_count(seed):
+    """Sum over rounds of |A_k| equals sum_v (1 + coreness(v)) (Theorem 1's
+    proof), and each vertex enters exactly one frontier."""
+    n, s, d = gg.small_random(60 + 20 * seed, 300 + 90 * seed, 500 + seed)
+    off, adj, c_bz, c_a1, st = _all_three(n, s, d)
+    assert st["sum_active"] == int(np.sum(1 + c_bz.astype(np.int64)))
+    assert st["frontier_inserts"] == n
+    assert st["rounds"] == int(c_bz.max()) + 1
+    assert st["sum_active"] <= n + len(adj)
+
+
+def test_theorem1_on_er10k():
+    n, s, d = gg.workload_er10k()
+    off, adj, c_bz, c_a1, st = _all_three(n, s, d)
+    np.testing.assert_array_equal(c_bz, c_a1)
+    assert st["sum_active"] == int(np.sum(1 + c_bz.astype(np.int64)))
+    assert st["frontier_inserts"] == n
+
+
+# ----------------------------------------------------------------- certificate
+def test_check_rejects_k4_all_two():
+    """K4 with every value 2 passes (i) and (ii); only (iii) rejects it."""
+    n, s, d = gg.complete(4)
+    off, adj = _csr(n, s, d)
+    code, bad = oracle.check(n, off, adj, np.full(4, 2, np.int32))
+    assert code == 3 and bad >= 0
+
+
+@pytest.mark.parametrize("seed", range(30))
+def test_check_rejects_off_by_one(seed):
+    rng = np.random.default_rng(seed)
+    n, s, d = gg.small_random(40, 160, 900 + seed)
+    off, adj = _csr(n, s, d)
+    c = oracle.bz(n, off, adj)
+    assert oracle.check(n, off, adj, c)[0] == 0
+    for delta in (1, -1):
+        bad = c.copy()
+        v = int(rng.integers(0, n))
+        if bad[v] + delta < 0:
+            continue
+        bad[v] += delta
+        assert oracle.check(n, off, adj, bad)[0] != 0
+
+
+def test_check_rejects_shifted_vector():
+    n, s, d = gg.workload_er10k()
+    off, adj = _csr(n, s, d)
+    c = oracle.bz(n, off, adj)
+    assert oracle.check(n, off, adj, c)[0] == 0
+    assert oracle.check(n, off, adj, c + 1)[0] != 0
+    assert oracle.check(n, off, adj, np.maximum(c - 1, 0))[0] != 0
+
+
+# ----------------------------------------------------------------- CSR builder
+@pytest.mark.parametrize("seed", range(40))
+def test_build_csr_matches_set_definition(seed):
+    rng = np.random.default_rng(seed)
+    n = int(rng.integers(1, 50))
+    n, s, d = gg.small_random(n, int(rng.integers(0, 200)), seed)
+    off, adj = _csr(n, s, d)
+    nb = [set() for _ in range(n)]
+    for a, b in zip(s.tolist(), d.tolist()):
+        if a != b:
+            nb[a].add(b)
+            nb[b].add(a)
+    assert off[0] == 0 and off[-1] == len(adj)
+    for v in range(n):
+        assert adj[off[v]:off[v + 1]].tolist() == sorted(nb[v])
+    assert oracle.check_simple(n, off, adj) == 0
+
+
+def test_check_simple_rejects_bad_csr():
+    n, s, d = gg.cycle(6)
+    off, adj = _csr(n, s, d)
+    assert oracle.check_simple(n, off, adj) == 0
+    a2 = adj.copy()
+    a2[0] = 3  # 0 -> 3 has no reverse arc, and list order breaks
+    assert oracle.check_simple(n, off, a2) != 0
+    a3 = adj.copy()
+    a3[off[2]] = 2  # self-loop
+    assert oracle.check_simple(n, off, a3) != 0
+
+
+def test_build_csr_rejects_out_of_range():
+    with pytest.raises(ValueError):
+        oracle.build_csr(3, np.array([0, 5], np.int32), np.array([1, 1], np.int32))
+
+
+# ----------------------------------------------------------------- batch helper
+def test_bz_batch_matches_union():
+    spec = gg.batch_spec(6, nmin=50, nmax=400, seed=11)
+    eoff, s, d = gg.batch_edges(spec)
+    gv = np.zeros(len(spec) + 1, np.int64)
+    np.cumsum(spec[:, 0], out=gv[1:])
+    # union CSR with global ids
+    gs = np.concatenate([s[eoff[g]:eoff[g + 1]].astype(np.int64) + gv[g] for g in range(len(spec))])
+    gd = np.concatenate([d[eoff[g]:eoff[g + 1]].astype(np.int64) + gv[g] for g in range(len(spec))])
+    N = int(gv[-1])
+    off, adj = oracle.build_csr(N, gs.astype(np.int32), gd.astype(np.int32))
+    want = oracle.bz(N, off, adj)
+    # segmented CSR: same offsets, graph-local ids
+    gid = np.repeat(np.arange(len(spec)), np.diff(gv))
+    src_of_arc = np.repeat(np.arange(N), np.diff(off))
+    local = adj - gv[gid[src_of_arc]]
+    core, km = oracle.bz_batch(gv, off, local.astype(np.int32))
+    np.testing.assert_array_equal(core, want)
+    for g in range(len(spec)):
+        assert km[g] == want[gv[g]:gv[g + 1]].max()
