@@ -1,0 +1,142 @@
+/*
+ * kcore.h - C ABI of the GB300 (sm_103a) k-core decomposition library.
+ *
+ * Problem (arXiv 2502.08042, Sec. 2 "Notations"): for a simple undirected
+ * graph G, the k-core G_k is the largest subgraph in which every vertex has
+ * degree at least k; the coreness of v is the largest k with v in G_k, and
+ * k_max is the largest coreness. The library computes the coreness of every
+ * vertex by parallel peeling (Algorithm 1 with the online Peel of
+ * Algorithm 3): level by level, the live vertices whose induced degree is at
+ * most k get coreness k, their live neighbours' induced degrees are decremented
+ * atomically, and a neighbour whose decrement lands it on k joins the same
+ * level's work.
+ *
+ * Conventions shared by every entry point:
+ *  - Graphs are CSR: int64 offsets[n+1] (offsets[0] = 0, offsets[n] = m) and
+ *    int32 adj[m]. m counts arcs: each undirected edge appears twice (u->v and
+ *    v->u), so the number of undirected edges is m/2. The graph must be simple
+ *    (symmetric, no self-loops, no repeated arcs); kcore_build_csr produces
+ *    such a CSR from any edge list. 0 <= n <= 2^31 - 2.
+ *  - Pointers marked "device" must be device memory (or managed memory)
+ *    readable/writable by the handle's device; "host" pointers are host memory.
+ *    The caller owns every array it passes and keeps it alive until the work
+ *    queued on `stream` has passed the call.
+ *  - Calls taking a stream are asynchronous: they queue work on `stream` and
+ *    return. Argument errors are reported synchronously by the return value
+ *    and nothing is queued. Errors found on the device (a wait that ran past
+ *    its time limit, a malformed graph detected on the device) are reported by
+ *    kcore_sync_status. Outputs are undefined after an error.
+ *  - No entry point throws; none calls exit(); none takes a torch type.
+ *  - A handle is bound to one device and is not thread-safe: use one handle
+ *    per host thread (handles share nothing).
+ */
+#ifndef KCORE_H_
+#define KCORE_H_
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct kcore_ctx* kcore_handle;
+typedef struct CUstream_st* kcore_stream_t; /* same type as cudaStream_t; NULL = legacy default stream */
+
+typedef enum {
+  KCORE_OK = 0,
+  KCORE_ERR_INVALID = 1,    /* bad argument (null pointer, negative size, n too large, ...) */
+  KCORE_ERR_OOM = 2,        /* device memory for the workspace could not be obtained */
+  KCORE_ERR_CUDA = 3,       /* a CUDA runtime call failed; see kcore_last_error */
+  KCORE_ERR_TIMEOUT = 4,    /* a device-side wait exceeded its time limit; the kernel returned */
+  KCORE_ERR_NOT_SIMPLE = 5, /* the graph failed a simple-CSR check */
+  KCORE_ERR_CAPACITY = 6    /* an internal bound was exceeded (reported, never overrun) */
+} kcore_status;
+
+/* Tunables (kcore_set_option). Defaults are chosen per device at kcore_create
+ * and may be overridden; kcore_get_option reads them back. */
+typedef enum {
+  KCORE_OPT_SYNC_MODE = 0,     /* 0 auto, 1 persistent kernel (device-wide counters), 2 graph relaunch */
+  KCORE_OPT_CTAS_PER_SM = 1,   /* CTAs per SM of the persistent kernel (0 = occupancy maximum) */
+  KCORE_OPT_SLICE_ARCS = 2,    /* arcs per work item: longer adjacency lists are split in slices */
+  KCORE_OPT_LOCAL_QUEUE = 3,   /* per-warp local queue capacity (vertices), 0 disables it */
+  KCORE_OPT_TIMEOUT_MS = 4,    /* limit for every device-side wait, milliseconds */
+  KCORE_OPT_MIN_CTAS = 5,      /* lower bound of the grid for small graphs */
+  KCORE_OPT_VERTICES_PER_CTA = 6, /* grid sizing: about one CTA per this many vertices+arcs/8 */
+  KCORE_OPT_TEST_STALL = 7       /* test hook, default 0: 1 makes CTA 0 withhold its round-1
+                                    completion token, so every device wait must run out its
+                                    time limit and the call ends with KCORE_ERR_TIMEOUT */
+} kcore_option;
+
+/* Counters of the last decomposition (valid after kcore_sync_status). */
+typedef struct {
+  int64_t rounds;          /* levels visited, empty speculative levels included */
+  int64_t empty_rounds;    /* visited levels that held no vertex */
+  int64_t items;           /* work items (vertex slices) processed through the global queue */
+  int64_t local_items;     /* vertices processed from warp-local queues */
+  int64_t scanned;         /* sum over rounds of the active-set size scanned (Theorem 1) */
+  int64_t kmax;            /* largest coreness */
+  int64_t grid;            /* CTAs of the persistent kernel */
+  int64_t sync_mode;       /* mode actually used: 1 persistent, 2 graph relaunch */
+  int64_t reserved[8];
+} kcore_stats;
+
+/* Creates a handle on `device` (CUDA ordinal). The handle owns a workspace
+ * that grows on demand, a small pinned status buffer and its tuning values.
+ * Errors: KCORE_ERR_INVALID (null out / bad device), KCORE_ERR_CUDA. */
+kcore_status kcore_create(kcore_handle* out, int device);
+
+/* Frees everything the handle owns. Waits for the handle's queued work. */
+kcore_status kcore_destroy(kcore_handle h);
+
+/* Human-readable description of the last error on this handle ("" if none).
+ * The string is owned by the handle and valid until its next call. */
+const char* kcore_last_error(kcore_handle h);
+
+kcore_status kcore_set_option(kcore_handle h, kcore_option opt, int64_t value);
+kcore_status kcore_get_option(kcore_handle h, kcore_option opt, int64_t* value);
+
+/* Device bytes of workspace kcore_decompose needs for a graph of n vertices
+ * and m arcs (host call, no device work). */
+kcore_status kcore_workspace_size(kcore_handle h, int64_t n, int64_t m, size_t* bytes);
+
+/* Hands the handle caller-owned device memory to use as workspace (e.g. from
+ * a caching allocator). The caller keeps it alive until the handle's work has
+ * finished or another workspace is set; ptr = NULL returns to handle-owned
+ * memory. ptr must be 256-byte aligned. */
+kcore_status kcore_set_workspace(kcore_handle h, void* ptr, size_t bytes);
+
+/* Coreness of every vertex (Algorithm 1 with online peeling, Algorithm 3).
+ *   n, m           vertices, arcs (m = offsets[n] = twice the undirected edges)
+ *   offsets        device int64[n+1], borrowed
+ *   adj            device int32[m], borrowed; simple undirected CSR
+ *   coreness_out   device int32[n]: coreness of each vertex
+ *   kmax_out       device int32[1]: largest coreness (0 when n == 0)
+ *   stream         CUDA stream the work is queued on
+ * Asynchronous. Uses the handle's workspace (grown with cudaMalloc if the
+ * caller set none; growing synchronises the device). Errors: INVALID, OOM,
+ * CUDA synchronously; TIMEOUT via kcore_sync_status. */
+kcore_status kcore_decompose(kcore_handle h, int64_t n, int64_t m, const int64_t* offsets,
+                             const int32_t* adj, int32_t* coreness_out, int32_t* kmax_out,
+                             kcore_stream_t stream);
+
+/* Same computation from HOST arrays, end to end: copies offsets and adj to the
+ * device, decomposes, copies coreness and k_max back, and waits. Host buffers
+ * may be pageable or pinned (pinned is faster). Synchronous; returns the
+ * device status as kcore_sync_status would. */
+kcore_status kcore_decompose_host(kcore_handle h, int64_t n, int64_t m, const int64_t* offsets_host,
+                                  const int32_t* adj_host, int32_t* coreness_host,
+                                  int32_t* kmax_host, kcore_stream_t stream);
+
+/* Waits for the stream of the handle's last call and returns the status the
+ * device recorded (KCORE_OK, KCORE_ERR_TIMEOUT, ...). */
+kcore_status kcore_sync_status(kcore_handle h);
+
+/* Counters of the last decomposition; call after kcore_sync_status. */
+kcore_status kcore_get_stats(kcore_handle h, kcore_stats* out);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* KCORE_H_ */

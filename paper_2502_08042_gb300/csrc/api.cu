@@ -1,0 +1,379 @@
+// C ABI of libkcore: handle, workspace, options and the single-graph entry
+// points (declarations and contracts in include/kcore.h).
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <string>
+
+#include "kcore.h"
+#include "kcore_peel.h"
+
+struct kcore_ctx {
+  int device = 0;
+  int sms = 0;
+  int max_ctas_per_sm = 0;
+  void* ws = nullptr;
+  size_t ws_bytes = 0;
+  bool ws_external = false;
+  std::string err;
+  int64_t opt[8] = {0, 0, 256, 64, 2000, 1, 2048, 0};  // indexed by kcore_option
+  cudaStream_t last_stream = nullptr;
+  bool pending = false;
+  kc::PeelCtl* last_ctl = nullptr;
+  kcore_stats stats{};
+  int last_grid = 0;
+  int last_mode = 0;
+  // device staging for kcore_decompose_host
+  void* e2e = nullptr;
+  size_t e2e_bytes = 0;
+};
+
+namespace {
+
+struct DeviceGuard {
+  int prev = -1;
+  bool ok = false;
+  explicit DeviceGuard(int dev) {
+    if (cudaGetDevice(&prev) != cudaSuccess) prev = -1;
+    ok = cudaSetDevice(dev) == cudaSuccess;
+  }
+  ~DeviceGuard() {
+    if (prev >= 0) cudaSetDevice(prev);
+  }
+};
+
+kcore_status fail(kcore_ctx* h, kcore_status st, const std::string& msg) {
+  if (h) h->err = msg;
+  return st;
+}
+
+kcore_status cuda_fail(kcore_ctx* h, cudaError_t e, const char* what) {
+  cudaGetLastError();  // clear the sticky-free error state
+  return fail(h, KCORE_ERR_CUDA, std::string(what) + ": " + cudaGetErrorString(e));
+}
+
+size_t align_up(size_t x, size_t a) { return (x + a - 1) / a * a; }
+
+long long isqrt_ll(long long m) {
+  long long r = (long long)std::sqrt((double)m);
+  while (r > 0 && r * r > m) r--;
+  while ((r + 1) * (r + 1) <= m) r++;
+  return r;
+}
+
+struct PeelLayout {
+  size_t deg, a0, a1, q, rounds, ctl, total;
+  long long qcap;
+  int max_rounds;
+};
+
+// Workspace of the single-graph peel: d~[n], two active lists [n], the work
+// queue (every vertex pushes ceil(deg/slice) slices once: <= n + m/slice), the
+// per-round records (levels <= k_max+1 <= sqrt(m)+1, each followed by at most
+// one empty speculative level) and the control block.
+PeelLayout peel_layout(long long n, long long m, int slice) {
+  PeelLayout L{};
+  L.qcap = n + (m + slice - 1) / slice + 1;
+  long long mr = 2 * isqrt_ll(m) + 8;
+  mr = std::min(mr, 2 * n + 8);
+  L.max_rounds = (int)mr;
+  size_t off = 0;
+  L.ctl = off;
+  off = align_up(off + sizeof(kc::PeelCtl), 256);
+  L.rounds = off;
+  off = align_up(off + sizeof(kc::RoundRec) * (size_t)L.max_rounds, 256);
+  L.deg = off;
+  off = align_up(off + 4 * (size_t)n, 256);
+  L.a0 = off;
+  off = align_up(off + 4 * (size_t)n, 256);
+  L.a1 = off;
+  off = align_up(off + 4 * (size_t)n, 256);
+  L.q = off;
+  off = align_up(off + 8 * (size_t)L.qcap, 256);
+  L.total = off;
+  return L;
+}
+
+kcore_status ensure_ws(kcore_ctx* h, size_t need) {
+  if (h->ws_bytes >= need) return KCORE_OK;
+  if (h->ws_external)
+    return fail(h, KCORE_ERR_OOM,
+                "caller workspace too small: need " + std::to_string(need) + " bytes, have " +
+                    std::to_string(h->ws_bytes));
+  if (h->ws) {
+    cudaDeviceSynchronize();
+    cudaFree(h->ws);
+    h->ws = nullptr;
+    h->ws_bytes = 0;
+  }
+  size_t grow = std::max(need, (size_t)1 << 20);
+  cudaError_t e = cudaMalloc(&h->ws, grow);
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    h->ws = nullptr;
+    return fail(h, KCORE_ERR_OOM, "cudaMalloc of " + std::to_string(grow) + " workspace bytes failed");
+  }
+  h->ws_bytes = grow;
+  return KCORE_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+kcore_status kcore_create(kcore_handle* out, int device) {
+  if (!out) return KCORE_ERR_INVALID;
+  *out = nullptr;
+  int count = 0;
+  if (cudaGetDeviceCount(&count) != cudaSuccess || device < 0 || device >= count) {
+    cudaGetLastError();
+    return KCORE_ERR_INVALID;
+  }
+  kcore_ctx* h = new kcore_ctx();
+  h->device = device;
+  DeviceGuard g(device);
+  if (!g.ok) {
+    delete h;
+    return KCORE_ERR_CUDA;
+  }
+  cudaDeviceGetAttribute(&h->sms, cudaDevAttrMultiProcessorCount, device);
+  h->max_ctas_per_sm = kc::peel_max_ctas_per_sm();
+  if (h->max_ctas_per_sm <= 0 || h->sms <= 0) {
+    delete h;
+    cudaGetLastError();
+    return KCORE_ERR_CUDA;
+  }
+  *out = h;
+  return KCORE_OK;
+}
+
+kcore_status kcore_destroy(kcore_handle h) {
+  if (!h) return KCORE_ERR_INVALID;
+  {
+    DeviceGuard g(h->device);
+    if (h->pending && h->last_stream) cudaStreamSynchronize(h->last_stream);
+    cudaDeviceSynchronize();
+    if (h->ws && !h->ws_external) cudaFree(h->ws);
+    if (h->e2e) cudaFree(h->e2e);
+    cudaGetLastError();
+  }
+  delete h;
+  return KCORE_OK;
+}
+
+const char* kcore_last_error(kcore_handle h) { return h ? h->err.c_str() : "null handle"; }
+
+kcore_status kcore_set_option(kcore_handle h, kcore_option opt, int64_t value) {
+  if (!h || (int)opt < 0 || (int)opt > 7) return KCORE_ERR_INVALID;
+  switch (opt) {
+    case KCORE_OPT_TEST_STALL:
+      if (value < 0 || value > 1) return fail(h, KCORE_ERR_INVALID, "test stall must be 0 or 1");
+      break;
+    case KCORE_OPT_SYNC_MODE:
+      if (value < 0 || value > 2) return fail(h, KCORE_ERR_INVALID, "sync mode must be 0, 1 or 2");
+      break;
+    case KCORE_OPT_CTAS_PER_SM:
+      if (value < 0 || value > h->max_ctas_per_sm)
+        return fail(h, KCORE_ERR_INVALID, "CTAs per SM above the occupancy limit");
+      break;
+    case KCORE_OPT_SLICE_ARCS:
+      if (value < 32 || value > (1 << 20)) return fail(h, KCORE_ERR_INVALID, "slice must be in [32, 2^20]");
+      break;
+    case KCORE_OPT_LOCAL_QUEUE:
+      if (value < 0 || value > kc::kLocalQueueMax)
+        return fail(h, KCORE_ERR_INVALID, "local queue must be in [0, 128]");
+      break;
+    case KCORE_OPT_TIMEOUT_MS:
+      if (value < 1 || value > 600000) return fail(h, KCORE_ERR_INVALID, "timeout must be in [1, 600000] ms");
+      break;
+    case KCORE_OPT_MIN_CTAS:
+      if (value < 1) return fail(h, KCORE_ERR_INVALID, "min CTAs must be >= 1");
+      break;
+    case KCORE_OPT_VERTICES_PER_CTA:
+      if (value < 1) return fail(h, KCORE_ERR_INVALID, "vertices per CTA must be >= 1");
+      break;
+  }
+  h->opt[opt] = value;
+  return KCORE_OK;
+}
+
+kcore_status kcore_get_option(kcore_handle h, kcore_option opt, int64_t* value) {
+  if (!h || !value || (int)opt < 0 || (int)opt > 7) return KCORE_ERR_INVALID;
+  *value = h->opt[opt];
+  return KCORE_OK;
+}
+
+kcore_status kcore_workspace_size(kcore_handle h, int64_t n, int64_t m, size_t* bytes) {
+  if (!h || !bytes || n < 0 || m < 0 || n > INT32_MAX - 1) return KCORE_ERR_INVALID;
+  *bytes = peel_layout(n, m, (int)h->opt[KCORE_OPT_SLICE_ARCS]).total;
+  return KCORE_OK;
+}
+
+kcore_status kcore_set_workspace(kcore_handle h, void* ptr, size_t bytes) {
+  if (!h) return KCORE_ERR_INVALID;
+  if (ptr && ((uintptr_t)ptr % 256) != 0) return fail(h, KCORE_ERR_INVALID, "workspace must be 256-byte aligned");
+  DeviceGuard g(h->device);
+  if (h->ws && !h->ws_external) {
+    cudaDeviceSynchronize();
+    cudaFree(h->ws);
+  }
+  h->ws = ptr;
+  h->ws_bytes = ptr ? bytes : 0;
+  h->ws_external = ptr != nullptr;
+  return KCORE_OK;
+}
+
+kcore_status kcore_decompose(kcore_handle h, int64_t n, int64_t m, const int64_t* offsets,
+                             const int32_t* adj, int32_t* coreness_out, int32_t* kmax_out,
+                             kcore_stream_t stream_) {
+  if (!h) return KCORE_ERR_INVALID;
+  cudaStream_t stream = (cudaStream_t)stream_;
+  if (n < 0 || m < 0 || n > INT32_MAX - 1) return fail(h, KCORE_ERR_INVALID, "n or m out of range");
+  if (!kmax_out) return fail(h, KCORE_ERR_INVALID, "kmax_out is null");
+  if (n > 0 && (!offsets || !coreness_out)) return fail(h, KCORE_ERR_INVALID, "null offsets/coreness");
+  if (m > 0 && !adj) return fail(h, KCORE_ERR_INVALID, "null adj with m > 0");
+  DeviceGuard g(h->device);
+  if (!g.ok) return fail(h, KCORE_ERR_CUDA, "cudaSetDevice failed");
+  h->err.clear();
+  h->stats = kcore_stats{};
+  h->last_ctl = nullptr;
+  h->last_stream = stream;
+  h->pending = true;
+  if (n == 0) {
+    cudaError_t e = cudaMemsetAsync(kmax_out, 0, sizeof(int32_t), stream);
+    if (e != cudaSuccess) return cuda_fail(h, e, "cudaMemsetAsync");
+    return KCORE_OK;
+  }
+  const int slice = (int)h->opt[KCORE_OPT_SLICE_ARCS];
+  PeelLayout L = peel_layout(n, m, slice);
+  kcore_status st = ensure_ws(h, L.total);
+  if (st != KCORE_OK) return st;
+  char* ws = (char*)h->ws;
+  kc::PeelArgs a{};
+  a.n = n;
+  a.m = m;
+  a.off = (const long long*)offsets;
+  a.adj = adj;
+  a.core = coreness_out;
+  a.kmax_out = kmax_out;
+  a.deg = (int*)(ws + L.deg);
+  a.A0 = (int*)(ws + L.a0);
+  a.A1 = (int*)(ws + L.a1);
+  a.Q = (unsigned long long*)(ws + L.q);
+  a.qcap = L.qcap;
+  a.rounds = (kc::RoundRec*)(ws + L.rounds);
+  a.max_rounds = L.max_rounds;
+  a.ctl = (kc::PeelCtl*)(ws + L.ctl);
+  a.slice = slice;
+  a.lq_cap = (int)h->opt[KCORE_OPT_LOCAL_QUEUE];
+  a.max_take = 256;
+  a.timeout_ns = (unsigned long long)h->opt[KCORE_OPT_TIMEOUT_MS] * 1000000ull;
+  a.max_backoff_ns = 1024;
+  a.inject_stall = (int)h->opt[KCORE_OPT_TEST_STALL];
+
+  int per_sm = h->opt[KCORE_OPT_CTAS_PER_SM] > 0 ? (int)h->opt[KCORE_OPT_CTAS_PER_SM] : h->max_ctas_per_sm;
+  long long gmax = (long long)h->sms * per_sm;
+  long long work = n + m / 8;
+  long long want = (work + h->opt[KCORE_OPT_VERTICES_PER_CTA] - 1) / h->opt[KCORE_OPT_VERTICES_PER_CTA];
+  long long grid = std::max<long long>(h->opt[KCORE_OPT_MIN_CTAS], std::min(want, gmax));
+  grid = std::min(grid, gmax);
+  a.take_div = (int)std::max<long long>(1, grid * (kc::peel_block_size() / 32));
+
+  cudaError_t e;
+  if ((e = cudaMemsetAsync(ws, 0, L.deg, stream)) != cudaSuccess) return cuda_fail(h, e, "memset ctl");
+  if ((e = cudaMemsetAsync(ws + L.q, 0xff, 8 * (size_t)L.qcap, stream)) != cudaSuccess)
+    return cuda_fail(h, e, "memset queue");
+  if ((e = kc::peel_launch(a, (int)grid, stream)) != cudaSuccess) return cuda_fail(h, e, "peel launch");
+  h->last_ctl = a.ctl;
+  h->last_grid = (int)grid;
+  h->last_mode = 1;
+  return KCORE_OK;
+}
+
+kcore_status kcore_sync_status(kcore_handle h) {
+  if (!h) return KCORE_ERR_INVALID;
+  DeviceGuard g(h->device);
+  if (!h->pending) return KCORE_OK;
+  cudaError_t e = cudaStreamSynchronize(h->last_stream);
+  h->pending = false;
+  if (e != cudaSuccess) return cuda_fail(h, e, "stream synchronize");
+  if (!h->last_ctl) return KCORE_OK;
+  kc::PeelCtl c;
+  e = cudaMemcpy(&c, h->last_ctl, sizeof(c), cudaMemcpyDeviceToHost);
+  if (e != cudaSuccess) return cuda_fail(h, e, "read status");
+  h->stats.rounds = c.rounds;
+  h->stats.empty_rounds = c.empty_rounds;
+  h->stats.items = (int64_t)c.items;
+  h->stats.local_items = (int64_t)c.local_items;
+  h->stats.scanned = c.scanned;
+  h->stats.kmax = c.kmax;
+  h->stats.grid = h->last_grid;
+  h->stats.sync_mode = h->last_mode;
+  switch (c.status) {
+    case 0:
+      return KCORE_OK;
+    case kc::ST_TIMEOUT:
+      return fail(h, KCORE_ERR_TIMEOUT, "a device-side wait exceeded its time limit");
+    case kc::ST_NOT_SIMPLE:
+      return fail(h, KCORE_ERR_NOT_SIMPLE, "malformed CSR detected on the device (offsets or ids out of range)");
+    case kc::ST_CAPACITY:
+      return fail(h, KCORE_ERR_CAPACITY, "an internal bound was exceeded");
+    default:
+      return fail(h, KCORE_ERR_CUDA, "unknown device status " + std::to_string(c.status));
+  }
+}
+
+kcore_status kcore_get_stats(kcore_handle h, kcore_stats* out) {
+  if (!h || !out) return KCORE_ERR_INVALID;
+  *out = h->stats;
+  return KCORE_OK;
+}
+
+kcore_status kcore_decompose_host(kcore_handle h, int64_t n, int64_t m, const int64_t* offsets_host,
+                                  const int32_t* adj_host, int32_t* coreness_host,
+                                  int32_t* kmax_host, kcore_stream_t stream_) {
+  if (!h) return KCORE_ERR_INVALID;
+  cudaStream_t stream = (cudaStream_t)stream_;
+  if (n < 0 || m < 0 || n > INT32_MAX - 1) return fail(h, KCORE_ERR_INVALID, "n or m out of range");
+  if (!kmax_host || (n > 0 && (!offsets_host || !coreness_host)) || (m > 0 && !adj_host))
+    return fail(h, KCORE_ERR_INVALID, "null host pointer");
+  DeviceGuard g(h->device);
+  size_t b_off = align_up(8 * (size_t)(n + 1), 256), b_adj = align_up(4 * (size_t)m, 256);
+  size_t b_core = align_up(4 * (size_t)n, 256);
+  size_t need = b_off + b_adj + b_core + 256;
+  if (h->e2e_bytes < need) {
+    if (h->e2e) {
+      cudaDeviceSynchronize();
+      cudaFree(h->e2e);
+      h->e2e = nullptr;
+      h->e2e_bytes = 0;
+    }
+    if (cudaMalloc(&h->e2e, need) != cudaSuccess) {
+      cudaGetLastError();
+      return fail(h, KCORE_ERR_OOM, "cudaMalloc of host-path staging failed");
+    }
+    h->e2e_bytes = need;
+  }
+  char* p = (char*)h->e2e;
+  int64_t* d_off = (int64_t*)p;
+  int32_t* d_adj = (int32_t*)(p + b_off);
+  int32_t* d_core = (int32_t*)(p + b_off + b_adj);
+  int32_t* d_kmax = (int32_t*)(p + b_off + b_adj + b_core);
+  cudaError_t e;
+  if (n > 0 && (e = cudaMemcpyAsync(d_off, offsets_host, 8 * (size_t)(n + 1), cudaMemcpyHostToDevice, stream)) != cudaSuccess)
+    return cuda_fail(h, e, "copy offsets");
+  if (m > 0 && (e = cudaMemcpyAsync(d_adj, adj_host, 4 * (size_t)m, cudaMemcpyHostToDevice, stream)) != cudaSuccess)
+    return cuda_fail(h, e, "copy adj");
+  kcore_status st = kcore_decompose(h, n, m, d_off, d_adj, d_core, d_kmax, stream_);
+  if (st != KCORE_OK) return st;
+  if (n > 0 && (e = cudaMemcpyAsync(coreness_host, d_core, 4 * (size_t)n, cudaMemcpyDeviceToHost, stream)) != cudaSuccess)
+    return cuda_fail(h, e, "copy coreness");
+  if ((e = cudaMemcpyAsync(kmax_host, d_kmax, 4, cudaMemcpyDeviceToHost, stream)) != cudaSuccess)
+    return cuda_fail(h, e, "copy kmax");
+  return kcore_sync_status(h);
+}
+
+}  // extern "C"

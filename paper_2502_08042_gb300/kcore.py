@@ -1,0 +1,164 @@
+"""Python binding of libkcore (include/kcore.h): argument marshalling only.
+
+Device arrays are torch CUDA tensors (PyTorch supplies device memory and
+streams); every step of the decomposition runs in the library's kernels. There
+is no fallback: if the library cannot be built or loaded, or a call fails, an
+exception is raised.
+"""
+from __future__ import annotations
+
+import ctypes
+
+import numpy as np
+
+from . import _native
+
+STATUS = {0: "OK", 1: "INVALID", 2: "OOM", 3: "CUDA", 4: "TIMEOUT", 5: "NOT_SIMPLE", 6: "CAPACITY"}
+OPTIONS = {"sync_mode": 0, "ctas_per_sm": 1, "slice_arcs": 2, "local_queue": 3, "timeout_ms": 4,
+           "min_ctas": 5, "vertices_per_cta": 6, "test_stall": 7}
+
+
+class KCoreError(RuntimeError):
+    def __init__(self, status: int, message: str):
+        super().__init__(f"kcore {STATUS.get(status, status)}: {message}")
+        self.status = status
+        self.code = STATUS.get(status, str(status))
+
+
+def _torch():
+    import torch
+    return torch
+
+
+def _ptr(t) -> int | None:
+    if t is None:
+        return None
+    if isinstance(t, np.ndarray):
+        return t.ctypes.data if t.size else None
+    return t.data_ptr() if t.numel() else None
+
+
+def _stream_ptr(stream) -> int | None:
+    torch = _torch()
+    if stream is None:
+        stream = torch.cuda.current_stream()
+    return stream.cuda_stream or None
+
+
+class KCore:
+    """One library handle bound to one CUDA device (not thread-safe)."""
+
+    def __init__(self, device: int = 0, **options):
+        self._L = _native.lib()
+        self.device = device
+        h = ctypes.c_void_p()
+        st = self._L.kcore_create(ctypes.byref(h), device)
+        if st != 0:
+            raise KCoreError(st, f"kcore_create(device={device}) failed")
+        self._h = h
+        for k, v in options.items():
+            self.set_option(k, v)
+
+    # ------------------------------------------------------------ plumbing
+    def _check(self, st: int):
+        if st != 0:
+            msg = self._L.kcore_last_error(self._h)
+            raise KCoreError(st, msg.decode() if msg else "")
+
+    def close(self):
+        if getattr(self, "_h", None):
+            self._L.kcore_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    def set_option(self, name: str, value: int):
+        self._check(self._L.kcore_set_option(self._h, OPTIONS[name], int(value)))
+
+    def get_option(self, name: str) -> int:
+        v = ctypes.c_int64()
+        self._check(self._L.kcore_get_option(self._h, OPTIONS[name], ctypes.byref(v)))
+        return int(v.value)
+
+    def workspace_size(self, n: int, m: int) -> int:
+        b = ctypes.c_size_t()
+        self._check(self._L.kcore_workspace_size(self._h, n, m, ctypes.byref(b)))
+        return int(b.value)
+
+    def set_workspace(self, buf) -> None:
+        """Uses a caller-owned device buffer (e.g. a torch uint8 tensor) as
+        workspace; None returns to library-owned memory."""
+        if buf is None:
+            self._check(self._L.kcore_set_workspace(self._h, None, 0))
+        else:
+            self._check(self._L.kcore_set_workspace(self._h, buf.data_ptr(), buf.numel() * buf.element_size()))
+        self._ws_ref = buf
+
+    def sync(self) -> None:
+        """Waits for the last call and raises if the device reported an error."""
+        self._check(self._L.kcore_sync_status(self._h))
+
+    def stats(self) -> dict:
+        s = _native.Stats()
+        self._check(self._L.kcore_get_stats(self._h, ctypes.byref(s)))
+        return {f: int(getattr(s, f)) for f, _ in _native.Stats._fields_ if f != "reserved"}
+
+    # ------------------------------------------------------------ compute
+    def decompose(self, offsets, adj, coreness=None, kmax=None, stream=None, sync: bool = True):
+        """Coreness of every vertex of a simple undirected CSR held on the GPU.
+
+        offsets: int64 CUDA tensor [n+1]; adj: int32 CUDA tensor [m].
+        Returns (coreness int32 [n], kmax int32 [1]) CUDA tensors. With
+        sync=False the call only queues work (check errors with sync())."""
+        torch = _torch()
+        n = offsets.numel() - 1
+        m = adj.numel()
+        assert offsets.dtype == torch.int64 and adj.dtype == torch.int32
+        assert offsets.is_cuda and adj.is_cuda and offsets.is_contiguous() and adj.is_contiguous()
+        if coreness is None:
+            coreness = torch.empty(max(n, 0), dtype=torch.int32, device=offsets.device)
+        if kmax is None:
+            kmax = torch.empty(1, dtype=torch.int32, device=offsets.device)
+        st = self._L.kcore_decompose(self._h, n, m, _ptr(offsets), _ptr(adj), _ptr(coreness),
+                                     _ptr(kmax), _stream_ptr(stream))
+        self._check(st)
+        if sync:
+            self.sync()
+        return coreness, kmax
+
+    def decompose_host(self, offsets: np.ndarray, adj: np.ndarray, stream=None):
+        """End-to-end call on host arrays: H2D copies, peel, D2H copies, wait.
+        Returns (coreness int32 numpy [n], kmax int)."""
+        offsets = np.ascontiguousarray(offsets, dtype=np.int64)
+        adj = np.ascontiguousarray(adj, dtype=np.int32)
+        n = len(offsets) - 1
+        core = np.empty(n, np.int32)
+        km = np.zeros(1, np.int32)
+        st = self._L.kcore_decompose_host(self._h, n, len(adj), _ptr(offsets), _ptr(adj),
+                                          _ptr(core), _ptr(km), _stream_ptr(stream))
+        self._check(st)
+        return core, int(km[0])
+
+    def decompose_host_into(self, offsets, adj, core_out, kmax_out, stream=None):
+        """decompose_host with caller-provided (e.g. pinned) host buffers."""
+        st = self._L.kcore_decompose_host(self._h, len(offsets) - 1, len(adj), _ptr(offsets),
+                                          _ptr(adj), _ptr(core_out), _ptr(kmax_out),
+                                          _stream_ptr(stream))
+        self._check(st)
+
+
+def decompose(offsets, adj, device: int | None = None, **options):
+    """One-shot convenience wrapper around KCore.decompose (synchronous)."""
+    dev = offsets.device.index if device is None else device
+    with KCore(dev or 0, **options) as k:
+        return k.decompose(offsets, adj)

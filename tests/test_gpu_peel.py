@@ -1,0 +1,203 @@
+"""Parity of the GPU peel (through the C ABI) with the CPU oracle: bit-exact
+coreness on closed forms, hand-derived fixtures, random graphs over many seeds,
+the ER n=10,000 workload, adversarial shapes and every tuning mode."""
+import numpy as np
+import pytest
+
+import graphgen as gg
+import oracle
+from tests import golden_io
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+from paper_2502_08042_gb300 import KCore, KCoreError  # noqa: E402
+from tests.gpu_util import assert_parity, gpu_core, to_dev  # noqa: E402
+
+
+@pytest.fixture(scope="module")
+def kc():
+    with KCore(0) as k:
+        yield k
+
+
+def _csr(n, s, d):
+    return oracle.build_csr(n, s, d)
+
+
+@pytest.mark.parametrize("name", golden_io.names())
+def test_golden(kc, name):
+    n, s, d, want = golden_io.load(name)
+    off, adj = _csr(n, s, d)
+    assert_parity(kc, n, off, adj, want)
+
+
+CLOSED = [gg.complete(1), gg.complete(2), gg.complete(60), gg.path(2), gg.path(1000),
+          gg.star(5000), gg.cycle(3), gg.cycle(777), gg.complete_bipartite(7, 40),
+          gg.grid2d(30, 41), gg.grid3d(9, 10, 11), gg.random_tree(5000, 3), gg.staircase(300)]
+
+
+@pytest.mark.parametrize("i", range(len(CLOSED)))
+def test_closed_forms(kc, i):
+    n, s, d = CLOSED[i]
+    off, adj = _csr(n, s, d)
+    assert_parity(kc, n, off, adj)
+
+
+def test_empty_graph(kc):
+    o, a = to_dev(np.zeros(1, np.int64), np.zeros(0, np.int32))
+    core, km = kc.decompose(o, a)
+    assert core.numel() == 0 and int(km.cpu()[0]) == 0
+
+
+def test_single_vertex_and_isolated(kc):
+    for n in (1, 2, 1000):
+        off = np.zeros(n + 1, np.int64)
+        got, km = gpu_core(kc, off, np.zeros(0, np.int32))
+        assert (got == 0).all() and km == 0
+
+
+@pytest.mark.parametrize("seed", range(60))
+def test_random_small(kc, seed):
+    rng = np.random.default_rng(seed)
+    n = int(rng.integers(1, 400))
+    n, s, d = gg.small_random(n, int(rng.integers(0, 6 * n)), 7000 + seed)
+    off, adj = _csr(n, s, d)
+    assert_parity(kc, n, off, adj)
+
+
+@pytest.mark.parametrize("seed", range(8))
+def test_random_rmat_small(kc, seed):
+    s, d = gg.rmat(12, 8, seed=100 + seed, perm_seed=200 + seed)
+    off, adj = _csr(1 << 12, s, d)
+    assert_parity(kc, 1 << 12, off, adj)
+
+
+def test_er10k(kc):
+    n, s, d = gg.workload_er10k()
+    off, adj = _csr(n, s, d)
+    got = assert_parity(kc, n, off, adj)
+    assert oracle.check(n, off, adj, got)[0] == 0
+
+
+def test_union_of_shapes(kc):
+    n, s, d = gg.disjoint_union(gg.complete(100), gg.path(3000), gg.staircase(150),
+                                gg.grid2d(50, 50), gg.star(20000), gg.cycle(10))
+    off, adj = _csr(n, s, d)
+    assert_parity(kc, n, off, adj)
+
+
+@pytest.mark.parametrize("opts", [
+    dict(slice_arcs=32), dict(slice_arcs=4096), dict(local_queue=0), dict(local_queue=128),
+    dict(ctas_per_sm=1), dict(min_ctas=1, vertices_per_cta=1 << 40), dict(vertices_per_cta=1),
+])
+def test_tuning_modes(opts):
+    n, s, d = gg.disjoint_union(gg.rmat_n(30000, 300000, seed=5), gg.staircase(120),
+                                gg.path(2000), gg.star(3000))
+    off, adj = _csr(n, s, d)
+    want = oracle.bz(n, off, adj)
+    with KCore(0, **opts) as k:
+        assert_parity(k, n, off, adj, want)
+
+
+def test_star_hub(kc):
+    n, s, d = gg.star(1_000_000)
+    off, adj = _csr(n, s, d)
+    got, km = gpu_core(kc, off, adj)
+    assert (got == 1).all() and km == 1
+
+
+def test_long_path(kc):
+    n, s, d = gg.path(1_000_000)
+    off, adj = _csr(n, s, d)
+    got, km = gpu_core(kc, off, adj)
+    assert (got == 1).all() and km == 1
+
+
+def test_staircase_many_levels(kc):
+    n, s, d = gg.staircase(2000)
+    off, adj = _csr(n, s, d)
+    got = assert_parity(kc, n, off, adj)
+    assert got.max() == 2000
+    st = kc.stats()
+    assert st["kmax"] == 2000 and st["rounds"] >= 2000
+
+
+def test_each_vertex_processed_once(kc):
+    """Every vertex with arcs is processed exactly once (Theorem 1's proof):
+    as global slices or from a warp-local queue."""
+    n, s, d = gg.rmat_n(50000, 400000, seed=9)
+    off, adj = _csr(n, s, d)
+    assert_parity(kc, n, off, adj)
+    st = kc.stats()
+    deg = np.diff(off)
+    slices = int(np.sum((deg + 255) // 256))
+    local = st["local_items"]
+    # local items are one-slice vertices taken out of the global stream
+    assert st["items"] + local == slices
+
+
+def test_host_entry_point(kc):
+    n, s, d = gg.workload_er10k()
+    off, adj = _csr(n, s, d)
+    core, km = kc.decompose_host(off, adj)
+    want = oracle.bz(n, off, adj)
+    np.testing.assert_array_equal(core, want)
+    assert km == want.max()
+
+
+def test_caller_workspace(kc):
+    n, s, d = gg.rmat_n(20000, 100000, seed=3)
+    off, adj = _csr(n, s, d)
+    with KCore(0) as k:
+        ws = torch.empty(k.workspace_size(n, len(adj)), dtype=torch.uint8, device="cuda:0")
+        k.set_workspace(ws)
+        assert_parity(k, n, off, adj)
+        small = torch.empty(1024, dtype=torch.uint8, device="cuda:0")
+        k.set_workspace(small)
+        o, a = to_dev(off, adj)
+        with pytest.raises(KCoreError) as e:
+            k.decompose(o, a)
+        assert e.value.code == "OOM"
+
+
+def test_timeout_is_reported_and_context_survives():
+    """A wait that can never be satisfied (CTA 0 withholds its completion
+    token) must end at the time limit with KCORE_ERR_TIMEOUT, and the same
+    context must then decompose normally."""
+    n, s, d = gg.rmat_n(5000, 40000, seed=1)
+    off, adj = _csr(n, s, d)
+    o, a = to_dev(off, adj)
+    with KCore(0, timeout_ms=200, test_stall=1) as k:
+        with pytest.raises(KCoreError) as e:
+            k.decompose(o, a)
+        assert e.value.code == "TIMEOUT"
+        k.set_option("test_stall", 0)
+        assert_parity(k, n, off, adj)
+
+
+def test_malformed_offsets_rejected_on_device(kc):
+    off = np.array([0, 2, 1, 3], np.int64)  # decreasing offsets
+    adj = np.array([1, 2, 0], np.int32)
+    o, a = to_dev(off, adj)
+    with pytest.raises(KCoreError) as e:
+        kc.decompose(o, a)
+    assert e.value.code == "NOT_SIMPLE"
+
+
+def test_out_of_range_neighbour_rejected(kc):
+    off = np.array([0, 1, 2], np.int64)
+    adj = np.array([1, 7], np.int32)  # 7 is not a vertex
+    o, a = to_dev(off, adj)
+    with pytest.raises(KCoreError) as e:
+        kc.decompose(o, a)
+    assert e.value.code == "NOT_SIMPLE"
+
+
+def test_argument_errors(kc):
+    o, a = to_dev(np.array([0, 1, 2], np.int64), np.array([1, 0], np.int32))
+    L = kc._L
+    assert L.kcore_decompose(kc._h, -1, 2, o.data_ptr(), a.data_ptr(), None, None, None) == 1
+    assert L.kcore_decompose(kc._h, 2, 2, None, a.data_ptr(), None, None, None) == 1
+    with pytest.raises(KCoreError):
+        kc.set_option("slice_arcs", 1)
