@@ -58,14 +58,15 @@ typedef enum {
 typedef enum {
   KCORE_OPT_SYNC_MODE = 0,     /* 0 auto, 1 persistent kernel (device-wide counters), 2 graph relaunch */
   KCORE_OPT_CTAS_PER_SM = 1,   /* CTAs per SM of the persistent kernel (0 = occupancy maximum) */
-  KCORE_OPT_SLICE_ARCS = 2,    /* arcs per work item: longer adjacency lists are split in slices */
+  KCORE_OPT_SLICE_ARCS = 2,    /* arcs per work item (16 .. 2^20): longer lists are split in slices */
   KCORE_OPT_LOCAL_QUEUE = 3,   /* per-warp local queue capacity (vertices), 0 disables it */
   KCORE_OPT_TIMEOUT_MS = 4,    /* limit for every device-side wait, milliseconds */
   KCORE_OPT_MIN_CTAS = 5,      /* lower bound of the grid for small graphs */
   KCORE_OPT_VERTICES_PER_CTA = 6, /* grid sizing: about one CTA per this many vertices+arcs/8 */
-  KCORE_OPT_TEST_STALL = 7       /* test hook, default 0: 1 makes CTA 0 withhold its round-1
+  KCORE_OPT_TEST_STALL = 7,      /* test hook, default 0: 1 makes CTA 0 withhold its round-1
                                     completion token, so every device wait must run out its
                                     time limit and the call ends with KCORE_ERR_TIMEOUT */
+  KCORE_OPT_TRACE = 8            /* 1 records a per-round timeline (kcore_get_trace) */
 } kcore_option;
 
 /* Counters of the last decomposition (valid after kcore_sync_status). */
@@ -128,12 +129,46 @@ kcore_status kcore_decompose_host(kcore_handle h, int64_t n, int64_t m, const in
                                   const int32_t* adj_host, int32_t* coreness_host,
                                   int32_t* kmax_host, kcore_stream_t stream);
 
+/* Simple undirected CSR of an edge list (a1 of the pipeline; the paper
+ * symmetrises directed inputs, Sec. 6.1 "Datasets"): every pair (src[i],
+ * dst[i]) with src[i] != dst[i] contributes the arcs src->dst and dst->src;
+ * self-loops are dropped and repeated arcs kept once; each adjacency list is
+ * ascending.
+ *   n               vertices (ids in [0, n)); 0 <= n <= 2^31 - 2
+ *   num_edges       pairs in src/dst (may contain duplicates, both directions,
+ *                   self-loops)
+ *   src, dst        device int32[num_edges], borrowed
+ *   offsets_out     device int64[n+1]
+ *   adj_out         device int32 with room for 2 * num_edges entries (the
+ *                   worst case); the first m are written
+ *   m_out           device int64[1]: m, the number of arcs written
+ * Asynchronous; uses the handle's workspace (kcore_build_csr_workspace_size
+ * bytes: two key buffers of 2 * num_edges uint64 plus histograms). A vertex id
+ * outside [0, n) is reported as KCORE_ERR_INVALID by kcore_sync_status. */
+kcore_status kcore_build_csr(kcore_handle h, int64_t n, int64_t num_edges, const int32_t* src,
+                             const int32_t* dst, int64_t* offsets_out, int32_t* adj_out,
+                             int64_t* m_out, kcore_stream_t stream);
+
+/* Workspace bytes kcore_build_csr needs (host call). */
+kcore_status kcore_build_csr_workspace_size(kcore_handle h, int64_t n, int64_t num_edges, size_t* bytes);
+
 /* Waits for the stream of the handle's last call and returns the status the
  * device recorded (KCORE_OK, KCORE_ERR_TIMEOUT, ...). */
 kcore_status kcore_sync_status(kcore_handle h);
 
 /* Counters of the last decomposition; call after kcore_sync_status. */
 kcore_status kcore_get_stats(kcore_handle h, kcore_stats* out);
+
+/* Per-round timeline of the last decomposition when KCORE_OPT_TRACE was 1
+ * (call after kcore_sync_status). out receives 12 uint64 per round:
+ * [0] device time (ns) the round started, [1] when its scan finished,
+ * [2] when the round finished, [3] its level k, [4] active-list entries
+ * scanned, [5] frontier vertices found by the scan, [6] work items queued,
+ * [7] CTAs that scanned, [8] arcs read, [9] decrements issued, [10] longest
+ * scan of one CTA (ns), [11] latest round start of a CTA after CTA 0 (ns).
+ * Tracing adds atomics and slows the run. At most max_rounds rounds are
+ * copied; *rounds_out receives the number copied. */
+kcore_status kcore_get_trace(kcore_handle h, uint64_t* out, int64_t max_rounds, int64_t* rounds_out);
 
 #ifdef __cplusplus
 }

@@ -39,7 +39,7 @@ def _sources():
 
 def _deps():
     return _sources() + sorted(glob.glob(os.path.join(CSRC, "*.h"))) + \
-        sorted(glob.glob(os.path.join(CSRC, "*.cuh"))) + [os.path.join(INCLUDE, "kcore.h")]
+        sorted(glob.glob(os.path.join(CSRC, "*.cuh"))) + sorted(glob.glob(os.path.join(INCLUDE, "*.h")))
 
 
 def up_to_date() -> bool:
@@ -114,6 +114,9 @@ SIGNATURES = {
     "kcore_decompose_host": ([c_p, c_i64, c_i64, c_p, c_p, c_p, c_p, c_p], ctypes.c_int),
     "kcore_sync_status": ([c_p], ctypes.c_int),
     "kcore_get_stats": ([c_p, ctypes.POINTER(Stats)], ctypes.c_int),
+    "kcore_get_trace": ([c_p, c_p, c_i64, ctypes.POINTER(c_i64)], ctypes.c_int),
+    "kcore_build_csr": ([c_p, c_i64, c_i64, c_p, c_p, c_p, c_p, c_p, c_p], ctypes.c_int),
+    "kcore_build_csr_workspace_size": ([c_p, c_i64, c_i64, ctypes.POINTER(c_sz)], ctypes.c_int),
 }
 
 

@@ -9,6 +9,7 @@
 #include <string>
 
 #include "kcore.h"
+#include "kcore_csr.h"
 #include "kcore_peel.h"
 
 struct kcore_ctx {
@@ -19,10 +20,13 @@ struct kcore_ctx {
   size_t ws_bytes = 0;
   bool ws_external = false;
   std::string err;
-  int64_t opt[8] = {0, 0, 256, 64, 2000, 1, 2048, 0};  // indexed by kcore_option
+  int64_t opt[9] = {0, 0, 512, 32, 2000, 1, 2048, 0, 0};  // indexed by kcore_option
   cudaStream_t last_stream = nullptr;
   bool pending = false;
   kc::PeelCtl* last_ctl = nullptr;
+  int* last_csr_status = nullptr;  // device status word of the last CSR build
+  unsigned long long* last_trace = nullptr;
+  int last_max_rounds = 0;
   kcore_stats stats{};
   int last_grid = 0;
   int last_mode = 0;
@@ -65,7 +69,7 @@ long long isqrt_ll(long long m) {
 }
 
 struct PeelLayout {
-  size_t deg, a0, a1, q, rounds, ctl, total;
+  size_t deg, a0, a1, q, rounds, ctl, trace, total;
   long long qcap;
   int max_rounds;
 };
@@ -93,6 +97,8 @@ PeelLayout peel_layout(long long n, long long m, int slice) {
   off = align_up(off + 4 * (size_t)n, 256);
   L.q = off;
   off = align_up(off + 8 * (size_t)L.qcap, 256);
+  L.trace = off;
+  off = align_up(off + 8 * (size_t)kc::kTraceFields * (size_t)L.max_rounds, 256);
   L.total = off;
   return L;
 }
@@ -167,8 +173,11 @@ kcore_status kcore_destroy(kcore_handle h) {
 const char* kcore_last_error(kcore_handle h) { return h ? h->err.c_str() : "null handle"; }
 
 kcore_status kcore_set_option(kcore_handle h, kcore_option opt, int64_t value) {
-  if (!h || (int)opt < 0 || (int)opt > 7) return KCORE_ERR_INVALID;
+  if (!h || (int)opt < 0 || (int)opt > 8) return KCORE_ERR_INVALID;
   switch (opt) {
+    case KCORE_OPT_TRACE:
+      if (value < 0 || value > 1) return fail(h, KCORE_ERR_INVALID, "trace must be 0 or 1");
+      break;
     case KCORE_OPT_TEST_STALL:
       if (value < 0 || value > 1) return fail(h, KCORE_ERR_INVALID, "test stall must be 0 or 1");
       break;
@@ -180,7 +189,8 @@ kcore_status kcore_set_option(kcore_handle h, kcore_option opt, int64_t value) {
         return fail(h, KCORE_ERR_INVALID, "CTAs per SM above the occupancy limit");
       break;
     case KCORE_OPT_SLICE_ARCS:
-      if (value < 32 || value > (1 << 20)) return fail(h, KCORE_ERR_INVALID, "slice must be in [32, 2^20]");
+      if (value < kc::kMinSlice || value > (1 << 20))
+        return fail(h, KCORE_ERR_INVALID, "slice must be in [16, 2^20]");
       break;
     case KCORE_OPT_LOCAL_QUEUE:
       if (value < 0 || value > kc::kLocalQueueMax)
@@ -201,7 +211,7 @@ kcore_status kcore_set_option(kcore_handle h, kcore_option opt, int64_t value) {
 }
 
 kcore_status kcore_get_option(kcore_handle h, kcore_option opt, int64_t* value) {
-  if (!h || !value || (int)opt < 0 || (int)opt > 7) return KCORE_ERR_INVALID;
+  if (!h || !value || (int)opt < 0 || (int)opt > 8) return KCORE_ERR_INVALID;
   *value = h->opt[opt];
   return KCORE_OK;
 }
@@ -240,6 +250,8 @@ kcore_status kcore_decompose(kcore_handle h, int64_t n, int64_t m, const int64_t
   h->err.clear();
   h->stats = kcore_stats{};
   h->last_ctl = nullptr;
+  h->last_csr_status = nullptr;
+  h->last_trace = nullptr;
   h->last_stream = stream;
   h->pending = true;
   if (n == 0) {
@@ -271,8 +283,9 @@ kcore_status kcore_decompose(kcore_handle h, int64_t n, int64_t m, const int64_t
   a.lq_cap = (int)h->opt[KCORE_OPT_LOCAL_QUEUE];
   a.max_take = 256;
   a.timeout_ns = (unsigned long long)h->opt[KCORE_OPT_TIMEOUT_MS] * 1000000ull;
-  a.max_backoff_ns = 1024;
+  a.scan_min = 2048;
   a.inject_stall = (int)h->opt[KCORE_OPT_TEST_STALL];
+  a.trace = h->opt[KCORE_OPT_TRACE] ? (unsigned long long*)(ws + L.trace) : nullptr;
 
   int per_sm = h->opt[KCORE_OPT_CTAS_PER_SM] > 0 ? (int)h->opt[KCORE_OPT_CTAS_PER_SM] : h->max_ctas_per_sm;
   long long gmax = (long long)h->sms * per_sm;
@@ -286,10 +299,47 @@ kcore_status kcore_decompose(kcore_handle h, int64_t n, int64_t m, const int64_t
   if ((e = cudaMemsetAsync(ws, 0, L.deg, stream)) != cudaSuccess) return cuda_fail(h, e, "memset ctl");
   if ((e = cudaMemsetAsync(ws + L.q, 0xff, 8 * (size_t)L.qcap, stream)) != cudaSuccess)
     return cuda_fail(h, e, "memset queue");
+  if (a.trace && (e = cudaMemsetAsync(a.trace, 0, L.total - L.trace, stream)) != cudaSuccess)
+    return cuda_fail(h, e, "memset trace");
   if ((e = kc::peel_launch(a, (int)grid, stream)) != cudaSuccess) return cuda_fail(h, e, "peel launch");
   h->last_ctl = a.ctl;
+  h->last_trace = a.trace;
+  h->last_max_rounds = L.max_rounds;
   h->last_grid = (int)grid;
   h->last_mode = 1;
+  return KCORE_OK;
+}
+
+kcore_status kcore_build_csr_workspace_size(kcore_handle h, int64_t n, int64_t num_edges, size_t* bytes) {
+  if (!h || !bytes || n < 0 || n > INT32_MAX - 1 || num_edges < 0) return KCORE_ERR_INVALID;
+  *bytes = kc::csr_layout(n, num_edges, h->sms).total;
+  return KCORE_OK;
+}
+
+kcore_status kcore_build_csr(kcore_handle h, int64_t n, int64_t num_edges, const int32_t* src,
+                             const int32_t* dst, int64_t* offsets_out, int32_t* adj_out,
+                             int64_t* m_out, kcore_stream_t stream_) {
+  if (!h) return KCORE_ERR_INVALID;
+  cudaStream_t stream = (cudaStream_t)stream_;
+  if (n < 0 || n > INT32_MAX - 1 || num_edges < 0 || num_edges > ((int64_t)1 << 40))
+    return fail(h, KCORE_ERR_INVALID, "n or number of edges out of range");
+  if (!offsets_out || !m_out) return fail(h, KCORE_ERR_INVALID, "null offsets_out/m_out");
+  if (num_edges > 0 && (!src || !dst || !adj_out)) return fail(h, KCORE_ERR_INVALID, "null edge or adj pointer");
+  if (n == 0 && num_edges > 0) return fail(h, KCORE_ERR_INVALID, "edges given for an empty vertex set");
+  DeviceGuard g(h->device);
+  if (!g.ok) return fail(h, KCORE_ERR_CUDA, "cudaSetDevice failed");
+  h->err.clear();
+  h->last_ctl = nullptr;
+  h->last_trace = nullptr;
+  h->last_stream = stream;
+  h->pending = true;
+  kc::CsrLayout L = kc::csr_layout(n, num_edges, h->sms);
+  kcore_status st = ensure_ws(h, L.total);
+  if (st != KCORE_OK) return st;
+  cudaError_t e = kc::csr_build_launch(L, (char*)h->ws, n, num_edges, src, dst, (long long*)offsets_out,
+                                       adj_out, (long long*)m_out, stream);
+  if (e != cudaSuccess) return cuda_fail(h, e, "CSR build launch");
+  h->last_csr_status = (int*)((char*)h->ws + L.status);
   return KCORE_OK;
 }
 
@@ -300,6 +350,14 @@ kcore_status kcore_sync_status(kcore_handle h) {
   cudaError_t e = cudaStreamSynchronize(h->last_stream);
   h->pending = false;
   if (e != cudaSuccess) return cuda_fail(h, e, "stream synchronize");
+  if (h->last_csr_status) {
+    int cs = 0;
+    e = cudaMemcpy(&cs, h->last_csr_status, sizeof(int), cudaMemcpyDeviceToHost);
+    h->last_csr_status = nullptr;
+    if (e != cudaSuccess) return cuda_fail(h, e, "read status");
+    if (cs != 0) return fail(h, KCORE_ERR_INVALID, "edge list holds a vertex id outside [0, n)");
+    return KCORE_OK;
+  }
   if (!h->last_ctl) return KCORE_OK;
   kc::PeelCtl c;
   e = cudaMemcpy(&c, h->last_ctl, sizeof(c), cudaMemcpyDeviceToHost);
@@ -324,6 +382,21 @@ kcore_status kcore_sync_status(kcore_handle h) {
     default:
       return fail(h, KCORE_ERR_CUDA, "unknown device status " + std::to_string(c.status));
   }
+}
+
+kcore_status kcore_get_trace(kcore_handle h, uint64_t* out, int64_t max_rounds, int64_t* rounds_out) {
+  if (!h || !out || !rounds_out || max_rounds < 0) return KCORE_ERR_INVALID;
+  *rounds_out = 0;
+  if (!h->last_trace) return fail(h, KCORE_ERR_INVALID, "the last decomposition ran without tracing");
+  DeviceGuard g(h->device);
+  int64_t r = std::min<int64_t>(std::min<int64_t>(max_rounds, h->stats.rounds), h->last_max_rounds);
+  if (r > 0) {
+    cudaError_t e = cudaMemcpy(out, h->last_trace, sizeof(uint64_t) * kc::kTraceFields * (size_t)r,
+                               cudaMemcpyDeviceToHost);
+    if (e != cudaSuccess) return cuda_fail(h, e, "read trace");
+  }
+  *rounds_out = r;
+  return KCORE_OK;
 }
 
 kcore_status kcore_get_stats(kcore_handle h, kcore_stats* out) {

@@ -1,0 +1,325 @@
+// CSR build on sm_103a: edge list -> simple undirected CSR.
+//
+// The paper symmetrises directed inputs (Sec. 6.1, "Datasets"); the peel needs
+// a simple graph. Steps, all on the device:
+//   1. keys: each pair (a, b) with a != b gives the arcs a->b and b->a as
+//      integers (a << B) | b with B = bits of n-1; self-loops and ids out of
+//      range become a sentinel that sorts last (ids out of range also set an
+//      error status).
+//   2. stable LSD radix sort of the keys over their 2B significant bits, 8-bit
+//      digits. Each CTA owns a contiguous chunk; a pass is an upsweep (digit
+//      histogram per CTA), a scan of the 256 x CTAs histogram, and a downsweep
+//      that ranks each 4096-key tile in shared memory (warp match for the
+//      within-iteration rank) and writes runs of equal digits contiguously.
+//   3. unique + emit: keys equal to their predecessor are dropped; the rest
+//      are written in order as adj[] (low B bits), and the first arc of each
+//      source vertex fixes offsets[] (vertices without arcs take the next
+//      vertex's offset).
+// Lists come out ascending and duplicate-free, the canonical form of the CPU
+// builder, so the two are comparable bit for bit.
+#include <climits>
+
+#include "kcore_csr.h"
+#include "kcore_device.cuh"
+
+namespace kc {
+
+constexpr int kCsrBlock = 256;
+constexpr int kKeysPerThread = 16;
+constexpr int kTile = kCsrBlock * kKeysPerThread;  // 4096
+constexpr unsigned long long kSentinel = ~0ull;
+
+__global__ void csr_make_keys(const int* src, const int* dst, long long E, long long n, int B,
+                              unsigned long long* keys, int* status) {
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < E;
+       i += (long long)gridDim.x * blockDim.x) {
+    int a = src[i], b = dst[i];
+    unsigned long long k0 = kSentinel, k1 = kSentinel;
+    if ((unsigned long long)(unsigned)a >= (unsigned long long)n ||
+        (unsigned long long)(unsigned)b >= (unsigned long long)n) {
+      atomicCAS(status, 0, 1);
+    } else if (a != b) {
+      k0 = ((unsigned long long)a << B) | (unsigned long long)b;
+      k1 = ((unsigned long long)b << B) | (unsigned long long)a;
+    }
+    keys[2 * i] = k0;
+    keys[2 * i + 1] = k1;
+  }
+}
+
+__device__ __forceinline__ int digit_of(unsigned long long k, int shift) {
+  return (int)((k >> shift) & 0xffull);
+}
+
+// Per-CTA digit histogram of its chunk: hist[d * G + g].
+__global__ void __launch_bounds__(kCsrBlock) rs_upsweep(const unsigned long long* keys, long long N,
+                                                        long long chunk, int shift,
+                                                        unsigned* hist) {
+  __shared__ unsigned cnt[kCsrBlock / 32][256];
+  const int tid = threadIdx.x, warp = tid >> 5;
+  for (int i = tid; i < (kCsrBlock / 32) * 256; i += kCsrBlock) (&cnt[0][0])[i] = 0;
+  __syncthreads();
+  long long lo = (long long)blockIdx.x * chunk, hi = min(N, lo + chunk);
+  for (long long i = lo + tid; i < hi; i += kCsrBlock) atomicAdd(&cnt[warp][digit_of(keys[i], shift)], 1u);
+  __syncthreads();
+  unsigned s = 0;
+  for (int w = 0; w < kCsrBlock / 32; w++) s += cnt[w][tid];
+  hist[(long long)tid * gridDim.x + blockIdx.x] = s;
+}
+
+// Exclusive scan of a uint32 array into uint64 (one CTA of 1024 threads).
+__global__ void __launch_bounds__(1024) scan_u32_to_u64(const unsigned* in, unsigned long long* out,
+                                                        long long len) {
+  __shared__ unsigned long long part[32];
+  __shared__ unsigned long long carry;
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  if (tid == 0) carry = 0;
+  __syncthreads();
+  for (long long base = 0; base < len; base += 1024) {
+    long long i = base + tid;
+    unsigned long long x = i < len ? in[i] : 0;
+    unsigned long long incl = warp_incl_scan(x, lane);
+    if (lane == 31) part[warp] = incl;
+    __syncthreads();
+    if (warp == 0) {
+      unsigned long long p = part[lane];
+      unsigned long long pi = warp_incl_scan(p, lane);
+      part[lane] = pi - p;
+    }
+    __syncthreads();
+    unsigned long long c = carry;
+    if (i < len) out[i] = c + part[warp] + incl - x;
+    __syncthreads();
+    if (tid == 1023) carry = c + part[warp] + incl;
+    __syncthreads();
+  }
+}
+
+// Stable scatter of one radix pass. Each CTA walks its chunk tile by tile, in
+// order; offs[d * G + g] is where its first key of digit d goes.
+__global__ void __launch_bounds__(kCsrBlock) rs_downsweep(const unsigned long long* in,
+                                                          unsigned long long* out, long long N,
+                                                          long long chunk, int shift,
+                                                          const unsigned long long* offs) {
+  __shared__ unsigned long long buf[kTile];
+  __shared__ unsigned wbase[kCsrBlock / 32][256];
+  __shared__ unsigned local_off[256];
+  __shared__ unsigned tile_cnt[256];
+  __shared__ unsigned long long run[256];
+  __shared__ unsigned part[kCsrBlock / 32];
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const int G = gridDim.x;
+  run[tid] = offs[(long long)tid * G + blockIdx.x];
+  long long lo = (long long)blockIdx.x * chunk, hi = min(N, lo + chunk);
+  for (long long ts = lo; ts < hi; ts += kTile) {
+    const long long tn = min((long long)kTile, hi - ts);
+    for (int i = tid; i < (kCsrBlock / 32) * 256; i += kCsrBlock) (&wbase[0][0])[i] = 0;
+    __syncthreads();
+    unsigned long long k[kKeysPerThread];
+    int dg[kKeysPerThread];
+#pragma unroll
+    for (int it = 0; it < kKeysPerThread; it++) {
+      long long j = (long long)warp * (kKeysPerThread * 32) + it * 32 + lane;
+      dg[it] = 256;  // invalid lane
+      k[it] = 0;
+      if (j < tn) {
+        k[it] = in[ts + j];
+        dg[it] = digit_of(k[it], shift);
+        atomicAdd(&wbase[warp][dg[it]], 1u);
+      }
+    }
+    __syncthreads();
+    // per digit (thread d): tile count, then exclusive scan over digits
+    unsigned tc = 0;
+    for (int w = 0; w < kCsrBlock / 32; w++) tc += wbase[w][tid];
+    tile_cnt[tid] = tc;
+    unsigned incl = warp_incl_scan(tc, lane);
+    if (lane == 31) part[warp] = incl;
+    __syncthreads();
+    if (warp == 0) {
+      unsigned p = lane < kCsrBlock / 32 ? part[lane] : 0;
+      unsigned pi = warp_incl_scan(p, lane);
+      if (lane < kCsrBlock / 32) part[lane] = pi - p;
+    }
+    __syncthreads();
+    unsigned lo_d = part[warp] + incl - tc;
+    local_off[tid] = lo_d;
+    unsigned acc = lo_d;
+    for (int w = 0; w < kCsrBlock / 32; w++) {
+      unsigned c = wbase[w][tid];
+      wbase[w][tid] = acc;
+      acc += c;
+    }
+    __syncthreads();
+    // ranks in key order: warps own consecutive sub-ranges, iterations go in order
+#pragma unroll
+    for (int it = 0; it < kKeysPerThread; it++) {
+      unsigned peers = __match_any_sync(kFull, dg[it]);
+      int rank = __popc(peers & lanemask_lt());
+      unsigned b = 0;
+      if (dg[it] < 256) {
+        b = wbase[warp][dg[it]];
+        buf[b + rank] = k[it];
+      }
+      __syncwarp();
+      if (dg[it] < 256 && rank == 0) wbase[warp][dg[it]] = b + __popc(peers);
+      __syncwarp();
+    }
+    __syncthreads();
+    for (int j = tid; j < tn; j += kCsrBlock) {
+      unsigned long long key = buf[j];
+      int d = digit_of(key, shift);
+      out[run[d] + (unsigned long long)(j - local_off[d])] = key;
+    }
+    __syncthreads();
+    run[tid] += tile_cnt[tid];
+    __syncthreads();
+  }
+}
+
+// Unique keys of each CTA chunk (a key differing from its predecessor).
+__global__ void __launch_bounds__(kCsrBlock) csr_count_unique(const unsigned long long* k, long long N,
+                                                              long long chunk, unsigned* cnt) {
+  __shared__ unsigned part[kCsrBlock / 32];
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  long long lo = (long long)blockIdx.x * chunk, hi = min(N, lo + chunk);
+  unsigned c = 0;
+  for (long long i = lo + tid; i < hi; i += kCsrBlock) {
+    unsigned long long x = k[i];
+    if (x != kSentinel && (i == 0 || k[i - 1] != x)) c++;
+  }
+  c = warp_sum(c);
+  if (lane == 0) part[warp] = c;
+  __syncthreads();
+  if (tid == 0) {
+    unsigned s = 0;
+    for (int w = 0; w < kCsrBlock / 32; w++) s += part[w];
+    cnt[blockIdx.x] = s;
+  }
+}
+
+// Ordered emission of the unique keys: adj[pos] = low B bits; the first arc
+// of each source fixes offsets[] for that source and every source without
+// arcs just below it; the last arc fills the offsets of the sources above it.
+__global__ void __launch_bounds__(kCsrBlock) csr_emit(const unsigned long long* k, long long N,
+                                                      long long chunk, int B, long long n,
+                                                      const unsigned long long* base, int* adj,
+                                                      long long* off, long long* m_out) {
+  __shared__ unsigned part[kCsrBlock / 32];
+  __shared__ unsigned long long running;
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const unsigned long long mask = (1ull << B) - 1;
+  long long lo = (long long)blockIdx.x * chunk, hi = min(N, lo + chunk);
+  if (tid == 0) running = base[blockIdx.x];
+  __syncthreads();
+  for (long long ts = lo; ts < hi; ts += kCsrBlock) {
+    long long i = ts + tid;
+    bool f = false;
+    unsigned long long x = 0, prev = kSentinel;
+    if (i < hi) {
+      x = k[i];
+      prev = i > 0 ? k[i - 1] : kSentinel;
+      f = x != kSentinel && (i == 0 || prev != x);
+    }
+    unsigned flag = f ? 1u : 0u;
+    unsigned incl = warp_incl_scan(flag, lane);
+    if (lane == 31) part[warp] = incl;
+    __syncthreads();
+    if (warp == 0) {
+      unsigned p = lane < kCsrBlock / 32 ? part[lane] : 0;
+      unsigned pi = warp_incl_scan(p, lane);
+      if (lane < kCsrBlock / 32) part[lane] = pi - p;
+    }
+    __syncthreads();
+    unsigned long long r0 = running;
+    // position of the latest unique key at or before i (this one when f)
+    unsigned long long pos = r0 + part[warp] + incl - 1;
+    if (f) {
+      adj[pos] = (int)(x & mask);
+      long long s = (long long)(x >> B);
+      long long ps = (i == 0 || prev == kSentinel) ? -1 : (long long)(prev >> B);
+      if (s != ps)
+        for (long long v = ps + 1; v <= s; v++) off[v] = (long long)pos;
+    }
+    // the last valid key (unique or a repeat) closes the offsets above its source
+    if (i < hi && x != kSentinel && ((i + 1 == N) || k[i + 1] == kSentinel)) {
+      long long s = (long long)(x >> B);
+      for (long long v = s + 1; v <= n; v++) off[v] = (long long)pos + 1;
+      *m_out = (long long)pos + 1;
+    }
+    __syncthreads();
+    if (tid == kCsrBlock - 1) running = r0 + part[warp] + incl;
+    __syncthreads();
+  }
+}
+
+// ------------------------------------------------------------------ host side
+static int bits_for(long long n) {
+  int B = 1;
+  while ((1ll << B) < n) B++;
+  return B;
+}
+
+CsrLayout csr_layout(long long n, long long E, int sms) {
+  CsrLayout L{};
+  long long N = 2 * E;
+  long long G = (long long)sms * 2;
+  long long tiles = (N + kTile - 1) / kTile;
+  if (tiles < G) G = tiles < 1 ? 1 : tiles;
+  L.grid = (int)G;
+  long long chunk = (N + G - 1) / G;
+  chunk = (chunk + kTile - 1) / kTile * kTile;
+  if (chunk < kTile) chunk = kTile;
+  L.chunk = chunk;
+  L.N = N;
+  L.B = bits_for(n);
+  size_t off = 0;
+  auto al = [](size_t x) { return (x + 255) / 256 * 256; };
+  L.status = off;
+  off = al(off + 256);
+  L.keys0 = off;
+  off = al(off + 8 * (size_t)(N > 0 ? N : 1));
+  L.keys1 = off;
+  off = al(off + 8 * (size_t)(N > 0 ? N : 1));
+  L.hist = off;
+  off = al(off + 4 * 256 * (size_t)G);
+  L.offs = off;
+  off = al(off + 8 * 256 * (size_t)G);
+  L.total = off;
+  return L;
+}
+
+cudaError_t csr_build_launch(const CsrLayout& L, char* ws, long long n, long long E, const int* src,
+                             const int* dst, long long* off_out, int* adj_out, long long* m_out,
+                             cudaStream_t stream) {
+  cudaError_t e;
+  int* status = (int*)(ws + L.status);
+  unsigned long long* k0 = (unsigned long long*)(ws + L.keys0);
+  unsigned long long* k1 = (unsigned long long*)(ws + L.keys1);
+  unsigned* hist = (unsigned*)(ws + L.hist);
+  unsigned long long* offs = (unsigned long long*)(ws + L.offs);
+  if ((e = cudaMemsetAsync(status, 0, 256, stream)) != cudaSuccess) return e;
+  if ((e = cudaMemsetAsync(off_out, 0, 8 * (size_t)(n + 1), stream)) != cudaSuccess) return e;
+  if ((e = cudaMemsetAsync(m_out, 0, 8, stream)) != cudaSuccess) return e;
+  if (E == 0) return cudaSuccess;
+  const long long N = L.N;
+  const int G = L.grid;
+  int kb = (int)std::min<long long>((E + kCsrBlock - 1) / kCsrBlock, 65536);
+  csr_make_keys<<<kb, kCsrBlock, 0, stream>>>(src, dst, E, n, L.B, k0, status);
+  const int passes = (2 * L.B + 7) / 8;
+  for (int p = 0; p < passes; p++) {
+    int shift = 8 * p;
+    rs_upsweep<<<G, kCsrBlock, 0, stream>>>(k0, N, L.chunk, shift, hist);
+    scan_u32_to_u64<<<1, 1024, 0, stream>>>(hist, offs, 256ll * G);
+    rs_downsweep<<<G, kCsrBlock, 0, stream>>>(k0, k1, N, L.chunk, shift, offs);
+    unsigned long long* t = k0;
+    k0 = k1;
+    k1 = t;
+  }
+  csr_count_unique<<<G, kCsrBlock, 0, stream>>>(k0, N, L.chunk, hist);
+  scan_u32_to_u64<<<1, 1024, 0, stream>>>(hist, offs, G);
+  csr_emit<<<G, kCsrBlock, 0, stream>>>(k0, N, L.chunk, L.B, n, offs, adj_out, off_out, m_out);
+  return cudaGetLastError();
+}
+
+}  // namespace kc

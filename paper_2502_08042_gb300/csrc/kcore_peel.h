@@ -9,26 +9,42 @@ namespace kc {
 enum : int { ST_OK = 0, ST_TIMEOUT = 4, ST_NOT_SIMPLE = 5, ST_CAPACITY = 6 };
 
 constexpr int kLocalQueueMax = 128;
+constexpr int kMinSlice = 16;  // keeps slice indices below 2^27 (27-bit field of a work item)
 
-// Per-round record (zeroed before launch).
+// Per-round record (zeroed before launch). Each hot word has its own 128-byte
+// line: the termination counter, the queue's claim and append counters.
 struct RoundRec {
-  unsigned long long cnt;    // (scan tokens << 40) + outstanding work items
+  unsigned long long cnt;  // (scan tokens << 40) + outstanding work items
+  char pad0[120];
+  unsigned long long head;  // tickets handed out in this round's queue segment
+  char pad1[120];
+  unsigned long long tail;  // items appended to this round's queue segment
+  char pad2[120];
   unsigned long long found;  // frontier vertices claimed by the scan
   unsigned long long alen;   // length of the next active list
   int minkey;                // max over survivors of INT_MAX - d~ (0: no survivor)
-  int pad;
+  int pad3;
+  char pad4[104];
 };
 
-// Device control block (zeroed before launch); hot words on their own lines.
+// Round-completion broadcast: the thread whose counter update finishes round r
+// copies the round's results here and then publishes round = r + 1. Each CTA
+// polls one of kDoneLines copies, so no single cache line takes every poll.
+constexpr int kDoneLines = 16;
+struct DoneLine {
+  int round;
+  int minkey;
+  unsigned long long found, alen, tail;
+  char pad[96];
+};
+
+// Device control block (zeroed before launch).
 struct PeelCtl {
-  unsigned long long qtail;
-  char pad0[120];
-  unsigned long long qhead;
-  char pad1[120];
+  DoneLine done[kDoneLines];
   int status;
-  int pad2[31];
-  unsigned long long progress;
-  char pad4[120];
+  int pad1[31];
+  unsigned long long progress;  // heartbeat of long single-warp chains
+  char pad2[120];
   unsigned long long items, local_items;
   long long rounds, empty_rounds, scanned, kmax;
   char pad3[80];
@@ -52,10 +68,18 @@ struct PeelArgs {
   int lq_cap;
   int max_take;
   int take_div;
-  int max_backoff_ns;
+  int scan_min;  // active-list entries per scanning CTA (at least)
   unsigned long long timeout_ns;
   int inject_stall;
+  unsigned long long* trace;  // optional: kTraceFields words per round (nullptr = off)
 };
+
+// Per-round trace record (KCORE_OPT_TRACE): globaltimer at round start (CTA 0),
+// when the last scan token arrived, when the round finished; the level, the
+// active-list length scanned, frontier vertices found, items queued, the
+// scanning CTAs, arcs read, decrements issued, the longest scan of one CTA
+// (ns) and the latest round start of a CTA after CTA 0's (ns).
+constexpr int kTraceFields = 12;
 
 int peel_max_ctas_per_sm();
 int peel_block_size();

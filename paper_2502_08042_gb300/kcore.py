@@ -15,7 +15,10 @@ from . import _native
 
 STATUS = {0: "OK", 1: "INVALID", 2: "OOM", 3: "CUDA", 4: "TIMEOUT", 5: "NOT_SIMPLE", 6: "CAPACITY"}
 OPTIONS = {"sync_mode": 0, "ctas_per_sm": 1, "slice_arcs": 2, "local_queue": 3, "timeout_ms": 4,
-           "min_ctas": 5, "vertices_per_cta": 6, "test_stall": 7}
+           "min_ctas": 5, "vertices_per_cta": 6, "test_stall": 7,
+           "trace": 8}
+TRACE_FIELDS = ("t_start", "t_scanned", "t_done", "level", "scanned", "found", "queued", "scan_ctas",
+                "arcs", "decrements", "max_cta_scan_ns", "max_cta_start_delay_ns")
 
 
 class KCoreError(RuntimeError):
@@ -113,6 +116,15 @@ class KCore:
         self._check(self._L.kcore_get_stats(self._h, ctypes.byref(s)))
         return {f: int(getattr(s, f)) for f, _ in _native.Stats._fields_ if f != "reserved"}
 
+    def trace(self) -> np.ndarray:
+        """Per-round timeline of the last decomposition (needs trace=1):
+        structured array with the fields of TRACE_FIELDS."""
+        max_r = max(self.stats()["rounds"], 0)
+        buf = np.zeros((max(max_r, 1), len(TRACE_FIELDS)), np.uint64)
+        got = ctypes.c_int64()
+        self._check(self._L.kcore_get_trace(self._h, buf.ctypes.data, max_r, ctypes.byref(got)))
+        return buf[:got.value]
+
     # ------------------------------------------------------------ compute
     def decompose(self, offsets, adj, coreness=None, kmax=None, stream=None, sync: bool = True):
         """Coreness of every vertex of a simple undirected CSR held on the GPU.
@@ -135,6 +147,29 @@ class KCore:
         if sync:
             self.sync()
         return coreness, kmax
+
+    def build_csr(self, n: int, src, dst, stream=None, sync: bool = True):
+        """Simple undirected CSR of a device edge list (int32 tensors).
+        Returns (offsets int64 [n+1], adj int32 [m]) CUDA tensors; with
+        sync=False returns (offsets, adj_buffer [2E], m_tensor) without waiting."""
+        torch = _torch()
+        E = src.numel()
+        assert dst.numel() == E and src.dtype == torch.int32 and dst.dtype == torch.int32
+        dev = src.device
+        off = torch.empty(n + 1, dtype=torch.int64, device=dev)
+        adj = torch.empty(max(2 * E, 1), dtype=torch.int32, device=dev)
+        m = torch.zeros(1, dtype=torch.int64, device=dev)
+        self._check(self._L.kcore_build_csr(self._h, n, E, _ptr(src), _ptr(dst), _ptr(off), _ptr(adj),
+                                            _ptr(m), _stream_ptr(stream)))
+        if not sync:
+            return off, adj, m
+        self.sync()
+        return off, adj[: int(m.item())]
+
+    def build_csr_workspace_size(self, n: int, E: int) -> int:
+        b = ctypes.c_size_t()
+        self._check(self._L.kcore_build_csr_workspace_size(self._h, n, E, ctypes.byref(b)))
+        return int(b.value)
 
     def decompose_host(self, offsets: np.ndarray, adj: np.ndarray, stream=None):
         """End-to-end call on host arrays: H2D copies, peel, D2H copies, wait.

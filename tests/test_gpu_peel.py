@@ -88,11 +88,12 @@ def test_union_of_shapes(kc):
 
 
 @pytest.mark.parametrize("opts", [
-    dict(slice_arcs=32), dict(slice_arcs=4096), dict(local_queue=0), dict(local_queue=128),
+    dict(slice_arcs=16), dict(slice_arcs=128), dict(slice_arcs=4096), dict(local_queue=0),
+    dict(local_queue=128),
     dict(ctas_per_sm=1), dict(min_ctas=1, vertices_per_cta=1 << 40), dict(vertices_per_cta=1),
 ])
 def test_tuning_modes(opts):
-    n, s, d = gg.disjoint_union(gg.rmat_n(30000, 300000, seed=5), gg.staircase(120),
+    n, s, d = gg.disjoint_union((30000, *gg.rmat_n(30000, 300000, seed=5)), gg.staircase(120),
                                 gg.path(2000), gg.star(3000))
     off, adj = _csr(n, s, d)
     want = oracle.bz(n, off, adj)
@@ -126,15 +127,17 @@ def test_staircase_many_levels(kc):
 def test_each_vertex_processed_once(kc):
     """Every vertex with arcs is processed exactly once (Theorem 1's proof):
     as global slices or from a warp-local queue."""
-    n, s, d = gg.rmat_n(50000, 400000, seed=9)
+    n = 50000
+    s, d = gg.rmat_n(n, 400000, seed=9)
     off, adj = _csr(n, s, d)
     assert_parity(kc, n, off, adj)
     st = kc.stats()
     deg = np.diff(off)
-    slices = int(np.sum((deg + 255) // 256))
-    local = st["local_items"]
-    # local items are one-slice vertices taken out of the global stream
-    assert st["items"] + local == slices
+    sl = kc.get_option("slice_arcs")
+    slices = int(np.sum((deg + sl - 1) // sl))
+    # each vertex with arcs is taken once as a whole item (from the global or a
+    # warp-local queue) and its list is split into ceil(deg / slice) slices
+    assert st["items"] + st["local_items"] == slices
 
 
 def test_host_entry_point(kc):
@@ -147,7 +150,8 @@ def test_host_entry_point(kc):
 
 
 def test_caller_workspace(kc):
-    n, s, d = gg.rmat_n(20000, 100000, seed=3)
+    n = 20000
+    s, d = gg.rmat_n(n, 100000, seed=3)
     off, adj = _csr(n, s, d)
     with KCore(0) as k:
         ws = torch.empty(k.workspace_size(n, len(adj)), dtype=torch.uint8, device="cuda:0")
@@ -165,7 +169,8 @@ def test_timeout_is_reported_and_context_survives():
     """A wait that can never be satisfied (CTA 0 withholds its completion
     token) must end at the time limit with KCORE_ERR_TIMEOUT, and the same
     context must then decompose normally."""
-    n, s, d = gg.rmat_n(5000, 40000, seed=1)
+    n = 5000
+    s, d = gg.rmat_n(n, 40000, seed=1)
     off, adj = _csr(n, s, d)
     o, a = to_dev(off, adj)
     with KCore(0, timeout_ms=200, test_stall=1) as k:
