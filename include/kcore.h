@@ -66,7 +66,9 @@ typedef enum {
   KCORE_OPT_TEST_STALL = 7,      /* test hook, default 0: 1 makes CTA 0 withhold its round-1
                                     completion token, so every device wait must run out its
                                     time limit and the call ends with KCORE_ERR_TIMEOUT */
-  KCORE_OPT_TRACE = 8            /* 1 records a per-round timeline (kcore_get_trace) */
+  KCORE_OPT_TRACE = 8,           /* 1 records a per-round timeline (kcore_get_trace) */
+  KCORE_OPT_IDLE_SLEEP_NS = 9,   /* nanosleep of a warp waiting for work (0 .. 100000) */
+  KCORE_OPT_POLL_SLEEP_NS = 10   /* nanosleep of a CTA's round-end poller (0 .. 100000) */
 } kcore_option;
 
 /* Counters of the last decomposition (valid after kcore_sync_status). */
@@ -160,12 +162,13 @@ kcore_status kcore_sync_status(kcore_handle h);
 kcore_status kcore_get_stats(kcore_handle h, kcore_stats* out);
 
 /* Per-round timeline of the last decomposition when KCORE_OPT_TRACE was 1
- * (call after kcore_sync_status). out receives 12 uint64 per round:
+ * (call after kcore_sync_status). out receives 14 uint64 per round:
  * [0] device time (ns) the round started, [1] when its scan finished,
  * [2] when the round finished, [3] its level k, [4] active-list entries
  * scanned, [5] frontier vertices found by the scan, [6] work items queued,
  * [7] CTAs that scanned, [8] arcs read, [9] decrements issued, [10] longest
- * scan of one CTA (ns), [11] latest round start of a CTA after CTA 0 (ns).
+ * scan of one CTA (ns), [11] latest round start of a CTA after CTA 0 (ns),
+ * [12] summed time warps spent in work batches (ns), [13] work batches.
  * Tracing adds atomics and slows the run. At most max_rounds rounds are
  * copied; *rounds_out receives the number copied. */
 kcore_status kcore_get_trace(kcore_handle h, uint64_t* out, int64_t max_rounds, int64_t* rounds_out);

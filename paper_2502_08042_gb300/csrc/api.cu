@@ -20,7 +20,7 @@ struct kcore_ctx {
   size_t ws_bytes = 0;
   bool ws_external = false;
   std::string err;
-  int64_t opt[9] = {0, 0, 512, 32, 2000, 1, 2048, 0, 0};  // indexed by kcore_option
+  int64_t opt[11] = {0, 0, 512, 32, 2000, 1, 2048, 0, 0, 192, 64};  // indexed by kcore_option
   cudaStream_t last_stream = nullptr;
   bool pending = false;
   kc::PeelCtl* last_ctl = nullptr;
@@ -173,8 +173,12 @@ kcore_status kcore_destroy(kcore_handle h) {
 const char* kcore_last_error(kcore_handle h) { return h ? h->err.c_str() : "null handle"; }
 
 kcore_status kcore_set_option(kcore_handle h, kcore_option opt, int64_t value) {
-  if (!h || (int)opt < 0 || (int)opt > 8) return KCORE_ERR_INVALID;
+  if (!h || (int)opt < 0 || (int)opt > 10) return KCORE_ERR_INVALID;
   switch (opt) {
+    case KCORE_OPT_IDLE_SLEEP_NS:
+    case KCORE_OPT_POLL_SLEEP_NS:
+      if (value < 0 || value > 100000) return fail(h, KCORE_ERR_INVALID, "sleep must be in [0, 100000] ns");
+      break;
     case KCORE_OPT_TRACE:
       if (value < 0 || value > 1) return fail(h, KCORE_ERR_INVALID, "trace must be 0 or 1");
       break;
@@ -211,7 +215,7 @@ kcore_status kcore_set_option(kcore_handle h, kcore_option opt, int64_t value) {
 }
 
 kcore_status kcore_get_option(kcore_handle h, kcore_option opt, int64_t* value) {
-  if (!h || !value || (int)opt < 0 || (int)opt > 8) return KCORE_ERR_INVALID;
+  if (!h || !value || (int)opt < 0 || (int)opt > 10) return KCORE_ERR_INVALID;
   *value = h->opt[opt];
   return KCORE_OK;
 }
@@ -284,6 +288,8 @@ kcore_status kcore_decompose(kcore_handle h, int64_t n, int64_t m, const int64_t
   a.max_take = 256;
   a.timeout_ns = (unsigned long long)h->opt[KCORE_OPT_TIMEOUT_MS] * 1000000ull;
   a.scan_min = 2048;
+  a.idle_sleep_ns = (int)h->opt[KCORE_OPT_IDLE_SLEEP_NS];
+  a.poll_sleep_ns = (int)h->opt[KCORE_OPT_POLL_SLEEP_NS];
   a.inject_stall = (int)h->opt[KCORE_OPT_TEST_STALL];
   a.trace = h->opt[KCORE_OPT_TRACE] ? (unsigned long long*)(ws + L.trace) : nullptr;
 

@@ -70,6 +70,8 @@ struct PeelArgs {
   int take_div;
   int scan_min;  // active-list entries per scanning CTA (at least)
   unsigned long long timeout_ns;
+  int idle_sleep_ns;  // sleep of a waiting warp between looks at its ticket slots
+  int poll_sleep_ns;  // sleep of the CTA's round poller between polls
   int inject_stall;
   unsigned long long* trace;  // optional: kTraceFields words per round (nullptr = off)
 };
@@ -78,8 +80,9 @@ struct PeelArgs {
 // when the last scan token arrived, when the round finished; the level, the
 // active-list length scanned, frontier vertices found, items queued, the
 // scanning CTAs, arcs read, decrements issued, the longest scan of one CTA
-// (ns) and the latest round start of a CTA after CTA 0's (ns).
-constexpr int kTraceFields = 12;
+// (ns), the latest round start of a CTA after CTA 0's (ns), the summed time
+// warps spent in work batches (ns) and the number of batches.
+constexpr int kTraceFields = 14;
 
 int peel_max_ctas_per_sm();
 int peel_block_size();

@@ -174,9 +174,9 @@ __device__ __forceinline__ void push_vertices(const PeelArgs& a, PeelShared& sh,
 // list is longer than one slice first queues its other slices. Then every arc
 // v->u of the items' slices decrements d~[u] when u is still above level t;
 // the decrement returning t+1 lands u on t, claims it for level t and pushes it.
-__device__ __forceinline__ void process_batch(const PeelArgs& a, PeelShared& sh,
-                                              const RoundCtx& rc, unsigned long long item, int c,
-                                              int warp, int lane) {
+__device__ __forceinline__ void process_batch_body(const PeelArgs& a, PeelShared& sh,
+                                                   const RoundCtx& rc, unsigned long long item,
+                                                   int c, int warp, int lane) {
   const int t = rc.t;
   long long a0 = 0, nsplit = 0;
   int len = 0, v = 0;
@@ -258,6 +258,22 @@ __device__ __forceinline__ void process_batch(const PeelArgs& a, PeelShared& sh,
     }
   }
   __syncwarp();
+}
+
+__device__ __forceinline__ void process_batch(const PeelArgs& a, PeelShared& sh,
+                                              const RoundCtx& rc, unsigned long long item, int c,
+                                              int warp, int lane) {
+  if (!a.trace) {
+    process_batch_body(a, sh, rc, item, c, warp, lane);
+    return;
+  }
+  uint64_t t0 = globaltimer_ns();
+  process_batch_body(a, sh, rc, item, c, warp, lane);
+  if (lane == 0) {
+    unsigned long long* tr = a.trace + (size_t)rc.r * kTraceFields;
+    atomicAdd(tr + 12, (unsigned long long)(globaltimer_ns() - t0));
+    atomicAdd(tr + 13, 1ull);
+  }
 }
 
 // Scan of one round: active-list entries [lo, hi) of this CTA. Round 0 reads
@@ -472,9 +488,9 @@ __device__ int process_round(const PeelArgs& a, PeelShared& sh, const RoundCtx& 
       }
       f = __shfl_sync(kFull, f, 0);
       if (f) return f;
-      __nanosleep(64);
+      __nanosleep(a.poll_sleep_ns);
     } else {
-      __nanosleep(192);
+      __nanosleep(a.idle_sleep_ns);
     }
   }
 }
