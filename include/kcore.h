@@ -154,6 +154,33 @@ kcore_status kcore_build_csr(kcore_handle h, int64_t n, int64_t num_edges, const
 /* Workspace bytes kcore_build_csr needs (host call). */
 kcore_status kcore_build_csr_workspace_size(kcore_handle h, int64_t n, int64_t num_edges, size_t* bytes);
 
+/* Largest graph kcore_decompose_static accepts. */
+#define KCORE_STATIC_MAX_VERTICES (1LL << 20)
+#define KCORE_STATIC_MAX_ARCS (1LL << 24)
+
+/* kcore_decompose for callers that cannot allocate device memory. The paper has
+ * no counterpart: this is a deployment variant of the same peel.
+ *
+ * Some callers cannot call cudaMalloc: another allocator may own all of their
+ * device memory, their policy may forbid allocation after start-up, or they
+ * cannot accept the device-wide synchronisation an allocation can cause. This
+ * call allocates nothing (no cudaMalloc, no cudaFree, no allocating library
+ * routine) and needs no handle: its scratch memory is one fixed array in the
+ * library's device memory (about 25 MB), present on every GPU that loads the
+ * library until the process exits. The caller still passes the graph and the
+ * output arrays, exactly as for kcore_decompose (same layout and meaning):
+ *   n <= KCORE_STATIC_MAX_VERTICES, m <= KCORE_STATIC_MAX_ARCS; larger graphs
+ *   are rejected with KCORE_ERR_CAPACITY before any work is queued.
+ * It runs on the calling thread's current device and waits for `stream` before
+ * returning the device status (KCORE_OK, KCORE_ERR_TIMEOUT, ...).
+ * The first call on a device looks up the array's device address (a one-time
+ * set-up per device); make that first call before any stream capture.
+ * Every call uses the same array and leaves its contents behind (each call
+ * clears what must start from zero); calls that overlap on the GPU, from two
+ * threads or two streams, race on it and must not be made. */
+kcore_status kcore_decompose_static(int64_t n, int64_t m, const int64_t* offsets, const int32_t* adj,
+                                    int32_t* coreness_out, int32_t* kmax_out, kcore_stream_t stream);
+
 /* Waits for the stream of the handle's last call and returns the status the
  * device recorded (KCORE_OK, KCORE_ERR_TIMEOUT, ...). */
 kcore_status kcore_sync_status(kcore_handle h);
