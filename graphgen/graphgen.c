@@ -257,14 +257,17 @@ int gg_rmat_n(int64_t n, int64_t m, double a, double b, double c, uint64_t seed,
     return -3;
   }
   uint64_t key = stream_key(seed, 0x726d6174ULL);
-  double ab = a + b, abc = a + b + c;
+  /* quadrant thresholds in 16-bit fixed point: one 64-bit draw serves 4 levels */
+  uint32_t ta = (uint32_t)llround(a * 65536.0), tab = (uint32_t)llround((a + b) * 65536.0),
+           tabc = (uint32_t)llround((a + b + c) * 65536.0);
   uint64_t ctr = 0;
   int64_t got = 0;
   while (got < m) {
-    uint64_t u = 0, v = 0;
+    uint64_t u = 0, v = 0, r = 0;
     for (int l = 0; l < scale; l++) {
-      double x = u01(rng_at(key, ctr++));
-      uint64_t bu = x >= ab, bv = (x >= a && x < ab) || x >= abc;
+      if ((l & 3) == 0) r = rng_at(key, ctr++);
+      uint32_t x = (uint32_t)((r >> (16 * (l & 3))) & 0xffffu);
+      uint64_t bu = x >= tab, bv = (x >= ta && x < tab) || x >= tabc;
       u = (u << 1) | bu;
       v = (v << 1) | bv;
     }

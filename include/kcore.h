@@ -68,7 +68,12 @@ typedef enum {
                                     time limit and the call ends with KCORE_ERR_TIMEOUT */
   KCORE_OPT_TRACE = 8,           /* 1 records a per-round timeline (kcore_get_trace) */
   KCORE_OPT_IDLE_SLEEP_NS = 9,   /* nanosleep of a warp waiting for work (0 .. 100000) */
-  KCORE_OPT_POLL_SLEEP_NS = 10   /* nanosleep of a CTA's round-end poller (0 .. 100000) */
+  KCORE_OPT_POLL_SLEEP_NS = 10,  /* nanosleep of a CTA's round-end poller (0 .. 100000) */
+  KCORE_OPT_BATCH_BLOCK = 11,    /* batched peel: threads per CTA (256, 512 or 1024; default 1024) */
+  KCORE_OPT_BATCH_SMEM_VERTICES = 12, /* batched peel: graphs with at most this many vertices keep
+                                         their induced degrees in shared memory (-1 = as many as
+                                         fit with the CTAs per SM below) */
+  KCORE_OPT_BATCH_CTAS_PER_SM = 13    /* batched peel: resident CTAs per SM (0 = occupancy limit) */
 } kcore_option;
 
 /* Counters of the last decomposition (valid after kcore_sync_status). */
@@ -153,6 +158,55 @@ kcore_status kcore_build_csr(kcore_handle h, int64_t n, int64_t num_edges, const
 
 /* Workspace bytes kcore_build_csr needs (host call). */
 kcore_status kcore_build_csr_workspace_size(kcore_handle h, int64_t n, int64_t num_edges, size_t* bytes);
+
+/* Coreness of many independent graphs in one launch (the batched form of the
+ * same peel; the paper peels one graph at a time). The graphs form a
+ * segmented CSR: graph g owns global vertices [graph_vertex_offsets[g],
+ * graph_vertex_offsets[g+1]), offsets[] is one global int64 offsets array over
+ * all N vertices (offsets[N] = total_arcs), and each adjacency list holds
+ * GRAPH-LOCAL ids (0 .. n_g - 1). Each graph must be a simple undirected graph.
+ *   num_graphs            G (0 <= G <= 2^24)
+ *   total_vertices        N = graph_vertex_offsets[G]
+ *   total_arcs            offsets[N]
+ *   graph_vertex_offsets  device int64[G+1], starts at 0, non-decreasing
+ *   offsets, adj          device int64[N+1], int32[total_arcs]
+ *   coreness_out          device int32[N]: coreness of every vertex in its graph
+ *   kmax_out              device int32[G]: largest coreness of each graph (0 if empty)
+ * Asynchronous; one persistent kernel (each graph peeled by one CTA, induced
+ * degrees in shared memory when the graph fits, largest graphs first). Uses
+ * kcore_batched_workspace_size bytes of workspace (20 bytes per vertex).
+ * Malformed offsets or ids are reported as KCORE_ERR_NOT_SIMPLE by
+ * kcore_sync_status. */
+kcore_status kcore_decompose_batched(kcore_handle h, int64_t num_graphs, int64_t total_vertices,
+                                     int64_t total_arcs, const int64_t* graph_vertex_offsets,
+                                     const int64_t* offsets, const int32_t* adj, int32_t* coreness_out,
+                                     int32_t* kmax_out, kcore_stream_t stream);
+
+/* Segmented CSR of a batch of edge lists (the batched form of
+ * kcore_build_csr): graph g owns vertices [graph_vertex_offsets[g],
+ * graph_vertex_offsets[g+1]) and edges [graph_edge_offsets[g],
+ * graph_edge_offsets[g+1]) of src/dst, whose ids are GRAPH-LOCAL. The output is
+ * the input of kcore_decompose_batched: one global offsets array over all
+ * vertices and graph-local adjacency ids, each graph symmetrised, without
+ * self-loops or repeated arcs, each list ascending.
+ *   num_graphs >= 1; total_vertices = graph_vertex_offsets[G] <= 2^31 - 2
+ *   max_graph_vertices    the largest n_g (host value; sizes the sort keys)
+ *   graph_vertex_offsets, graph_edge_offsets   device int64[G+1]
+ *   src, dst              device int32[num_edges], local ids
+ *   offsets_out           device int64[total_vertices + 1]
+ *   adj_out               device int32 with room for 2 * num_edges
+ *   m_out                 device int64[1]: arcs written
+ * Asynchronous; a local id outside its graph is reported as KCORE_ERR_INVALID
+ * by kcore_sync_status. Workspace as kcore_build_csr. */
+kcore_status kcore_build_csr_batched(kcore_handle h, int64_t num_graphs, int64_t total_vertices,
+                                     int64_t num_edges, int64_t max_graph_vertices,
+                                     const int64_t* graph_vertex_offsets, const int64_t* graph_edge_offsets,
+                                     const int32_t* src, const int32_t* dst, int64_t* offsets_out,
+                                     int32_t* adj_out, int64_t* m_out, kcore_stream_t stream);
+
+/* Workspace bytes kcore_decompose_batched needs (host call). */
+kcore_status kcore_batched_workspace_size(kcore_handle h, int64_t num_graphs, int64_t total_vertices,
+                                          size_t* bytes);
 
 /* Largest graph kcore_decompose_static accepts. */
 #define KCORE_STATIC_MAX_VERTICES (1LL << 20)

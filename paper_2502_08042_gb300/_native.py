@@ -118,6 +118,11 @@ SIGNATURES = {
     "kcore_build_csr": ([c_p, c_i64, c_i64, c_p, c_p, c_p, c_p, c_p, c_p], ctypes.c_int),
     "kcore_build_csr_workspace_size": ([c_p, c_i64, c_i64, ctypes.POINTER(c_sz)], ctypes.c_int),
     "kcore_decompose_static": ([c_i64, c_i64, c_p, c_p, c_p, c_p, c_p], ctypes.c_int),
+    "kcore_decompose_batched": ([c_p, c_i64, c_i64, c_i64, c_p, c_p, c_p, c_p, c_p, c_p],
+                                ctypes.c_int),
+    "kcore_batched_workspace_size": ([c_p, c_i64, c_i64, ctypes.POINTER(c_sz)], ctypes.c_int),
+    "kcore_build_csr_batched": ([c_p, c_i64, c_i64, c_i64, c_i64, c_p, c_p, c_p, c_p, c_p, c_p, c_p,
+                                 c_p], ctypes.c_int),
 }
 
 

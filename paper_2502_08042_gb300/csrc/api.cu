@@ -9,6 +9,7 @@
 #include <string>
 
 #include "kcore.h"
+#include "kcore_batched.h"
 #include "kcore_csr.h"
 #include "kcore_peel.h"
 
@@ -20,11 +21,13 @@ struct kcore_ctx {
   size_t ws_bytes = 0;
   bool ws_external = false;
   std::string err;
-  int64_t opt[11] = {0, 0, 512, 32, 2000, 1, 2048, 0, 0, 192, 64};  // indexed by kcore_option
+  int64_t opt[14] = {0, 0, 512, 32, 2000, 1, 2048, 0, 0, 192, 64, 1024, -1, 0};  // indexed by kcore_option
   cudaStream_t last_stream = nullptr;
   bool pending = false;
   kc::PeelCtl* last_ctl = nullptr;
   int* last_csr_status = nullptr;  // device status word of the last CSR build
+  int* last_batch_status = nullptr;  // device status word of the last batched call
+  int last_batch_block = 0, last_batch_grid = 0, last_batch_smem_vertices = 0;
   unsigned long long* last_trace = nullptr;
   int last_max_rounds = 0;
   kcore_stats stats{};
@@ -173,8 +176,18 @@ kcore_status kcore_destroy(kcore_handle h) {
 const char* kcore_last_error(kcore_handle h) { return h ? h->err.c_str() : "null handle"; }
 
 kcore_status kcore_set_option(kcore_handle h, kcore_option opt, int64_t value) {
-  if (!h || (int)opt < 0 || (int)opt > 10) return KCORE_ERR_INVALID;
+  if (!h || (int)opt < 0 || (int)opt > 13) return KCORE_ERR_INVALID;
   switch (opt) {
+    case KCORE_OPT_BATCH_BLOCK:
+      if (value != 256 && value != 512 && value != 1024)
+        return fail(h, KCORE_ERR_INVALID, "batch block must be 256, 512 or 1024");
+      break;
+    case KCORE_OPT_BATCH_SMEM_VERTICES:
+      if (value < -1 || value > 60000) return fail(h, KCORE_ERR_INVALID, "batch smem vertices in [-1, 60000]");
+      break;
+    case KCORE_OPT_BATCH_CTAS_PER_SM:
+      if (value < 0 || value > 8) return fail(h, KCORE_ERR_INVALID, "batch CTAs per SM in [0, 8]");
+      break;
     case KCORE_OPT_IDLE_SLEEP_NS:
     case KCORE_OPT_POLL_SLEEP_NS:
       if (value < 0 || value > 100000) return fail(h, KCORE_ERR_INVALID, "sleep must be in [0, 100000] ns");
@@ -215,7 +228,7 @@ kcore_status kcore_set_option(kcore_handle h, kcore_option opt, int64_t value) {
 }
 
 kcore_status kcore_get_option(kcore_handle h, kcore_option opt, int64_t* value) {
-  if (!h || !value || (int)opt < 0 || (int)opt > 10) return KCORE_ERR_INVALID;
+  if (!h || !value || (int)opt < 0 || (int)opt > 13) return KCORE_ERR_INVALID;
   *value = h->opt[opt];
   return KCORE_OK;
 }
@@ -337,14 +350,172 @@ kcore_status kcore_build_csr(kcore_handle h, int64_t n, int64_t num_edges, const
   h->err.clear();
   h->last_ctl = nullptr;
   h->last_trace = nullptr;
+  h->last_batch_status = nullptr;
   h->last_stream = stream;
   h->pending = true;
   kc::CsrLayout L = kc::csr_layout(n, num_edges, h->sms);
   kcore_status st = ensure_ws(h, L.total);
   if (st != KCORE_OK) return st;
-  cudaError_t e = kc::csr_build_launch(L, (char*)h->ws, n, num_edges, src, dst, (long long*)offsets_out,
-                                       adj_out, (long long*)m_out, stream);
+  cudaError_t e = kc::csr_build_launch(L, (char*)h->ws, n, num_edges, src, dst, nullptr, nullptr, 0,
+                                       (long long*)offsets_out, adj_out, (long long*)m_out, stream);
   if (e != cudaSuccess) return cuda_fail(h, e, "CSR build launch");
+  h->last_csr_status = (int*)((char*)h->ws + L.status);
+  return KCORE_OK;
+}
+
+namespace {
+struct BatchLayout {
+  size_t ctl, order, deg, a0, a1, f0, f1, total;
+};
+BatchLayout batch_layout(int64_t G, int64_t N) {
+  BatchLayout L{};
+  size_t off = 0;
+  L.ctl = off;
+  off = align_up(off + 256, 256);
+  L.order = off;
+  off = align_up(off + 4 * (size_t)std::max<int64_t>(G, 1), 256);
+  L.deg = off;
+  off = align_up(off + 4 * (size_t)N, 256);
+  L.a0 = off;
+  off = align_up(off + 4 * (size_t)N, 256);
+  L.a1 = off;
+  off = align_up(off + 4 * (size_t)N, 256);
+  L.f0 = off;
+  off = align_up(off + 4 * (size_t)N, 256);
+  L.f1 = off;
+  off = align_up(off + 4 * (size_t)N, 256);
+  L.total = off;
+  return L;
+}
+
+// Batched launch shape from the handle's options: block size, vertices kept in
+// shared memory, CTAs per SM.
+void batch_shape(kcore_ctx* h, int* block, int* smem_vertices, int* grid, size_t* smem) {
+  int b = (int)h->opt[KCORE_OPT_BATCH_BLOCK];
+  int sv = (int)h->opt[KCORE_OPT_BATCH_SMEM_VERTICES];
+  int cps = (int)h->opt[KCORE_OPT_BATCH_CTAS_PER_SM];
+  int dev_smem = 0;
+  cudaDeviceGetAttribute(&dev_smem, cudaDevAttrMaxSharedMemoryPerBlockOptin, h->device);
+  int sm_total = 0;
+  cudaDeviceGetAttribute(&sm_total, cudaDevAttrMaxSharedMemoryPerMultiprocessor, h->device);
+  size_t stat = kc::batch_static_smem(b);
+  if (sv < 0) {
+    // default: two CTAs per SM share the SM's shared memory
+    int want = cps > 0 ? cps : 2;
+    long long per = (long long)sm_total / want - (long long)stat - 2048;
+    per = std::min<long long>(per, (long long)dev_smem - (long long)stat - 1024);
+    sv = (int)std::max<long long>(0, per / 4);
+  }
+  size_t sm = (size_t)sv * 4;
+  if (sm + stat > (size_t)dev_smem) {
+    sv = (int)(((size_t)dev_smem - stat - 1024) / 4);
+    sm = (size_t)sv * 4;
+  }
+  int occ = kc::batch_occupancy(b, sm);
+  if (occ < 1) occ = 1;
+  if (cps > 0) occ = std::min(occ, cps);
+  *block = b;
+  *smem_vertices = sv;
+  *grid = h->sms * occ;
+  *smem = sm;
+}
+}  // namespace
+
+kcore_status kcore_batched_workspace_size(kcore_handle h, int64_t num_graphs, int64_t total_vertices,
+                                          size_t* bytes) {
+  if (!h || !bytes || num_graphs < 0 || total_vertices < 0) return KCORE_ERR_INVALID;
+  *bytes = batch_layout(num_graphs, total_vertices).total;
+  return KCORE_OK;
+}
+
+kcore_status kcore_decompose_batched(kcore_handle h, int64_t num_graphs, int64_t total_vertices,
+                                     int64_t total_arcs, const int64_t* graph_vertex_offsets,
+                                     const int64_t* offsets, const int32_t* adj, int32_t* coreness_out,
+                                     int32_t* kmax_out, kcore_stream_t stream_) {
+  if (!h) return KCORE_ERR_INVALID;
+  cudaStream_t stream = (cudaStream_t)stream_;
+  if (num_graphs < 0 || total_vertices < 0 || total_arcs < 0 || num_graphs > ((int64_t)1 << 24))
+    return fail(h, KCORE_ERR_INVALID, "batch sizes out of range");
+  if (num_graphs > 0 && (!graph_vertex_offsets || !kmax_out))
+    return fail(h, KCORE_ERR_INVALID, "null graph offsets / kmax");
+  if (total_vertices > 0 && (!offsets || !coreness_out)) return fail(h, KCORE_ERR_INVALID, "null offsets / coreness");
+  if (total_arcs > 0 && !adj) return fail(h, KCORE_ERR_INVALID, "null adj");
+  DeviceGuard g(h->device);
+  if (!g.ok) return fail(h, KCORE_ERR_CUDA, "cudaSetDevice failed");
+  h->err.clear();
+  h->stats = kcore_stats{};
+  h->last_ctl = nullptr;
+  h->last_trace = nullptr;
+  h->last_csr_status = nullptr;
+  h->last_batch_status = nullptr;
+  h->last_stream = stream;
+  h->pending = true;
+  if (num_graphs == 0) return KCORE_OK;
+  BatchLayout L = batch_layout(num_graphs, total_vertices);
+  kcore_status st = ensure_ws(h, L.total);
+  if (st != KCORE_OK) return st;
+  char* ws = (char*)h->ws;
+  int block, sv, grid;
+  size_t smem;
+  batch_shape(h, &block, &sv, &grid, &smem);
+  kc::BatchArgs a{};
+  a.G = num_graphs;
+  a.m = total_arcs;
+  a.gv = (const long long*)graph_vertex_offsets;
+  a.off = (const long long*)offsets;
+  a.adj = adj;
+  a.core = coreness_out;
+  a.kmax = kmax_out;
+  a.deg = (int*)(ws + L.deg);
+  a.A0 = (int*)(ws + L.a0);
+  a.A1 = (int*)(ws + L.a1);
+  a.F0 = (int*)(ws + L.f0);
+  a.F1 = (int*)(ws + L.f1);
+  bool sort_graphs = num_graphs <= kc::kMaxSortGraphs && num_graphs > 1;
+  a.order = sort_graphs ? (const int*)(ws + L.order) : nullptr;
+  a.next_graph = (int*)(ws + L.ctl);
+  a.status = (int*)(ws + L.ctl) + 32;
+  a.smem_deg_max = sv;
+  cudaError_t e;
+  if ((e = cudaMemsetAsync(ws + L.ctl, 0, 256, stream)) != cudaSuccess) return cuda_fail(h, e, "memset");
+  if ((e = kc::batch_launch(a, block, grid, smem, sort_graphs, stream)) != cudaSuccess)
+    return cuda_fail(h, e, "batched launch");
+  h->last_batch_status = a.status;
+  h->last_batch_block = block;
+  h->last_batch_grid = grid;
+  h->last_batch_smem_vertices = sv;
+  return KCORE_OK;
+}
+
+kcore_status kcore_build_csr_batched(kcore_handle h, int64_t num_graphs, int64_t total_vertices,
+                                     int64_t num_edges, int64_t max_graph_vertices,
+                                     const int64_t* graph_vertex_offsets, const int64_t* graph_edge_offsets,
+                                     const int32_t* src, const int32_t* dst, int64_t* offsets_out,
+                                     int32_t* adj_out, int64_t* m_out, kcore_stream_t stream_) {
+  if (!h) return KCORE_ERR_INVALID;
+  cudaStream_t stream = (cudaStream_t)stream_;
+  if (num_graphs < 1 || total_vertices < 0 || total_vertices > INT32_MAX - 1 || num_edges < 0 ||
+      num_edges > ((int64_t)1 << 40) || max_graph_vertices < 1 || max_graph_vertices > total_vertices + 1)
+    return fail(h, KCORE_ERR_INVALID, "batch CSR sizes out of range");
+  if (!graph_vertex_offsets || !graph_edge_offsets || !offsets_out || !m_out)
+    return fail(h, KCORE_ERR_INVALID, "null pointer");
+  if (num_edges > 0 && (!src || !dst || !adj_out)) return fail(h, KCORE_ERR_INVALID, "null edge or adj pointer");
+  DeviceGuard g(h->device);
+  if (!g.ok) return fail(h, KCORE_ERR_CUDA, "cudaSetDevice failed");
+  h->err.clear();
+  h->last_ctl = nullptr;
+  h->last_trace = nullptr;
+  h->last_batch_status = nullptr;
+  h->last_stream = stream;
+  h->pending = true;
+  kc::CsrLayout L = kc::csr_layout(total_vertices, num_edges, h->sms, max_graph_vertices);
+  kcore_status st = ensure_ws(h, L.total);
+  if (st != KCORE_OK) return st;
+  cudaError_t e = kc::csr_build_launch(L, (char*)h->ws, total_vertices, num_edges, src, dst,
+                                       (const long long*)graph_vertex_offsets,
+                                       (const long long*)graph_edge_offsets, num_graphs,
+                                       (long long*)offsets_out, adj_out, (long long*)m_out, stream);
+  if (e != cudaSuccess) return cuda_fail(h, e, "batched CSR build launch");
   h->last_csr_status = (int*)((char*)h->ws + L.status);
   return KCORE_OK;
 }
@@ -356,6 +527,19 @@ kcore_status kcore_sync_status(kcore_handle h) {
   cudaError_t e = cudaStreamSynchronize(h->last_stream);
   h->pending = false;
   if (e != cudaSuccess) return cuda_fail(h, e, "stream synchronize");
+  if (h->last_batch_status) {
+    int bs = 0;
+    e = cudaMemcpy(&bs, h->last_batch_status, sizeof(int), cudaMemcpyDeviceToHost);
+    h->last_batch_status = nullptr;
+    if (e != cudaSuccess) return cuda_fail(h, e, "read status");
+    h->stats.grid = h->last_batch_grid;
+    h->stats.reserved[0] = h->last_batch_block;
+    h->stats.reserved[1] = h->last_batch_smem_vertices;
+    if (bs == kc::ST_NOT_SIMPLE)
+      return fail(h, KCORE_ERR_NOT_SIMPLE, "malformed segmented CSR detected on the device");
+    if (bs != 0) return fail(h, KCORE_ERR_CUDA, "unknown device status " + std::to_string(bs));
+    return KCORE_OK;
+  }
   if (h->last_csr_status) {
     int cs = 0;
     e = cudaMemcpy(&cs, h->last_csr_status, sizeof(int), cudaMemcpyDeviceToHost);

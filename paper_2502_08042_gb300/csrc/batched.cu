@@ -1,0 +1,380 @@
+// Batched k-core peel for sm_103a: thousands of independent graphs, one launch.
+//
+// Input is a segmented CSR: graph g owns vertices [gv[g], gv[g+1]) of one
+// global offsets array, and its adjacency lists hold graph-local ids. Each
+// graph is peeled by one CTA with Algorithm 1's round structure and the
+// online Peel of Algorithm 3, entirely inside the CTA:
+//   * levels: the next level is the minimum induced degree of the live
+//     vertices (found while the active list is compacted, so empty levels are
+//     never visited); the frontier is the live vertices sitting at that level;
+//   * subrounds: the arcs of the current frontier are processed edge-balanced
+//     by all threads of the CTA (a block scan of the frontier's degrees, then
+//     each thread takes arcs of the concatenated lists); a decrement that
+//     returns k+1 lands its vertex on k and appends it to the next subround's
+//     frontier; __syncthreads separates subrounds and levels;
+//   * the induced degrees live in shared memory when the graph is small enough
+//     (shared-memory atomics), otherwise in a per-graph slice of the workspace.
+// Persistent CTAs take graphs from a device counter in descending order of
+// arcs (longest-processing-time first), so the largest graphs start first.
+// Nothing waits on another CTA: the kernel has no spin-waits.
+#include <climits>
+
+#include "kcore_batched.h"
+#include "kcore_device.cuh"
+
+namespace kc {
+
+constexpr int kBatchIlp = 4;
+constexpr int kScanItems = 8;  // active-list entries per thread per scan tile
+
+template <int BLOCK>
+struct BatchShared {
+  int pre[BLOCK];
+  long long start[BLOCK];
+  int part[BLOCK / 32];
+  int red[BLOCK / 32];
+  int cnt;
+  int g;
+  int total;
+};
+
+// Block-wide exclusive scan of one int per thread; returns the exclusive value,
+// *total gets the sum. Contains two __syncthreads.
+template <int BLOCK>
+__device__ __forceinline__ int block_excl_scan(int x, BatchShared<BLOCK>& sh, int* total) {
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  int incl = warp_incl_scan(x, lane);
+  if (lane == 31) sh.part[warp] = incl;
+  __syncthreads();
+  if (warp == 0) {
+    int p = lane < BLOCK / 32 ? sh.part[lane] : 0;
+    int pi = warp_incl_scan(p, lane);
+    if (lane < BLOCK / 32) sh.part[lane] = pi - p;
+    if (lane == BLOCK / 32 - 1) sh.total = pi;
+  }
+  __syncthreads();
+  *total = sh.total;
+  return sh.part[warp] + incl - x;
+}
+
+template <int BLOCK>
+__device__ __forceinline__ int block_min(int x, BatchShared<BLOCK>& sh) {
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  x = warp_min(x);
+  if (lane == 0) sh.red[warp] = x;
+  __syncthreads();
+  int m = INT_MAX;
+  for (int w = 0; w < BLOCK / 32; w++) m = min(m, sh.red[w]);
+  __syncthreads();
+  return m;
+}
+
+// d~ read: shared memory, or L2 (atomics are performed in L2, so a global
+// d~ must not be read through L1).
+__device__ __forceinline__ int load_deg(const int* D, int v, bool in_smem) {
+  return in_smem ? D[v] : __ldcg(D + v);
+}
+
+// One pass over the active list after level k: entries with D > k survive
+// into `out` (their minimum goes to *dmin); among them, those at exactly k+1
+// are also written to F (the next frontier if level k+1 is not empty).
+// Returns the survivors; *nf gets the number written to F.
+template <int BLOCK>
+__device__ int compact_active(const int* A, int la, int* out, int* F, const int* D, bool in_smem,
+                              int k, BatchShared<BLOCK>& sh, int* dmin, int* nf) {
+  int written = 0, wf = 0, lmin = INT_MAX;
+  for (int base = 0; base < la; base += BLOCK * kScanItems) {
+    int v[kScanItems];
+    unsigned keep = 0, front = 0;
+#pragma unroll
+    for (int q = 0; q < kScanItems; q++) {
+      int i = base + q * BLOCK + threadIdx.x;
+      v[q] = -1;
+      if (i < la) v[q] = A[i];
+    }
+#pragma unroll
+    for (int q = 0; q < kScanItems; q++) {
+      if (v[q] >= 0) {
+        int d = load_deg(D, v[q], in_smem);
+        if (d > k) {
+          keep |= 1u << q;
+          lmin = min(lmin, d);
+          if (d == k + 1) front |= 1u << q;
+        }
+      }
+    }
+    int tot;
+    int packed = __popc(keep) | (__popc(front) << 16);
+    int pos = block_excl_scan(packed, sh, &tot);
+    int pk = written + (pos & 0xffff), pf = wf + (pos >> 16);
+#pragma unroll
+    for (int q = 0; q < kScanItems; q++) {
+      if ((keep >> q) & 1u) out[pk++] = v[q];
+      if ((front >> q) & 1u) F[pf++] = v[q];
+    }
+    written += tot & 0xffff;
+    wf += tot >> 16;
+  }
+  *dmin = block_min(lmin, sh);
+  *nf = wf;
+  return written;
+}
+
+// Selection of the frontier: entries of A with D[v] == k.
+template <int BLOCK>
+__device__ int select_frontier(const int* A, int la, int* F, const int* D, bool in_smem, int k,
+                               BatchShared<BLOCK>& sh) {
+  int written = 0;
+  for (int base = 0; base < la; base += BLOCK * kScanItems) {
+    int v[kScanItems];
+    unsigned take = 0;
+#pragma unroll
+    for (int q = 0; q < kScanItems; q++) {
+      int i = base + q * BLOCK + threadIdx.x;
+      v[q] = -1;
+      if (i < la) v[q] = A[i];
+    }
+#pragma unroll
+    for (int q = 0; q < kScanItems; q++)
+      if (v[q] >= 0 && load_deg(D, v[q], in_smem) == k) take |= 1u << q;
+    int tot;
+    int pos = block_excl_scan(__popc(take), sh, &tot);
+    int p = written + pos;
+#pragma unroll
+    for (int q = 0; q < kScanItems; q++)
+      if ((take >> q) & 1u) F[p++] = v[q];
+    written += tot;
+  }
+  return written;
+}
+
+template <int BLOCK>
+__device__ void peel_one_graph(const BatchArgs& a, long long g, int* sdeg, BatchShared<BLOCK>& sh) {
+  const int tid = threadIdx.x, lane = tid & 31;
+  const long long v0 = a.gv[g];
+  const long long nl = a.gv[g + 1] - v0;
+  if (nl <= 0) {
+    if (tid == 0) a.kmax[g] = 0;
+    return;
+  }
+  const int n = (int)nl;
+  const bool in_smem = n <= a.smem_deg_max;
+  int* D = in_smem ? sdeg : a.deg + v0;
+  const long long* O = a.off + v0;
+  int* core = a.core + v0;
+  int* A0 = a.A0 + v0;
+  int* A1 = a.A1 + v0;
+  int* F0 = a.F0 + v0;
+  int* F1 = a.F1 + v0;
+
+  // degrees, identity active list, minimum degree
+  int lmin = INT_MAX;
+  for (int v = tid; v < n; v += BLOCK) {
+    long long o0 = O[v], o1 = O[v + 1];
+    if (o0 < 0 || o1 < o0 || o1 > a.m || o1 - o0 >= n) {
+      atomicCAS(a.status, 0, ST_NOT_SIMPLE);
+      o1 = o0;
+    }
+    int d = (int)(o1 - o0);
+    D[v] = d;
+    A0[v] = v;
+    lmin = min(lmin, d);
+  }
+  int k = block_min(lmin, sh);  // also orders the writes above
+  int* A = A0;
+  int* An = A1;
+  int la = n;
+  int kmax = 0;
+  int nf = select_frontier<BLOCK>(A, la, F0, D, in_smem, k, sh);
+  for (;;) {
+    int* Fc = F0;
+    int* Fn = F1;
+    while (nf > 0) {
+      for (int i = tid; i < nf; i += BLOCK) core[Fc[i]] = k;
+      if (tid == 0) sh.cnt = 0;
+      __syncthreads();
+      for (int c0 = 0; c0 < nf; c0 += BLOCK) {
+        const int cnum = min(BLOCK, nf - c0);
+        int len = 0;
+        long long st = 0;
+        if (tid < cnum) {
+          int v = Fc[c0 + tid];
+          st = O[v];
+          len = (int)(O[v + 1] - st);
+        }
+        int total;
+        int ex = block_excl_scan(len, sh, &total);
+        sh.pre[tid] = ex;
+        sh.start[tid] = st;
+        __syncthreads();
+        for (int j0 = 0; j0 < total; j0 += BLOCK * kBatchIlp) {
+          int u[kBatchIlp];
+#pragma unroll
+          for (int q = 0; q < kBatchIlp; q++) {
+            int j = j0 + q * BLOCK + tid;
+            u[q] = -1;
+            if (j < total) {
+              int lo = 0, hi = cnum;
+              while (lo < hi) {
+                int mid = (lo + hi) >> 1;
+                if (sh.pre[mid] <= j) lo = mid + 1;
+                else hi = mid;
+              }
+              int idx = lo - 1;
+              u[q] = ld_stream_s32(a.adj + sh.start[idx] + (j - sh.pre[idx]));
+              if ((unsigned)u[q] >= (unsigned)n) {
+                atomicCAS(a.status, 0, ST_NOT_SIMPLE);
+                u[q] = -1;
+              }
+            }
+          }
+#pragma unroll
+          for (int q = 0; q < kBatchIlp; q++) {
+            bool cross = false;
+            if (u[q] >= 0 && load_deg(D, u[q], in_smem) > k) cross = atomicSub(&D[u[q]], 1) == k + 1;
+            unsigned m = __ballot_sync(kFull, cross);
+            if (m) {
+              int base = 0;
+              if (lane == __ffs(m) - 1) base = atomicAdd(&sh.cnt, __popc(m));
+              base = __shfl_sync(kFull, base, __ffs(m) - 1);
+              if (cross) Fn[base + __popc(m & lanemask_lt())] = u[q];
+            }
+          }
+        }
+        __syncthreads();
+      }
+      nf = sh.cnt;
+      __syncthreads();
+      int* t = Fc;
+      Fc = Fn;
+      Fn = t;
+    }
+    kmax = k;
+    // drop the vertices peeled at level k; the minimum induced degree of the
+    // rest is the next non-empty level; vertices at k+1 are collected on the
+    // way in case that level is the next one
+    int dmin;
+    la = compact_active<BLOCK>(A, la, An, F0, D, in_smem, k, sh, &dmin, &nf);
+    int* t = A;
+    A = An;
+    An = t;
+    if (la == 0) break;
+    if (dmin != k + 1) nf = select_frontier<BLOCK>(A, la, F0, D, in_smem, dmin, sh);
+    k = dmin;
+  }
+  if (tid == 0) a.kmax[g] = kmax;
+  __syncthreads();
+}
+
+template <int BLOCK>
+__global__ void __launch_bounds__(BLOCK, (BLOCK >= 1024 ? 1 : 2048 / BLOCK / 2)) batch_peel(BatchArgs a) {
+  extern __shared__ int sdeg[];
+  __shared__ BatchShared<BLOCK> sh;
+  for (;;) {
+    if (threadIdx.x == 0) sh.g = atomicAdd(a.next_graph, 1);
+    __syncthreads();
+    long long gi = sh.g;
+    __syncthreads();
+    if (gi >= a.G) break;
+    long long g = a.order ? a.order[gi] : gi;
+    peel_one_graph<BLOCK>(a, g, sdeg, sh);
+  }
+}
+
+// Order of graphs: descending number of arcs (ties by index). One CTA sorts
+// keys (~arcs << 24 | g) bitonically in shared memory; batches larger than
+// kMaxSortGraphs keep their given order.
+__global__ void __launch_bounds__(1024) batch_order(const long long* gv, const long long* off,
+                                                    long long G, int* order) {
+  extern __shared__ unsigned long long key[];
+  int P = 1;
+  while (P < G) P <<= 1;
+  for (int i = threadIdx.x; i < P; i += blockDim.x) {
+    if (i < G) {
+      unsigned long long arcs = (unsigned long long)(off[gv[i + 1]] - off[gv[i]]);
+      if (arcs > 0xffffffffffull) arcs = 0xffffffffffull;
+      key[i] = ((0xffffffffffull - arcs) << 24) | (unsigned long long)i;
+    } else {
+      key[i] = ~0ull;
+    }
+  }
+  __syncthreads();
+  for (int size = 2; size <= P; size <<= 1) {
+    for (int stride = size >> 1; stride > 0; stride >>= 1) {
+      for (int i = threadIdx.x; i < P; i += blockDim.x) {
+        int j = i ^ stride;
+        if (j > i) {
+          bool up = (i & size) == 0;
+          unsigned long long x = key[i], y = key[j];
+          if ((x > y) == up) {
+            key[i] = y;
+            key[j] = x;
+          }
+        }
+      }
+      __syncthreads();
+    }
+  }
+  for (int i = threadIdx.x; i < G; i += blockDim.x) order[i] = (int)(key[i] & 0xffffffull);
+}
+
+// ------------------------------------------------------------------ host side
+namespace {
+template <int BLOCK>
+cudaError_t launch_block(const BatchArgs& a, int grid, size_t smem, cudaStream_t stream) {
+  cudaError_t e = cudaFuncSetAttribute(batch_peel<BLOCK>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       (int)smem);
+  if (e != cudaSuccess) return e;
+  batch_peel<BLOCK><<<grid, BLOCK, smem, stream>>>(a);
+  return cudaGetLastError();
+}
+template <int BLOCK>
+int occupancy_block(size_t smem) {
+  int nb = 0;
+  cudaFuncSetAttribute(batch_peel<BLOCK>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, batch_peel<BLOCK>, BLOCK, smem) != cudaSuccess) {
+    cudaGetLastError();
+    return 0;
+  }
+  return nb;
+}
+}  // namespace
+
+int batch_occupancy(int block, size_t smem) {
+  switch (block) {
+    case 256: return occupancy_block<256>(smem);
+    case 512: return occupancy_block<512>(smem);
+    case 1024: return occupancy_block<1024>(smem);
+  }
+  return 0;
+}
+
+size_t batch_static_smem(int block) {
+  switch (block) {
+    case 256: return sizeof(BatchShared<256>);
+    case 512: return sizeof(BatchShared<512>);
+    case 1024: return sizeof(BatchShared<1024>);
+  }
+  return 0;
+}
+
+cudaError_t batch_launch(const BatchArgs& a, int block, int grid, size_t smem, bool sort_graphs,
+                         cudaStream_t stream) {
+  if (sort_graphs && a.order) {
+    int P = 1;
+    while (P < a.G) P <<= 1;
+    size_t ss = sizeof(unsigned long long) * (size_t)P;
+    cudaError_t e = cudaFuncSetAttribute(batch_order, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)ss);
+    if (e != cudaSuccess) return e;
+    batch_order<<<1, 1024, ss, stream>>>(a.gv, a.off, a.G, (int*)a.order);
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+  }
+  switch (block) {
+    case 256: return launch_block<256>(a, grid, smem, stream);
+    case 512: return launch_block<512>(a, grid, smem, stream);
+    case 1024: return launch_block<1024>(a, grid, smem, stream);
+  }
+  return cudaErrorInvalidValue;
+}
+
+}  // namespace kc

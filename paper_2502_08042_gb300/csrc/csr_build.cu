@@ -29,18 +29,34 @@ constexpr int kKeysPerThread = 16;
 constexpr int kTile = kCsrBlock * kKeysPerThread;  // 4096
 constexpr unsigned long long kSentinel = ~0ull;
 
-__global__ void csr_make_keys(const int* src, const int* dst, long long E, long long n, int B,
+// Keys (source << Bd) | target. Single graph: ids in [0, n), source = id.
+// Batch (gv != nullptr): edge i belongs to the graph g with eoff[g] <= i <
+// eoff[g+1]; its ids are graph-local in [0, gv[g+1] - gv[g]); the source part
+// is the global id gv[g] + local, the target part stays local.
+__global__ void csr_make_keys(const int* src, const int* dst, long long E, long long n, int Bd,
+                              const long long* gv, const long long* eoff, long long G,
                               unsigned long long* keys, int* status) {
   for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < E;
        i += (long long)gridDim.x * blockDim.x) {
     int a = src[i], b = dst[i];
+    long long base = 0, lim = n;
+    if (gv) {
+      long long lo = 0, hi = G;  // last g with eoff[g] <= i
+      while (hi - lo > 1) {
+        long long mid = (lo + hi) >> 1;
+        if (eoff[mid] <= i) lo = mid;
+        else hi = mid;
+      }
+      base = gv[lo];
+      lim = gv[lo + 1] - base;
+    }
     unsigned long long k0 = kSentinel, k1 = kSentinel;
-    if ((unsigned long long)(unsigned)a >= (unsigned long long)n ||
-        (unsigned long long)(unsigned)b >= (unsigned long long)n) {
+    if ((unsigned long long)(unsigned)a >= (unsigned long long)lim ||
+        (unsigned long long)(unsigned)b >= (unsigned long long)lim) {
       atomicCAS(status, 0, 1);
     } else if (a != b) {
-      k0 = ((unsigned long long)a << B) | (unsigned long long)b;
-      k1 = ((unsigned long long)b << B) | (unsigned long long)a;
+      k0 = ((unsigned long long)(base + a) << Bd) | (unsigned long long)b;
+      k1 = ((unsigned long long)(base + b) << Bd) | (unsigned long long)a;
     }
     keys[2 * i] = k0;
     keys[2 * i + 1] = k1;
@@ -198,7 +214,7 @@ __global__ void __launch_bounds__(kCsrBlock) csr_count_unique(const unsigned lon
   }
 }
 
-// Ordered emission of the unique keys: adj[pos] = low B bits; the first arc
+// Ordered emission of the unique keys: adj[pos] = low Bd bits; the first arc
 // of each source fixes offsets[] for that source and every source without
 // arcs just below it; the last arc fills the offsets of the sources above it.
 __global__ void __launch_bounds__(kCsrBlock) csr_emit(const unsigned long long* k, long long N,
@@ -260,7 +276,7 @@ static int bits_for(long long n) {
   return B;
 }
 
-CsrLayout csr_layout(long long n, long long E, int sms) {
+CsrLayout csr_layout(long long n, long long E, int sms, long long max_graph_n) {
   CsrLayout L{};
   long long N = 2 * E;
   long long G = (long long)sms * 2;
@@ -272,7 +288,10 @@ CsrLayout csr_layout(long long n, long long E, int sms) {
   if (chunk < kTile) chunk = kTile;
   L.chunk = chunk;
   L.N = N;
-  L.B = bits_for(n);
+  L.Bs = bits_for(n);
+  // batched: one spare code so that no valid (local) target has all bits set
+  // and a valid key can never equal the sentinel in the sorted bits
+  L.B = max_graph_n > 0 ? bits_for(max_graph_n + 1) : L.Bs;
   size_t off = 0;
   auto al = [](size_t x) { return (x + 255) / 256 * 256; };
   L.status = off;
@@ -290,8 +309,8 @@ CsrLayout csr_layout(long long n, long long E, int sms) {
 }
 
 cudaError_t csr_build_launch(const CsrLayout& L, char* ws, long long n, long long E, const int* src,
-                             const int* dst, long long* off_out, int* adj_out, long long* m_out,
-                             cudaStream_t stream) {
+                             const int* dst, const long long* gv, const long long* eoff, long long ngraphs,
+                             long long* off_out, int* adj_out, long long* m_out, cudaStream_t stream) {
   cudaError_t e;
   int* status = (int*)(ws + L.status);
   unsigned long long* k0 = (unsigned long long*)(ws + L.keys0);
@@ -305,8 +324,8 @@ cudaError_t csr_build_launch(const CsrLayout& L, char* ws, long long n, long lon
   const long long N = L.N;
   const int G = L.grid;
   int kb = (int)std::min<long long>((E + kCsrBlock - 1) / kCsrBlock, 65536);
-  csr_make_keys<<<kb, kCsrBlock, 0, stream>>>(src, dst, E, n, L.B, k0, status);
-  const int passes = (2 * L.B + 7) / 8;
+  csr_make_keys<<<kb, kCsrBlock, 0, stream>>>(src, dst, E, n, L.B, gv, eoff, ngraphs, k0, status);
+  const int passes = (L.Bs + L.B + 7) / 8;
   for (int p = 0; p < passes; p++) {
     int shift = 8 * p;
     rs_upsweep<<<G, kCsrBlock, 0, stream>>>(k0, N, L.chunk, shift, hist);

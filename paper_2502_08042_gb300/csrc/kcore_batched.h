@@ -1,0 +1,36 @@
+// Host/device shared declarations of the batched peel.
+#pragma once
+#include <cuda_runtime.h>
+#include <stddef.h>
+
+#include "kcore_peel.h"
+
+namespace kc {
+
+constexpr long long kMaxSortGraphs = 16384;  // batches up to this size are ordered by arcs
+
+struct BatchArgs {
+  long long G;
+  long long m;               // total arcs (bound for offsets)
+  const long long* gv;       // [G+1] first vertex of each graph
+  const long long* off;      // [N+1] global arc offsets
+  const int* adj;            // [m] graph-local neighbour ids
+  int* core;                 // [N]
+  int* kmax;                 // [G]
+  int* deg;                  // [N] induced degrees of graphs too large for shared memory
+  int* A0;                   // [N] active lists (ping-pong)
+  int* A1;
+  int* F0;                   // [N] frontiers (ping-pong)
+  int* F1;
+  const int* order;          // [G] processing order, or nullptr
+  int* next_graph;           // work counter
+  int* status;
+  int smem_deg_max;          // graphs with at most this many vertices keep d~ in shared memory
+};
+
+int batch_occupancy(int block, size_t smem);
+size_t batch_static_smem(int block);
+cudaError_t batch_launch(const BatchArgs& a, int block, int grid, size_t smem, bool sort_graphs,
+                         cudaStream_t stream);
+
+}  // namespace kc

@@ -16,7 +16,8 @@ from . import _native
 STATUS = {0: "OK", 1: "INVALID", 2: "OOM", 3: "CUDA", 4: "TIMEOUT", 5: "NOT_SIMPLE", 6: "CAPACITY"}
 OPTIONS = {"sync_mode": 0, "ctas_per_sm": 1, "slice_arcs": 2, "local_queue": 3, "timeout_ms": 4,
            "min_ctas": 5, "vertices_per_cta": 6, "test_stall": 7,
-           "trace": 8, "idle_sleep_ns": 9, "poll_sleep_ns": 10}
+           "trace": 8, "idle_sleep_ns": 9, "poll_sleep_ns": 10, "batch_block": 11,
+           "batch_smem_vertices": 12, "batch_ctas_per_sm": 13}
 TRACE_FIELDS = ("t_start", "t_scanned", "t_done", "level", "scanned", "found", "queued", "scan_ctas",
                 "arcs", "decrements", "max_cta_scan_ns", "max_cta_start_delay_ns", "busy_ns",
                 "batches")
@@ -148,6 +149,53 @@ class KCore:
         if sync:
             self.sync()
         return coreness, kmax
+
+    def decompose_batched(self, graph_vertex_offsets, offsets, adj, coreness=None, kmax=None,
+                          stream=None, sync: bool = True):
+        """Coreness of every graph of a segmented CSR on the GPU (graph-local
+        adjacency ids). graph_vertex_offsets: int64 [G+1]; offsets: int64 [N+1];
+        adj: int32 [M]. Returns (coreness int32 [N], kmax int32 [G])."""
+        torch = _torch()
+        G = graph_vertex_offsets.numel() - 1
+        N = offsets.numel() - 1
+        M = adj.numel()
+        dev = offsets.device
+        if coreness is None:
+            coreness = torch.empty(max(N, 0), dtype=torch.int32, device=dev)
+        if kmax is None:
+            kmax = torch.empty(max(G, 0), dtype=torch.int32, device=dev)
+        self._check(self._L.kcore_decompose_batched(
+            self._h, G, N, M, _ptr(graph_vertex_offsets), _ptr(offsets), _ptr(adj), _ptr(coreness),
+            _ptr(kmax), _stream_ptr(stream)))
+        if sync:
+            self.sync()
+        return coreness, kmax
+
+    def build_csr_batched(self, graph_vertex_offsets, graph_edge_offsets, src, dst,
+                          max_graph_vertices: int, stream=None, sync: bool = True):
+        """Segmented CSR of a batch of edge lists with graph-local ids (all CUDA
+        tensors; offsets int64). Returns (offsets int64 [N+1], adj int32 [m])."""
+        torch = _torch()
+        G = graph_vertex_offsets.numel() - 1
+        N = int(graph_vertex_offsets[-1].item())
+        E = src.numel()
+        dev = src.device
+        off = torch.empty(N + 1, dtype=torch.int64, device=dev)
+        adj = torch.empty(max(2 * E, 1), dtype=torch.int32, device=dev)
+        m = torch.zeros(1, dtype=torch.int64, device=dev)
+        self._check(self._L.kcore_build_csr_batched(
+            self._h, G, N, E, int(max_graph_vertices), _ptr(graph_vertex_offsets),
+            _ptr(graph_edge_offsets), _ptr(src), _ptr(dst), _ptr(off), _ptr(adj), _ptr(m),
+            _stream_ptr(stream)))
+        if not sync:
+            return off, adj, m
+        self.sync()
+        return off, adj[: int(m.item())]
+
+    def batched_workspace_size(self, G: int, N: int) -> int:
+        b = ctypes.c_size_t()
+        self._check(self._L.kcore_batched_workspace_size(self._h, G, N, ctypes.byref(b)))
+        return int(b.value)
 
     def build_csr(self, n: int, src, dst, stream=None, sync: bool = True):
         """Simple undirected CSR of a device edge list (int32 tensors).
