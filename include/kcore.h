@@ -208,6 +208,50 @@ kcore_status kcore_build_csr_batched(kcore_handle h, int64_t num_graphs, int64_t
 kcore_status kcore_batched_workspace_size(kcore_handle h, int64_t num_graphs, int64_t total_vertices,
                                           size_t* bytes);
 
+/* ------------------------------------------------------------------------
+ * Served peel (the paper peels one graph at a time; this is the request-loop
+ * form of the same peel). A server owns a device memory pool reserved at
+ * creation and admits a request only when its footprint (offsets, arcs,
+ * coreness and the peel state kept resident while it is in flight) fits and a
+ * slot is free. kcore_server_poll moves requests through copy-in, launch,
+ * copy-out without blocking on the device: the small requests that became
+ * ready together run as one batched launch (one CTA per graph) on one of
+ * several streams, so requests admitted while others are on the GPU overlap
+ * with them; large requests run the whole-GPU peel on their own stream.
+ * One host thread drives a server (not thread-safe). */
+typedef struct kcore_server_ctx* kcore_server;
+
+typedef struct {
+  size_t pool_bytes;      /* device pool for requests in flight (0: a quarter of free memory) */
+  int max_requests;       /* requests in flight at most (0: 4096) */
+  int streams;            /* launch streams for batched launches (0: 4, at most 32) */
+  int64_t large_vertices; /* requests with more vertices use the whole-GPU peel (0: 2^20) */
+  int64_t large_arcs;     /* ... or more arcs (0: 2^25) */
+} kcore_server_config;
+
+/* cfg may be NULL (defaults). Errors: INVALID, OOM (pool or pinned buffers). */
+kcore_status kcore_server_create(kcore_server* out, int device, const kcore_server_config* cfg);
+
+/* Queues one graph (simple undirected CSR in HOST memory, layout as for
+ * kcore_decompose) and returns its ticket. Non-blocking: offsets_host,
+ * adj_host and coreness_host must stay valid until the ticket is returned by
+ * kcore_server_poll (pinned host memory makes the copies asynchronous).
+ * KCORE_ERR_CAPACITY: not admitted now (pool or slots full); poll and retry. */
+kcore_status kcore_server_submit(kcore_server s, int64_t n, int64_t m, const int64_t* offsets_host,
+                                 const int32_t* adj_host, int32_t* coreness_host, int64_t* ticket_out);
+
+/* Advances all requests and returns up to max_out completed ones: their
+ * tickets, k_max and device status (0 = OK, else a kcore_status value); their
+ * coreness is in the coreness_host buffer given at submit. *n_out = count. */
+kcore_status kcore_server_poll(kcore_server s, int64_t* tickets_out, int32_t* kmax_out, int32_t* status_out,
+                               int max_out, int* n_out);
+
+/* Requests in flight and pool bytes in use / reserved (any pointer may be NULL). */
+kcore_status kcore_server_info(kcore_server s, int64_t* in_flight, int64_t* pool_used, int64_t* pool_bytes);
+
+/* Waits for the device and frees everything; results not yet polled are dropped. */
+kcore_status kcore_server_destroy(kcore_server s);
+
 /* Largest graph kcore_decompose_static accepts. */
 #define KCORE_STATIC_MAX_VERTICES (1LL << 20)
 #define KCORE_STATIC_MAX_ARCS (1LL << 24)

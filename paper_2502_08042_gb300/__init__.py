@@ -4,6 +4,6 @@ The compute runs in libkcore.so (hand-written CUDA for sm_103a behind the C ABI
 of include/kcore.h); this package only builds/loads it and marshals arguments.
 """
 from ._native import build, lib  # noqa: F401
-from .kcore import KCore, KCoreError, decompose  # noqa: F401
+from .kcore import KCore, KCoreError, KCoreServer, decompose  # noqa: F401
 
-__all__ = ["build", "lib", "KCore", "KCoreError", "decompose"]
+__all__ = ["build", "lib", "KCore", "KCoreError", "KCoreServer", "decompose"]

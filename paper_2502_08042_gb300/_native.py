@@ -123,7 +123,18 @@ SIGNATURES = {
     "kcore_batched_workspace_size": ([c_p, c_i64, c_i64, ctypes.POINTER(c_sz)], ctypes.c_int),
     "kcore_build_csr_batched": ([c_p, c_i64, c_i64, c_i64, c_i64, c_p, c_p, c_p, c_p, c_p, c_p, c_p,
                                  c_p], ctypes.c_int),
+    "kcore_server_create": ([ctypes.POINTER(c_p), ctypes.c_int, c_p], ctypes.c_int),
+    "kcore_server_submit": ([c_p, c_i64, c_i64, c_p, c_p, c_p, ctypes.POINTER(c_i64)], ctypes.c_int),
+    "kcore_server_poll": ([c_p, c_p, c_p, c_p, ctypes.c_int, ctypes.POINTER(ctypes.c_int)], ctypes.c_int),
+    "kcore_server_info": ([c_p, ctypes.POINTER(c_i64), ctypes.POINTER(c_i64), ctypes.POINTER(c_i64)],
+                          ctypes.c_int),
+    "kcore_server_destroy": ([c_p], ctypes.c_int),
 }
+
+
+class ServerConfig(ctypes.Structure):
+    _fields_ = [("pool_bytes", c_sz), ("max_requests", ctypes.c_int), ("streams", ctypes.c_int),
+                ("large_vertices", c_i64), ("large_arcs", c_i64)]
 
 
 def _declare(L):

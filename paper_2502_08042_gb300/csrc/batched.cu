@@ -148,31 +148,33 @@ __device__ int select_frontier(const int* A, int la, int* F, const int* D, bool 
   return written;
 }
 
+// Peels one graph with the whole CTA (see the file comment).
 template <int BLOCK>
-__device__ void peel_one_graph(const BatchArgs& a, long long g, int* sdeg, BatchShared<BLOCK>& sh) {
+__device__ void peel_one_graph(const GraphDesc& gd, int smem_deg_max, int* status, int* sdeg,
+                               BatchShared<BLOCK>& sh) {
   const int tid = threadIdx.x, lane = tid & 31;
-  const long long v0 = a.gv[g];
-  const long long nl = a.gv[g + 1] - v0;
-  if (nl <= 0) {
-    if (tid == 0) a.kmax[g] = 0;
+  if (gd.n <= 0) {
+    if (tid == 0) *gd.kmax = 0;
+    __syncthreads();
     return;
   }
-  const int n = (int)nl;
-  const bool in_smem = n <= a.smem_deg_max;
-  int* D = in_smem ? sdeg : a.deg + v0;
-  const long long* O = a.off + v0;
-  int* core = a.core + v0;
-  int* A0 = a.A0 + v0;
-  int* A1 = a.A1 + v0;
-  int* F0 = a.F0 + v0;
-  int* F1 = a.F1 + v0;
+  const int n = (int)gd.n;
+  const bool in_smem = n <= smem_deg_max;
+  int* D = in_smem ? sdeg : gd.deg;
+  const long long* O = gd.off;
+  const int* adj = gd.adj;
+  int* core = gd.core;
+  int* A0 = gd.A0;
+  int* A1 = gd.A1;
+  int* F0 = gd.F0;
+  int* F1 = gd.F1;
 
   // degrees, identity active list, minimum degree
   int lmin = INT_MAX;
   for (int v = tid; v < n; v += BLOCK) {
     long long o0 = O[v], o1 = O[v + 1];
-    if (o0 < 0 || o1 < o0 || o1 > a.m || o1 - o0 >= n) {
-      atomicCAS(a.status, 0, ST_NOT_SIMPLE);
+    if (o0 < 0 || o1 < o0 || o1 > gd.m || o1 - o0 >= n) {
+      atomicCAS(status, 0, ST_NOT_SIMPLE);
       o1 = o0;
     }
     int d = (int)(o1 - o0);
@@ -221,9 +223,9 @@ __device__ void peel_one_graph(const BatchArgs& a, long long g, int* sdeg, Batch
                 else hi = mid;
               }
               int idx = lo - 1;
-              u[q] = ld_stream_s32(a.adj + sh.start[idx] + (j - sh.pre[idx]));
+              u[q] = ld_stream_s32(adj + sh.start[idx] + (j - sh.pre[idx]));
               if ((unsigned)u[q] >= (unsigned)n) {
-                atomicCAS(a.status, 0, ST_NOT_SIMPLE);
+                atomicCAS(status, 0, ST_NOT_SIMPLE);
                 u[q] = -1;
               }
             }
@@ -262,7 +264,7 @@ __device__ void peel_one_graph(const BatchArgs& a, long long g, int* sdeg, Batch
     if (dmin != k + 1) nf = select_frontier<BLOCK>(A, la, F0, D, in_smem, dmin, sh);
     k = dmin;
   }
-  if (tid == 0) a.kmax[g] = kmax;
+  if (tid == 0) *gd.kmax = kmax;
   __syncthreads();
 }
 
@@ -277,7 +279,39 @@ __global__ void __launch_bounds__(BLOCK, (BLOCK >= 1024 ? 1 : 2048 / BLOCK / 2))
     __syncthreads();
     if (gi >= a.G) break;
     long long g = a.order ? a.order[gi] : gi;
-    peel_one_graph<BLOCK>(a, g, sdeg, sh);
+    GraphDesc gd;
+    const long long v0 = a.gv[g];
+    gd.n = a.gv[g + 1] - v0;
+    gd.m = a.m;
+    gd.off = a.off + v0;
+    gd.adj = a.adj;
+    gd.core = a.core + v0;
+    gd.kmax = a.kmax + g;
+    gd.deg = a.deg + v0;
+    gd.A0 = a.A0 + v0;
+    gd.A1 = a.A1 + v0;
+    gd.F0 = a.F0 + v0;
+    gd.F1 = a.F1 + v0;
+    peel_one_graph<BLOCK>(gd, a.smem_deg_max, a.status, sdeg, sh);
+  }
+}
+
+// The same peel over graph descriptors held in a device table (graphs in
+// separate allocations, as the server holds them). The launch lists the
+// table slots to process; CTAs take them from a counter.
+template <int BLOCK>
+__global__ void __launch_bounds__(BLOCK, (BLOCK >= 1024 ? 1 : 2048 / BLOCK / 2))
+    desc_peel(const GraphDesc* table, SlotList list, int* next, int smem_deg_max, int* status) {
+  extern __shared__ int sdeg[];
+  __shared__ BatchShared<BLOCK> sh;
+  for (;;) {
+    if (threadIdx.x == 0) sh.g = atomicAdd(next, 1);
+    __syncthreads();
+    int gi = sh.g;
+    __syncthreads();
+    if (gi >= list.count) break;
+    GraphDesc gd = table[list.slot[gi]];
+    peel_one_graph<BLOCK>(gd, smem_deg_max, status, sdeg, sh);
   }
 }
 
@@ -339,6 +373,17 @@ int occupancy_block(size_t smem) {
   return nb;
 }
 }  // namespace
+
+cudaError_t desc_launch(const GraphDesc* table, const SlotList& list, int* next, int smem_deg_max,
+                        int* status, int grid, size_t smem, cudaStream_t stream) {
+  cudaError_t e = cudaFuncSetAttribute(desc_peel<1024>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       (int)smem);
+  if (e != cudaSuccess) return e;
+  desc_peel<1024><<<grid, 1024, smem, stream>>>(table, list, next, smem_deg_max, status);
+  return cudaGetLastError();
+}
+
+size_t desc_static_smem() { return sizeof(BatchShared<1024>); }
 
 int batch_occupancy(int block, size_t smem) {
   switch (block) {

@@ -28,6 +28,33 @@ struct BatchArgs {
   int smem_deg_max;          // graphs with at most this many vertices keep d~ in shared memory
 };
 
+// One graph of a descriptor-driven launch: offsets hold absolute indices
+// into adj (bounded by m); scratch arrays hold n entries each.
+struct GraphDesc {
+  const long long* off;
+  const int* adj;
+  int* core;
+  int* kmax;
+  int* deg;
+  int* A0;
+  int* A1;
+  int* F0;
+  int* F1;
+  long long n;
+  long long m;
+};
+
+// Table slots of one descriptor-driven launch (passed by value as a kernel
+// parameter, so no host buffer must outlive the launch).
+constexpr int kMaxSlotsPerLaunch = 1024;
+struct SlotList {
+  int count;
+  int slot[kMaxSlotsPerLaunch];
+};
+
+cudaError_t desc_launch(const GraphDesc* table, const SlotList& list, int* next, int smem_deg_max,
+                        int* status, int grid, size_t smem, cudaStream_t stream);
+size_t desc_static_smem();
 int batch_occupancy(int block, size_t smem);
 size_t batch_static_smem(int block);
 cudaError_t batch_launch(const BatchArgs& a, int block, int grid, size_t smem, bool sort_graphs,

@@ -241,6 +241,75 @@ class KCore:
         self._check(st)
 
 
+class KCoreServer:
+    """Request loop with continuous batching (kcore_server_*). Host arrays given
+    to submit() must stay alive until their ticket comes back from poll()."""
+
+    def __init__(self, device: int = 0, pool_bytes: int = 0, max_requests: int = 0, streams: int = 0,
+                 large_vertices: int = 0, large_arcs: int = 0):
+        self._L = _native.lib()
+        cfg = _native.ServerConfig(pool_bytes, max_requests, streams, large_vertices, large_arcs)
+        h = ctypes.c_void_p()
+        st = self._L.kcore_server_create(ctypes.byref(h), device, ctypes.byref(cfg))
+        if st != 0:
+            raise KCoreError(st, "kcore_server_create failed")
+        self._h = h
+        self._keep = {}
+        self._cap = max_requests or 4096
+        self._t = np.zeros(self._cap, np.int64)
+        self._k = np.zeros(self._cap, np.int32)
+        self._s = np.zeros(self._cap, np.int32)
+
+    def submit(self, offsets: np.ndarray, adj: np.ndarray, coreness_out: np.ndarray):
+        """Queues a host CSR; returns its ticket, or None when not admitted now."""
+        n = len(offsets) - 1
+        t = ctypes.c_int64()
+        st = self._L.kcore_server_submit(self._h, n, len(adj), _ptr(offsets), _ptr(adj),
+                                         _ptr(coreness_out), ctypes.byref(t))
+        if st == 6:  # KCORE_ERR_CAPACITY: pool or slots full
+            return None
+        if st != 0:
+            raise KCoreError(st, "kcore_server_submit failed")
+        self._keep[t.value] = (offsets, adj, coreness_out)
+        return t.value
+
+    def poll(self):
+        """Advances all requests; returns a list of (ticket, kmax, status)."""
+        cnt = ctypes.c_int()
+        st = self._L.kcore_server_poll(self._h, self._t.ctypes.data, self._k.ctypes.data,
+                                       self._s.ctypes.data, self._cap, ctypes.byref(cnt))
+        if st != 0:
+            raise KCoreError(st, "kcore_server_poll failed")
+        out = []
+        for i in range(cnt.value):
+            t = int(self._t[i])
+            self._keep.pop(t, None)
+            out.append((t, int(self._k[i]), int(self._s[i])))
+        return out
+
+    def info(self):
+        a, b, c = ctypes.c_int64(), ctypes.c_int64(), ctypes.c_int64()
+        self._L.kcore_server_info(self._h, ctypes.byref(a), ctypes.byref(b), ctypes.byref(c))
+        return {"in_flight": a.value, "pool_used": b.value, "pool_bytes": c.value}
+
+    def close(self):
+        if getattr(self, "_h", None):
+            self._L.kcore_server_destroy(self._h)
+            self._h = None
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
 def decompose(offsets, adj, device: int | None = None, **options):
     """One-shot convenience wrapper around KCore.decompose (synchronous)."""
     dev = offsets.device.index if device is None else device
