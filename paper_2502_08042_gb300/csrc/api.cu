@@ -460,6 +460,7 @@ kcore_status kcore_decompose_batched(kcore_handle h, int64_t num_graphs, int64_t
   batch_shape(h, &block, &sv, &grid, &smem);
   kc::BatchArgs a{};
   a.G = num_graphs;
+  a.N = total_vertices;
   a.m = total_arcs;
   a.gv = (const long long*)graph_vertex_offsets;
   a.off = (const long long*)offsets;
@@ -528,16 +529,20 @@ kcore_status kcore_sync_status(kcore_handle h) {
   h->pending = false;
   if (e != cudaSuccess) return cuda_fail(h, e, "stream synchronize");
   if (h->last_batch_status) {
-    int bs = 0;
-    e = cudaMemcpy(&bs, h->last_batch_status, sizeof(int), cudaMemcpyDeviceToHost);
+    int bs[4] = {0, 0, 0, 0};
+    e = cudaMemcpy(bs, h->last_batch_status, sizeof(bs), cudaMemcpyDeviceToHost);
     h->last_batch_status = nullptr;
     if (e != cudaSuccess) return cuda_fail(h, e, "read status");
     h->stats.grid = h->last_batch_grid;
     h->stats.reserved[0] = h->last_batch_block;
     h->stats.reserved[1] = h->last_batch_smem_vertices;
-    if (bs == kc::ST_NOT_SIMPLE)
-      return fail(h, KCORE_ERR_NOT_SIMPLE, "malformed segmented CSR detected on the device");
-    if (bs != 0) return fail(h, KCORE_ERR_CUDA, "unknown device status " + std::to_string(bs));
+    if (bs[0] == kc::ST_NOT_SIMPLE) {
+      long long val = (long long)(unsigned)bs[2] | ((long long)bs[3] << 32);
+      return fail(h, KCORE_ERR_NOT_SIMPLE,
+                  "malformed segmented CSR detected on the device (check " + std::to_string(bs[1]) +
+                      ", value " + std::to_string(val) + "); the graphs concerned report k_max -1");
+    }
+    if (bs[0] != 0) return fail(h, KCORE_ERR_CUDA, "unknown device status " + std::to_string(bs[0]));
     return KCORE_OK;
   }
   if (h->last_csr_status) {

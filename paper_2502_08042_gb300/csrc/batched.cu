@@ -36,7 +36,19 @@ struct BatchShared {
   int cnt;
   int g;
   int total;
+  int bad;  // this graph failed a bounds check: stop peeling it
 };
+
+// Records a failed bounds check (first one wins: code, graph-local value) and
+// flags the status; the access itself is skipped by the caller.
+__device__ __forceinline__ void flag_bad(int* status, int code, long long value, int* bad) {
+  if (atomicCAS(status, 0, ST_NOT_SIMPLE) == 0) {
+    status[1] = code;
+    status[2] = (int)(value & 0xffffffffll);
+    status[3] = (int)(value >> 32);
+  }
+  *bad = 1;
+}
 
 // Block-wide exclusive scan of one int per thread; returns the exclusive value,
 // *total gets the sum. Contains two __syncthreads.
@@ -80,7 +92,7 @@ __device__ __forceinline__ int load_deg(const int* D, int v, bool in_smem) {
 // are also written to F (the next frontier if level k+1 is not empty).
 // Returns the survivors; *nf gets the number written to F.
 template <int BLOCK>
-__device__ int compact_active(const int* A, int la, int* out, int* F, const int* D, bool in_smem,
+__device__ int compact_active(const int* A, int la, int n, int* out, int* F, const int* D, bool in_smem,
                               int k, BatchShared<BLOCK>& sh, int* dmin, int* nf) {
   int written = 0, wf = 0, lmin = INT_MAX;
   for (int base = 0; base < la; base += BLOCK * kScanItems) {
@@ -90,7 +102,10 @@ __device__ int compact_active(const int* A, int la, int* out, int* F, const int*
     for (int q = 0; q < kScanItems; q++) {
       int i = base + q * BLOCK + threadIdx.x;
       v[q] = -1;
-      if (i < la) v[q] = A[i];
+      if (i < la) {
+        int x = A[i];
+        v[q] = (unsigned)x < (unsigned)n ? x : -1;  // ids are < n by construction; checked anyway
+      }
     }
 #pragma unroll
     for (int q = 0; q < kScanItems; q++) {
@@ -115,14 +130,14 @@ __device__ int compact_active(const int* A, int la, int* out, int* F, const int*
     written += tot & 0xffff;
     wf += tot >> 16;
   }
-  *dmin = block_min(lmin, sh);
+  *dmin = block_min(lmin, sh);  // its barriers also publish the writes above
   *nf = wf;
   return written;
 }
 
 // Selection of the frontier: entries of A with D[v] == k.
 template <int BLOCK>
-__device__ int select_frontier(const int* A, int la, int* F, const int* D, bool in_smem, int k,
+__device__ int select_frontier(const int* A, int la, int n, int* F, const int* D, bool in_smem, int k,
                                BatchShared<BLOCK>& sh) {
   int written = 0;
   for (int base = 0; base < la; base += BLOCK * kScanItems) {
@@ -132,7 +147,10 @@ __device__ int select_frontier(const int* A, int la, int* F, const int* D, bool 
     for (int q = 0; q < kScanItems; q++) {
       int i = base + q * BLOCK + threadIdx.x;
       v[q] = -1;
-      if (i < la) v[q] = A[i];
+      if (i < la) {
+        int x = A[i];
+        v[q] = (unsigned)x < (unsigned)n ? x : -1;  // ids are < n by construction; checked anyway
+      }
     }
 #pragma unroll
     for (int q = 0; q < kScanItems; q++)
@@ -145,6 +163,7 @@ __device__ int select_frontier(const int* A, int la, int* F, const int* D, bool 
       if ((take >> q) & 1u) F[p++] = v[q];
     written += tot;
   }
+  __syncthreads();  // the frontier is read by other threads next
   return written;
 }
 
@@ -170,11 +189,13 @@ __device__ void peel_one_graph(const GraphDesc& gd, int smem_deg_max, int* statu
   int* F1 = gd.F1;
 
   // degrees, identity active list, minimum degree
+  if (tid == 0) sh.bad = 0;
+  __syncthreads();
   int lmin = INT_MAX;
   for (int v = tid; v < n; v += BLOCK) {
     long long o0 = O[v], o1 = O[v + 1];
     if (o0 < 0 || o1 < o0 || o1 > gd.m || o1 - o0 >= n) {
-      atomicCAS(status, 0, ST_NOT_SIMPLE);
+      flag_bad(status, 1, v, &sh.bad);
       o1 = o0;
     }
     int d = (int)(o1 - o0);
@@ -183,16 +204,25 @@ __device__ void peel_one_graph(const GraphDesc& gd, int smem_deg_max, int* statu
     lmin = min(lmin, d);
   }
   int k = block_min(lmin, sh);  // also orders the writes above
+  if (sh.bad) {  // malformed offsets: leave this graph (its outputs are undefined)
+    if (tid == 0) *gd.kmax = -1;
+    __syncthreads();
+    return;
+  }
   int* A = A0;
   int* An = A1;
   int la = n;
   int kmax = 0;
-  int nf = select_frontier<BLOCK>(A, la, F0, D, in_smem, k, sh);
+  int nf = select_frontier<BLOCK>(A, la, n, F0, D, in_smem, k, sh);
   for (;;) {
     int* Fc = F0;
     int* Fn = F1;
     while (nf > 0) {
-      for (int i = tid; i < nf; i += BLOCK) core[Fc[i]] = k;
+      for (int i = tid; i < nf; i += BLOCK) {
+        int v = Fc[i];
+        if ((unsigned)v < (unsigned)n) core[v] = k;
+        else flag_bad(status, 6, v, &sh.bad);
+      }
       if (tid == 0) sh.cnt = 0;
       __syncthreads();
       for (int c0 = 0; c0 < nf; c0 += BLOCK) {
@@ -201,8 +231,14 @@ __device__ void peel_one_graph(const GraphDesc& gd, int smem_deg_max, int* statu
         long long st = 0;
         if (tid < cnum) {
           int v = Fc[c0 + tid];
-          st = O[v];
-          len = (int)(O[v + 1] - st);
+          if ((unsigned)v < (unsigned)n) {
+            st = O[v];
+            long long e = O[v + 1];
+            if (st < 0 || e < st || e > gd.m || e - st >= n) flag_bad(status, 2, v, &sh.bad);
+            else len = (int)(e - st);
+          } else {
+            flag_bad(status, 3, v, &sh.bad);
+          }
         }
         int total;
         int ex = block_excl_scan(len, sh, &total);
@@ -223,10 +259,15 @@ __device__ void peel_one_graph(const GraphDesc& gd, int smem_deg_max, int* statu
                 else hi = mid;
               }
               int idx = lo - 1;
-              u[q] = ld_stream_s32(adj + sh.start[idx] + (j - sh.pre[idx]));
-              if ((unsigned)u[q] >= (unsigned)n) {
-                atomicCAS(status, 0, ST_NOT_SIMPLE);
-                u[q] = -1;
+              long long arc = sh.start[idx] + (j - sh.pre[idx]);
+              if (idx < 0 || arc < 0 || arc >= gd.m) {
+                flag_bad(status, 4, arc, &sh.bad);
+              } else {
+                u[q] = ld_stream_s32(adj + arc);
+                if ((unsigned)u[q] >= (unsigned)n) {
+                  flag_bad(status, 5, u[q], &sh.bad);
+                  u[q] = -1;
+                }
               }
             }
           }
@@ -239,13 +280,18 @@ __device__ void peel_one_graph(const GraphDesc& gd, int smem_deg_max, int* statu
               int base = 0;
               if (lane == __ffs(m) - 1) base = atomicAdd(&sh.cnt, __popc(m));
               base = __shfl_sync(kFull, base, __ffs(m) - 1);
-              if (cross) Fn[base + __popc(m & lanemask_lt())] = u[q];
+              int pos = base + __popc(m & lanemask_lt());
+              if (cross) {
+                if (pos < n) Fn[pos] = u[q];
+                else flag_bad(status, 7, pos, &sh.bad);
+              }
             }
           }
         }
         __syncthreads();
       }
       nf = sh.cnt;
+      if (nf > n) nf = 0;  // cannot happen: every vertex lands on k at most once per level
       __syncthreads();
       int* t = Fc;
       Fc = Fn;
@@ -256,12 +302,12 @@ __device__ void peel_one_graph(const GraphDesc& gd, int smem_deg_max, int* statu
     // rest is the next non-empty level; vertices at k+1 are collected on the
     // way in case that level is the next one
     int dmin;
-    la = compact_active<BLOCK>(A, la, An, F0, D, in_smem, k, sh, &dmin, &nf);
+    la = compact_active<BLOCK>(A, la, n, An, F0, D, in_smem, k, sh, &dmin, &nf);
     int* t = A;
     A = An;
     An = t;
     if (la == 0) break;
-    if (dmin != k + 1) nf = select_frontier<BLOCK>(A, la, F0, D, in_smem, dmin, sh);
+    if (dmin != k + 1) nf = select_frontier<BLOCK>(A, la, n, F0, D, in_smem, dmin, sh);
     k = dmin;
   }
   if (tid == 0) *gd.kmax = kmax;
@@ -279,9 +325,20 @@ __global__ void __launch_bounds__(BLOCK, (BLOCK >= 1024 ? 1 : 2048 / BLOCK / 2))
     __syncthreads();
     if (gi >= a.G) break;
     long long g = a.order ? a.order[gi] : gi;
+    if (g < 0 || g >= a.G) {  // the order is a permutation of [0, G); checked anyway
+      if (threadIdx.x == 0) flag_bad(a.status, 8, g, &sh.bad);
+      continue;
+    }
     GraphDesc gd;
     const long long v0 = a.gv[g];
     gd.n = a.gv[g + 1] - v0;
+    if (v0 < 0 || gd.n < 0 || v0 + gd.n > a.N) {  // graph outside the vertex range
+      if (threadIdx.x == 0) {
+        flag_bad(a.status, 9, g, &sh.bad);
+        a.kmax[g] = -1;
+      }
+      continue;
+    }
     gd.m = a.m;
     gd.off = a.off + v0;
     gd.adj = a.adj;

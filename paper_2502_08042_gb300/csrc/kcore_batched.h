@@ -11,6 +11,7 @@ constexpr long long kMaxSortGraphs = 16384;  // batches up to this size are orde
 
 struct BatchArgs {
   long long G;
+  long long N;               // total vertices (gv[G])
   long long m;               // total arcs (bound for offsets)
   const long long* gv;       // [G+1] first vertex of each graph
   const long long* off;      // [N+1] global arc offsets
