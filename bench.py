@@ -301,7 +301,7 @@ def run_gpu(args):
     bmin = algorithmic_bytes(n, m)
     achieved = bmin / (ms_per_step / 1e3) / 1e9
     traffic = None
-    tp = os.path.join(ROOT, "profiles", "traffic.json")
+    tp = os.path.join(ROOT, "profiles", "peel_persistent_rmat24_traffic.json")
     if os.path.exists(tp):
         with open(tp) as f:
             tj = json.load(f)
