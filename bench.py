@@ -300,12 +300,13 @@ def run_gpu(args):
     peak, peak_kind = load_peaks()
     bmin = algorithmic_bytes(n, m)
     achieved = bmin / (ms_per_step / 1e3) / 1e9
+    kname, ksrc = PEEL_KERNELS[st["sync_mode"]]
     traffic = None
-    tp = os.path.join(ROOT, "profiles", "peel_persistent_rmat24_traffic.json")
+    tp = os.path.join(ROOT, "profiles", f"{kname}_{args.workload}_traffic.json")
     if os.path.exists(tp):
         with open(tp) as f:
             tj = json.load(f)
-        if tj.get("workload") == args.workload and tj.get("kernel_rev") == kernel_revision():
+        if tj.get("workload") == args.workload and tj.get("kernel_rev") == kernel_revision(ksrc):
             traffic = tj.get("dram_bytes_per_launch")
     cpu = None
     if not args.no_cpu_baseline:
@@ -318,13 +319,15 @@ def run_gpu(args):
             "workload": workload_name(args.workload, w),
             "n": n, "edges_drawn": E, "undirected_edges": mu, "arcs": m, "kmax": int(kmax.item()),
             "rounds": st["rounds"], "empty_rounds": st["empty_rounds"], "grid": st["grid"],
+            "sync_mode": st["sync_mode"], "slice_arcs": st["slice_arcs"], "passes": st["passes"],
+            "barriers": st["barriers"],
             "l2": "inputs larger than L2 and a 258 MB buffer written between timed steps",
             "csr_build_ms": min(csr_ms), "parallelism": "replicas" if ws > 1 else "single GPU",
             "wall_s": wall,
         },
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                      "frac": achieved / peak, "traffic": traffic, "peak_kind": peak_kind,
-                     "algorithmic_bytes": bmin, "kernel": "peel_persistent"},
+                     "algorithmic_bytes": bmin, "kernel": kname},
         "e2e": e2e,
         "gpu_launches": args.steps,
         "cpu_baseline": cpu,
@@ -616,10 +619,14 @@ def run_served(args):
     print(json.dumps(out), flush=True)
 
 
-def kernel_revision() -> str:
-    """Hash of the peel kernel source, to tie recorded ncu traffic to it."""
+# single-graph schedule (stats "sync_mode") -> (kernel name, its source file)
+PEEL_KERNELS = {1: ("peel_persistent", "peel.cu"), 2: ("peel_bsp", "peel_bsp.cu")}
+
+
+def kernel_revision(src: str = "peel_bsp.cu") -> str:
+    """Hash of a peel kernel source, to tie recorded ncu traffic to it."""
     import hashlib
-    p = os.path.join(ROOT, "paper_2502_08042_gb300", "csrc", "peel.cu")
+    p = os.path.join(ROOT, "paper_2502_08042_gb300", "csrc", src)
     with open(p, "rb") as f:
         return hashlib.sha1(f.read()).hexdigest()[:12]
 

@@ -56,15 +56,20 @@ typedef enum {
 /* Tunables (kcore_set_option). Defaults are chosen per device at kcore_create
  * and may be overridden; kcore_get_option reads them back. */
 typedef enum {
-  KCORE_OPT_SYNC_MODE = 0,     /* 0 auto, 1 persistent kernel (device-wide counters), 2 graph relaunch */
+  KCORE_OPT_SYNC_MODE = 0,     /* single-graph peel schedule: 0 auto (= 2); 1 asynchronous
+                                  persistent kernel (rounds end on device-wide counters, work
+                                  overlaps across subrounds); 2 bulk-synchronous persistent kernel
+                                  (a bounded grid barrier after the scan and after every subround) */
   KCORE_OPT_CTAS_PER_SM = 1,   /* CTAs per SM of the persistent kernel (0 = occupancy maximum) */
-  KCORE_OPT_SLICE_ARCS = 2,    /* arcs per work item (16 .. 2^20): longer lists are split in slices */
+  KCORE_OPT_SLICE_ARCS = 2,    /* arcs per work item (16 .. 2^20; 0 = auto: 128 in mode 2, 512 in
+                                  mode 1): longer lists are split in slices */
   KCORE_OPT_LOCAL_QUEUE = 3,   /* per-warp local queue capacity (vertices), 0 disables it */
   KCORE_OPT_TIMEOUT_MS = 4,    /* limit for every device-side wait, milliseconds */
   KCORE_OPT_MIN_CTAS = 5,      /* lower bound of the grid for small graphs */
   KCORE_OPT_VERTICES_PER_CTA = 6, /* grid sizing: about one CTA per this many vertices+arcs/8 */
   KCORE_OPT_TEST_STALL = 7,      /* test hook, default 0: 1 makes CTA 0 withhold its round-1
-                                    completion token, so every device wait must run out its
+                                    completion token (mode 1) or its arrival at the first grid
+                                    barrier (mode 2), so every device wait must run out its
                                     time limit and the call ends with KCORE_ERR_TIMEOUT */
   KCORE_OPT_TRACE = 8,           /* 1 records a per-round timeline (kcore_get_trace) */
   KCORE_OPT_IDLE_SLEEP_NS = 9,   /* nanosleep of a warp waiting for work (0 .. 100000) */
@@ -73,7 +78,11 @@ typedef enum {
   KCORE_OPT_BATCH_SMEM_VERTICES = 12, /* batched peel: graphs with at most this many vertices keep
                                          their induced degrees in shared memory (-1 = as many as
                                          fit with the CTAs per SM below) */
-  KCORE_OPT_BATCH_CTAS_PER_SM = 13    /* batched peel: resident CTAs per SM (0 = occupancy limit) */
+  KCORE_OPT_BATCH_CTAS_PER_SM = 13,   /* batched peel: resident CTAs per SM (0 = occupancy limit) */
+  KCORE_OPT_LOCAL_BATCHES = 14        /* mode 2: local-queue batches a warp may run after each chunk it
+                                         claims (0 .. 2^20, 0 = no limit); the rest of its local queue
+                                         then goes to the work queue, so a large cascade is shared by
+                                         all warps in the next subround instead of one warp */
 } kcore_option;
 
 /* Counters of the last decomposition (valid after kcore_sync_status). */
@@ -85,8 +94,13 @@ typedef struct {
   int64_t scanned;         /* sum over rounds of the active-set size scanned (Theorem 1) */
   int64_t kmax;            /* largest coreness */
   int64_t grid;            /* CTAs of the persistent kernel */
-  int64_t sync_mode;       /* mode actually used: 1 persistent, 2 graph relaunch */
-  int64_t reserved[8];
+  int64_t sync_mode;       /* mode actually used: 1 asynchronous, 2 bulk-synchronous */
+  int64_t passes;          /* bulk-synchronous mode: subround passes over the work queue */
+  int64_t barriers;        /* bulk-synchronous mode: grid barriers taken */
+  int64_t batch_block;     /* batched calls: threads per CTA used */
+  int64_t batch_smem_vertices; /* batched calls: largest graph kept in shared memory */
+  int64_t slice_arcs;      /* arcs per work item the last decomposition used */
+  int64_t reserved[3];
 } kcore_stats;
 
 /* Creates a handle on `device` (CUDA ordinal). The handle owns a workspace

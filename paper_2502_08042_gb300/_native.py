@@ -97,8 +97,9 @@ c_i64, c_i32, c_p, c_sz = ctypes.c_int64, ctypes.c_int32, ctypes.c_void_p, ctype
 
 class Stats(ctypes.Structure):
     _fields_ = [(name, c_i64) for name in ("rounds", "empty_rounds", "items", "local_items",
-                                           "scanned", "kmax", "grid", "sync_mode")] + \
-               [("reserved", c_i64 * 8)]
+                                           "scanned", "kmax", "grid", "sync_mode", "passes",
+                                           "barriers", "batch_block", "batch_smem_vertices", "slice_arcs")] + \
+               [("reserved", c_i64 * 3)]
 
 
 # Every exported symbol of include/kcore.h with its ctypes signature.

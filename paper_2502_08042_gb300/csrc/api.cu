@@ -17,11 +17,12 @@ struct kcore_ctx {
   int device = 0;
   int sms = 0;
   int max_ctas_per_sm = 0;
+  int bsp_max_ctas_per_sm = 0;
   void* ws = nullptr;
   size_t ws_bytes = 0;
   bool ws_external = false;
   std::string err;
-  int64_t opt[14] = {0, 0, 512, 32, 2000, 1, 2048, 0, 0, 192, 64, 1024, -1, 0};  // indexed by kcore_option
+  int64_t opt[15] = {0, 0, 0, 32, 2000, 1, 2048, 0, 0, 192, 64, 1024, -1, 0, 8};  // indexed by kcore_option
   cudaStream_t last_stream = nullptr;
   bool pending = false;
   kc::PeelCtl* last_ctl = nullptr;
@@ -33,6 +34,7 @@ struct kcore_ctx {
   kcore_stats stats{};
   int last_grid = 0;
   int last_mode = 0;
+  int last_slice = 0;
   // device staging for kcore_decompose_host
   void* e2e = nullptr;
   size_t e2e_bytes = 0;
@@ -72,7 +74,7 @@ long long isqrt_ll(long long m) {
 }
 
 struct PeelLayout {
-  size_t deg, a0, a1, q, rounds, ctl, trace, total;
+  size_t deg, a0, a1, q, rounds, claims, ctl, trace, total;
   long long qcap;
   int max_rounds;
 };
@@ -80,7 +82,8 @@ struct PeelLayout {
 // Workspace of the single-graph peel: d~[n], two active lists [n], the work
 // queue (every vertex pushes ceil(deg/slice) slices once: <= n + m/slice), the
 // per-round records (levels <= k_max+1 <= sqrt(m)+1, each followed by at most
-// one empty speculative level) and the control block.
+// one empty speculative level), the claim counters of the bulk-synchronous
+// mode and the control block. Everything below `deg` is zeroed per call.
 PeelLayout peel_layout(long long n, long long m, int slice) {
   PeelLayout L{};
   L.qcap = n + (m + slice - 1) / slice + 1;
@@ -92,6 +95,8 @@ PeelLayout peel_layout(long long n, long long m, int slice) {
   off = align_up(off + sizeof(kc::PeelCtl), 256);
   L.rounds = off;
   off = align_up(off + sizeof(kc::RoundRec) * (size_t)L.max_rounds, 256);
+  L.claims = off;
+  off = align_up(off + sizeof(kc::ClaimSet) * kc::kClaimRing, 256);
   L.deg = off;
   off = align_up(off + 4 * (size_t)n, 256);
   L.a0 = off;
@@ -104,6 +109,13 @@ PeelLayout peel_layout(long long n, long long m, int slice) {
   off = align_up(off + 8 * (size_t)kc::kTraceFields * (size_t)L.max_rounds, 256);
   L.total = off;
   return L;
+}
+
+// Schedule and slice length a call on this handle uses (option value 0 = auto).
+int effective_mode(const kcore_ctx* h) { return h->opt[KCORE_OPT_SYNC_MODE] == 1 ? 1 : 2; }
+int effective_slice(const kcore_ctx* h) {
+  if (h->opt[KCORE_OPT_SLICE_ARCS] > 0) return (int)h->opt[KCORE_OPT_SLICE_ARCS];
+  return effective_mode(h) == 2 ? 128 : 512;
 }
 
 kcore_status ensure_ws(kcore_ctx* h, size_t need) {
@@ -150,7 +162,8 @@ kcore_status kcore_create(kcore_handle* out, int device) {
   }
   cudaDeviceGetAttribute(&h->sms, cudaDevAttrMultiProcessorCount, device);
   h->max_ctas_per_sm = kc::peel_max_ctas_per_sm();
-  if (h->max_ctas_per_sm <= 0 || h->sms <= 0) {
+  h->bsp_max_ctas_per_sm = kc::bsp_max_ctas_per_sm();
+  if (h->max_ctas_per_sm <= 0 || h->bsp_max_ctas_per_sm <= 0 || h->sms <= 0) {
     delete h;
     cudaGetLastError();
     return KCORE_ERR_CUDA;
@@ -176,7 +189,7 @@ kcore_status kcore_destroy(kcore_handle h) {
 const char* kcore_last_error(kcore_handle h) { return h ? h->err.c_str() : "null handle"; }
 
 kcore_status kcore_set_option(kcore_handle h, kcore_option opt, int64_t value) {
-  if (!h || (int)opt < 0 || (int)opt > 13) return KCORE_ERR_INVALID;
+  if (!h || (int)opt < 0 || (int)opt > 14) return KCORE_ERR_INVALID;
   switch (opt) {
     case KCORE_OPT_BATCH_BLOCK:
       if (value != 256 && value != 512 && value != 1024)
@@ -187,6 +200,9 @@ kcore_status kcore_set_option(kcore_handle h, kcore_option opt, int64_t value) {
       break;
     case KCORE_OPT_BATCH_CTAS_PER_SM:
       if (value < 0 || value > 8) return fail(h, KCORE_ERR_INVALID, "batch CTAs per SM in [0, 8]");
+      break;
+    case KCORE_OPT_LOCAL_BATCHES:
+      if (value < 0 || value > (1 << 20)) return fail(h, KCORE_ERR_INVALID, "local batches in [0, 2^20]");
       break;
     case KCORE_OPT_IDLE_SLEEP_NS:
     case KCORE_OPT_POLL_SLEEP_NS:
@@ -206,8 +222,8 @@ kcore_status kcore_set_option(kcore_handle h, kcore_option opt, int64_t value) {
         return fail(h, KCORE_ERR_INVALID, "CTAs per SM above the occupancy limit");
       break;
     case KCORE_OPT_SLICE_ARCS:
-      if (value < kc::kMinSlice || value > (1 << 20))
-        return fail(h, KCORE_ERR_INVALID, "slice must be in [16, 2^20]");
+      if (value != 0 && (value < kc::kMinSlice || value > (1 << 20)))
+        return fail(h, KCORE_ERR_INVALID, "slice must be 0 (auto) or in [16, 2^20]");
       break;
     case KCORE_OPT_LOCAL_QUEUE:
       if (value < 0 || value > kc::kLocalQueueMax)
@@ -228,14 +244,14 @@ kcore_status kcore_set_option(kcore_handle h, kcore_option opt, int64_t value) {
 }
 
 kcore_status kcore_get_option(kcore_handle h, kcore_option opt, int64_t* value) {
-  if (!h || !value || (int)opt < 0 || (int)opt > 13) return KCORE_ERR_INVALID;
+  if (!h || !value || (int)opt < 0 || (int)opt > 14) return KCORE_ERR_INVALID;
   *value = h->opt[opt];
   return KCORE_OK;
 }
 
 kcore_status kcore_workspace_size(kcore_handle h, int64_t n, int64_t m, size_t* bytes) {
   if (!h || !bytes || n < 0 || m < 0 || n > INT32_MAX - 1) return KCORE_ERR_INVALID;
-  *bytes = peel_layout(n, m, (int)h->opt[KCORE_OPT_SLICE_ARCS]).total;
+  *bytes = peel_layout(n, m, effective_slice(h)).total;
   return KCORE_OK;
 }
 
@@ -276,7 +292,7 @@ kcore_status kcore_decompose(kcore_handle h, int64_t n, int64_t m, const int64_t
     if (e != cudaSuccess) return cuda_fail(h, e, "cudaMemsetAsync");
     return KCORE_OK;
   }
-  const int slice = (int)h->opt[KCORE_OPT_SLICE_ARCS];
+  const int slice = effective_slice(h);
   PeelLayout L = peel_layout(n, m, slice);
   kcore_status st = ensure_ws(h, L.total);
   if (st != KCORE_OK) return st;
@@ -305,8 +321,15 @@ kcore_status kcore_decompose(kcore_handle h, int64_t n, int64_t m, const int64_t
   a.poll_sleep_ns = (int)h->opt[KCORE_OPT_POLL_SLEEP_NS];
   a.inject_stall = (int)h->opt[KCORE_OPT_TEST_STALL];
   a.trace = h->opt[KCORE_OPT_TRACE] ? (unsigned long long*)(ws + L.trace) : nullptr;
+  a.claims = (kc::ClaimSet*)(ws + L.claims);
+  a.local_batches = h->opt[KCORE_OPT_LOCAL_BATCHES] > 0 ? (int)h->opt[KCORE_OPT_LOCAL_BATCHES] : INT32_MAX;
 
-  int per_sm = h->opt[KCORE_OPT_CTAS_PER_SM] > 0 ? (int)h->opt[KCORE_OPT_CTAS_PER_SM] : h->max_ctas_per_sm;
+  const int mode = effective_mode(h);
+  if (mode == 2 && m >= ((int64_t)1 << 40))
+    return fail(h, KCORE_ERR_INVALID, "the bulk-synchronous mode takes at most 2^40 arcs");
+  const int mode_max = mode == 2 ? h->bsp_max_ctas_per_sm : h->max_ctas_per_sm;
+  int per_sm = h->opt[KCORE_OPT_CTAS_PER_SM] > 0 ? (int)h->opt[KCORE_OPT_CTAS_PER_SM] : mode_max;
+  per_sm = std::min(per_sm, mode_max);
   long long gmax = (long long)h->sms * per_sm;
   long long work = n + m / 8;
   long long want = (work + h->opt[KCORE_OPT_VERTICES_PER_CTA] - 1) / h->opt[KCORE_OPT_VERTICES_PER_CTA];
@@ -316,16 +339,20 @@ kcore_status kcore_decompose(kcore_handle h, int64_t n, int64_t m, const int64_t
 
   cudaError_t e;
   if ((e = cudaMemsetAsync(ws, 0, L.deg, stream)) != cudaSuccess) return cuda_fail(h, e, "memset ctl");
-  if ((e = cudaMemsetAsync(ws + L.q, 0xff, 8 * (size_t)L.qcap, stream)) != cudaSuccess)
+  // the asynchronous mode polls queue slots for the item tag; the
+  // bulk-synchronous mode reads only slots written before its barrier
+  if (mode == 1 && (e = cudaMemsetAsync(ws + L.q, 0xff, 8 * (size_t)L.qcap, stream)) != cudaSuccess)
     return cuda_fail(h, e, "memset queue");
   if (a.trace && (e = cudaMemsetAsync(a.trace, 0, L.total - L.trace, stream)) != cudaSuccess)
     return cuda_fail(h, e, "memset trace");
-  if ((e = kc::peel_launch(a, (int)grid, stream)) != cudaSuccess) return cuda_fail(h, e, "peel launch");
+  e = mode == 2 ? kc::bsp_launch(a, (int)grid, stream) : kc::peel_launch(a, (int)grid, stream);
+  if (e != cudaSuccess) return cuda_fail(h, e, "peel launch");
   h->last_ctl = a.ctl;
   h->last_trace = a.trace;
   h->last_max_rounds = L.max_rounds;
   h->last_grid = (int)grid;
-  h->last_mode = 1;
+  h->last_mode = mode;
+  h->last_slice = slice;
   return KCORE_OK;
 }
 
@@ -534,8 +561,8 @@ kcore_status kcore_sync_status(kcore_handle h) {
     h->last_batch_status = nullptr;
     if (e != cudaSuccess) return cuda_fail(h, e, "read status");
     h->stats.grid = h->last_batch_grid;
-    h->stats.reserved[0] = h->last_batch_block;
-    h->stats.reserved[1] = h->last_batch_smem_vertices;
+    h->stats.batch_block = h->last_batch_block;
+    h->stats.batch_smem_vertices = h->last_batch_smem_vertices;
     if (bs[0] == kc::ST_NOT_SIMPLE) {
       long long val = (long long)(unsigned)bs[2] | ((long long)bs[3] << 32);
       return fail(h, KCORE_ERR_NOT_SIMPLE,
@@ -565,6 +592,9 @@ kcore_status kcore_sync_status(kcore_handle h) {
   h->stats.kmax = c.kmax;
   h->stats.grid = h->last_grid;
   h->stats.sync_mode = h->last_mode;
+  h->stats.passes = c.passes;
+  h->stats.barriers = c.barriers;
+  h->stats.slice_arcs = h->last_slice;
   switch (c.status) {
     case 0:
       return KCORE_OK;
@@ -584,7 +614,9 @@ kcore_status kcore_get_trace(kcore_handle h, uint64_t* out, int64_t max_rounds, 
   *rounds_out = 0;
   if (!h->last_trace) return fail(h, KCORE_ERR_INVALID, "the last decomposition ran without tracing");
   DeviceGuard g(h->device);
-  int64_t r = std::min<int64_t>(std::min<int64_t>(max_rounds, h->stats.rounds), h->last_max_rounds);
+  // the bulk-synchronous mode records one entry per non-empty level
+  const int64_t have = h->last_mode == 2 ? h->stats.rounds - h->stats.empty_rounds : h->stats.rounds;
+  int64_t r = std::min<int64_t>(std::min<int64_t>(max_rounds, have), h->last_max_rounds);
   if (r > 0) {
     cudaError_t e = cudaMemcpy(out, h->last_trace, sizeof(uint64_t) * kc::kTraceFields * (size_t)r,
                                cudaMemcpyDeviceToHost);

@@ -48,7 +48,28 @@ struct PeelCtl {
   unsigned long long items, local_items;
   long long rounds, empty_rounds, scanned, kmax;
   char pad3[80];
+  // bulk-synchronous mode: grid barrier (arrivals, generation), queue tail,
+  // subround passes and barriers taken
+  unsigned long long bar_count;
+  char pad4[120];
+  unsigned long long bar_gen;
+  char pad5[120];
+  unsigned long long qtail;
+  char pad6[120];
+  long long passes, barriers;
+  char pad7[112];
 };
+
+// Claim counters of one bulk-synchronous phase: the pass's queue range is cut
+// into kClaimParts partitions, each with its own counter on its own line.
+constexpr int kClaimParts = 32;
+struct ClaimSet {
+  struct {
+    unsigned long long next;
+    char pad[120];
+  } part[kClaimParts];
+};
+constexpr int kClaimRing = 3;  // phase p uses set p % 3
 
 struct PeelArgs {
   long long n, m;
@@ -74,6 +95,8 @@ struct PeelArgs {
   int poll_sleep_ns;  // sleep of the CTA's round poller between polls
   int inject_stall;
   unsigned long long* trace;  // optional: kTraceFields words per round (nullptr = off)
+  ClaimSet* claims;           // bulk-synchronous mode: kClaimRing sets (zeroed)
+  int local_batches;          // bulk-synchronous mode: local batches per claimed chunk
 };
 
 // Per-round trace record (KCORE_OPT_TRACE): globaltimer at round start (CTA 0),
@@ -87,5 +110,10 @@ constexpr int kTraceFields = 14;
 int peel_max_ctas_per_sm();
 int peel_block_size();
 cudaError_t peel_launch(const PeelArgs& args, int grid, cudaStream_t stream);
+
+// Bulk-synchronous mode (grid barrier between scan and subround phases).
+int bsp_max_ctas_per_sm();
+int bsp_block_size();
+cudaError_t bsp_launch(const PeelArgs& args, int grid, cudaStream_t stream);
 
 }  // namespace kc

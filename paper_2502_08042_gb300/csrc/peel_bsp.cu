@@ -1,0 +1,578 @@
+// Single-graph k-core peel, bulk-synchronous mode: one persistent cooperative
+// kernel whose phases are separated by a hand-written, bounded grid barrier.
+//
+// Algorithm 1's rounds with the online Peel of Algorithm 3, phase by phase:
+//   scan   - the active list is compacted to the vertices above the level
+//            being tried (k = previous level + 1) while the vertices sitting
+//            exactly at k are appended to the work queue as slices of at most
+//            `slice` arcs and get coreness k (frontier extraction and active-set
+//            refine, fused; Theorem 1 bounds the summed list lengths). The
+//            minimum induced degree of the kept vertices rides along: if level
+//            k is empty, it is the next non-empty level and a second scan
+//            collects its vertices.
+//   pass   - one subround over the queue range appended before it: warps claim
+//            up to 32 items at a time and process their arcs edge-balanced. A
+//            decrement of a neighbour above k that returns k+1 is the crossing
+//            of Algorithm 3: the neighbour gets coreness k and is processed by
+//            the same warp in the same pass if its list fits one slice and the
+//            warp's local queue has room (the local FIFO of vertical
+//            granularity control, Sec. 4.2); otherwise its slices go to the
+//            queue for the next pass. The level ends with a pass that appends
+//            nothing.
+// The queue range of a pass is fixed while it runs, so claims are plain
+// fetch-and-adds on counters spread over 32 partitions, pushes need no fences
+// and the pass ends at the barrier. A queue item is an arc range (first arc,
+// length), so processing it needs no offset lookup. Each phase counts its own
+// appends, which land after everything appended before the phase, so the next
+// range is known to every CTA after the barrier. Every vertex is appended at
+// most once over the whole run, so the queue never wraps. A warp runs at most
+// `local_batches` batches from its local queue per chunk it claims and then
+// moves the rest to the queue: a large cascade is shared by all warps in the
+// next pass instead of being walked by the warp that started it. Every wait is
+// bounded by the handle's time limit (KCORE_ERR_TIMEOUT).
+#include <climits>
+
+#include "kcore_device.cuh"
+#include "kcore_peel.h"
+
+namespace kc {
+
+namespace {
+
+constexpr int kBlock = 512;
+constexpr int kWarps = kBlock / kWarp;
+constexpr int kTile = 4;   // active-list entries per thread per scan tile
+constexpr int kIlp = 8;    // arcs per lane in flight
+constexpr int kTake = 32;  // most queue items per claim
+constexpr int kLenShift = 40;  // item = first arc | length << 40
+constexpr unsigned long long kArcMask = (1ull << kLenShift) - 1;
+constexpr unsigned long long kAbort = 1ull << 62;  // barrier word: a status was raised
+
+struct Shared {
+  int excl[kWarps][kWarp];
+  long long a0[kWarps][kWarp];
+  unsigned long long lq[kWarps][kLocalQueueMax];
+  int lqn[kWarps];
+  unsigned long long part[kWarps];
+  unsigned long long base_a, base_q;
+  unsigned long long red_found[kWarps];
+  int red_min[kWarps];
+  int flag;
+};
+
+// Records the first error and makes every CTA leave at its next barrier.
+__device__ __forceinline__ void raise_status(const PeelArgs& a, int code) {
+  atomicCAS(&a.ctl->status, 0, code);
+  atomicOr(&a.ctl->bar_count, kAbort);
+}
+
+__device__ __forceinline__ unsigned long long make_item(long long a0, long long len) {
+  return (unsigned long long)a0 | ((unsigned long long)len << kLenShift);
+}
+
+// Grid barrier on one word: the arrivals (release adds) and the abort bit.
+// Phase g is complete when (g + 1) * gridDim.x arrivals are counted; the
+// acquire load that sees them makes every CTA's writes of the phase visible.
+// Waiters give up after timeout_ns without progress (a warp running a long
+// local chain ticks ctl->progress). Returns false when a status was raised
+// before the barrier completed, or when the wait gave up.
+__device__ bool grid_barrier(const PeelArgs& a, Shared& sh, unsigned long long& gen) {
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    int ok = 1;
+    const unsigned long long target = (gen + 1) * gridDim.x;
+    __threadfence();
+    if (!(a.inject_stall && blockIdx.x == 0 && gen == 0))
+      asm volatile("red.release.gpu.global.add.u64 [%0], 1;" ::"l"(&a.ctl->bar_count) : "memory");
+    uint64_t t0 = 0;
+    unsigned long long pg = 0;
+    for (unsigned spins = 0;; spins++) {
+      const unsigned long long v = ld_acquire_u64(&a.ctl->bar_count);
+      if (v & kAbort) {
+        ok = 0;
+        break;
+      }
+      if (v >= target) break;
+      if ((spins & 31) == 0) {
+        const uint64_t now = globaltimer_ns();
+        const unsigned long long p2 = ld_relaxed_u64(&a.ctl->progress);
+        if (spins == 0 || p2 != pg) {
+          pg = p2;
+          t0 = now;
+        } else if (now - t0 > a.timeout_ns) {
+          raise_status(a, ST_TIMEOUT);
+          ok = 0;
+          break;
+        }
+      }
+      __nanosleep(a.poll_sleep_ns);
+    }
+    gen++;
+    sh.flag = ok;
+  }
+  __syncthreads();
+  return sh.flag != 0;
+}
+
+struct ScanOut {
+  unsigned long long found;
+  int dmin;
+};
+
+// Scan of active-list entries [lo, hi) by one CTA: entries with d~ > keep_above
+// go to Aout (their minimum d~ is returned), entries with d~ == take_at get
+// coreness take_at and their slices are appended to the queue after position
+// qbase (count in R->tail). With Ain == nullptr the list is 0..n-1 and d~ is
+// initialised from the offsets.
+__device__ ScanOut scan_range(const PeelArgs& a, Shared& sh, RoundRec* R, unsigned long long qbase,
+                              const int* Ain, int* Aout, long long lo, long long hi, int keep_above,
+                              int take_at) {
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  unsigned long long found = 0;
+  int dmin = INT_MAX;
+  for (long long tile = lo; tile < hi; tile += (long long)kBlock * kTile) {
+    int v[kTile];
+    int keep[kTile];
+    int nsl[kTile];
+    long long e0[kTile], e1[kTile];
+    int cs = 0, ps = 0;
+#pragma unroll
+    for (int q = 0; q < kTile; q++) {
+      const long long i = tile + (long long)q * kBlock + tid;
+      v[q] = -1;
+      keep[q] = 0;
+      nsl[q] = 0;
+      e0[q] = e1[q] = 0;
+      if (i >= hi) continue;
+      const int x = Ain ? __ldcg(Ain + i) : (int)i;
+      if ((unsigned)x >= (unsigned)a.n) {
+        raise_status(a, ST_NOT_SIMPLE);
+        continue;
+      }
+      int d;
+      if (!Ain) {
+        e0[q] = a.off[x];
+        e1[q] = a.off[x + 1];
+        if (e0[q] < 0 || e1[q] < e0[q] || e1[q] > a.m || e1[q] - e0[q] >= a.n) {
+          raise_status(a, ST_NOT_SIMPLE);  // malformed offsets: no arc of x is ever read
+          e0[q] = e1[q] = 0;
+        }
+        d = (int)(e1[q] - e0[q]);
+        a.deg[x] = d;
+      } else {
+        d = __ldcg(a.deg + x);
+      }
+      v[q] = x;
+      if (d > keep_above) {
+        keep[q] = 1;
+        dmin = min(dmin, d);
+      }
+      if (d == take_at) {
+        found++;
+        a.core[x] = take_at;
+        if (Ain) {
+          e0[q] = a.off[x];
+          e1[q] = a.off[x + 1];
+        }
+        nsl[q] = (int)((e1[q] - e0[q] + a.slice - 1) / a.slice);
+      }
+      cs += keep[q];
+      ps += nsl[q];
+    }
+    // block-wide exclusive offsets of (kept, slices), one atomic pair per tile
+    const unsigned long long packed = ((unsigned long long)(unsigned)ps << 32) | (unsigned)cs;
+    const unsigned long long incl = warp_incl_scan(packed, lane);
+    if (lane == 31) sh.part[warp] = incl;
+    __syncthreads();
+    if (warp == 0) {
+      const unsigned long long x = lane < kWarps ? sh.part[lane] : 0;
+      const unsigned long long xi = warp_incl_scan(x, lane);
+      if (lane < kWarps) sh.part[lane] = xi - x;
+      if (lane == kWarps - 1) {
+        const unsigned long long tc = xi & 0xffffffffull, tq = xi >> 32;
+        sh.base_a = tc ? atomicAdd(&R->alen, tc) : 0;
+        unsigned long long bq = qbase + (tq ? atomicAdd(&R->tail, tq) : 0);
+        if (bq + tq > (unsigned long long)a.qcap) {
+          raise_status(a, ST_CAPACITY);
+          bq = ~0ull;
+        }
+        sh.base_q = bq;
+      }
+    }
+    __syncthreads();
+    const unsigned long long ex = sh.part[warp] + incl - packed;
+    unsigned long long pa = sh.base_a + (ex & 0xffffffffull);
+    unsigned long long pq = sh.base_q + (ex >> 32);
+    const bool qok = sh.base_q != ~0ull;
+#pragma unroll
+    for (int q = 0; q < kTile; q++) {
+      if (keep[q]) Aout[pa++] = v[q];
+      if (nsl[q] && qok)
+        for (long long s0 = e0[q]; s0 < e1[q]; s0 += a.slice)
+          a.Q[pq++] = make_item(s0, min((long long)a.slice, e1[q] - s0));
+    }
+    __syncthreads();
+  }
+  const unsigned long long fw = warp_sum(found);
+  const int mw = warp_min(dmin);
+  if (lane == 0) {
+    sh.red_found[warp] = fw;
+    sh.red_min[warp] = mw;
+  }
+  __syncthreads();
+  ScanOut o{0, INT_MAX};
+  if (tid == 0) {
+    for (int w = 0; w < kWarps; w++) {
+      o.found += sh.red_found[w];
+      o.dmin = min(o.dmin, sh.red_min[w]);
+    }
+  }
+  return o;
+}
+
+// Context of one pass: where its appends go and its level.
+struct PassCtx {
+  RoundRec* R;              // R->tail counts this phase's appends
+  unsigned long long qbase; // appends start here
+  int t;
+};
+
+// Appends `cnt` items per lane (lane-owned arc ranges [e0, e1) cut in
+// slices) to the queue.
+__device__ __forceinline__ void append_ranges(const PeelArgs& a, const PassCtx& pc, int cnt, long long e0,
+                                              long long e1, int lane) {
+  const int incl = warp_incl_scan(cnt, lane);
+  const int tot = __shfl_sync(kFull, incl, 31);
+  if (tot == 0) return;
+  unsigned long long base = 0;
+  if (lane == 31) base = pc.qbase + atomicAdd(&pc.R->tail, (unsigned long long)tot);
+  base = __shfl_sync(kFull, base, 31);
+  if (base + (unsigned long long)tot > (unsigned long long)a.qcap) {
+    if (lane == 0) raise_status(a, ST_CAPACITY);
+    return;
+  }
+  unsigned long long p = base + (unsigned long long)(incl - cnt);
+  for (long long s0 = e0; s0 < e1 && cnt > 0; s0 += a.slice) a.Q[p++] = make_item(s0, min((long long)a.slice, e1 - s0));
+}
+
+// The vertices u of the lanes with `flag` crossed to the current level (their
+// coreness is set): one-slice lists go to the warp's local queue while it has
+// room, the rest go to the queue as slices for the next pass.
+__device__ __forceinline__ void push_crossed(const PeelArgs& a, Shared& sh, const PassCtx& pc, bool flag, int u,
+                                             int warp, int lane) {
+  long long e0 = 0, e1 = 0;
+  int nsl = 0;
+  if (flag) {
+    e0 = a.off[u];
+    e1 = a.off[u + 1];
+    nsl = (int)((e1 - e0 + a.slice - 1) / a.slice);
+  }
+  const bool one = flag && nsl == 1;
+  const unsigned om = __ballot_sync(kFull, one);
+  const int lqn = sh.lqn[warp];
+  const int room = max(a.lq_cap - lqn, 0);
+  const int rank = __popc(om & lanemask_lt());
+  const bool local = one && rank < room;
+  if (local) sh.lq[warp][lqn + rank] = make_item(e0, e1 - e0);
+  __syncwarp();
+  if (lane == 0) sh.lqn[warp] = lqn + min(__popc(om), room);
+  __syncwarp();
+  append_ranges(a, pc, (flag && !local) ? nsl : 0, e0, e1, lane);
+}
+
+// Arcs of the items held by lanes < c, spread evenly over the warp.
+__device__ void process_items(const PeelArgs& a, Shared& sh, const PassCtx& pc, unsigned long long item, int c,
+                              int warp, int lane) {
+  const int t = pc.t;
+  const long long a0 = lane < c ? (long long)(item & kArcMask) : 0;
+  const int len = lane < c ? (int)(item >> kLenShift) : 0;
+  const int incl = warp_incl_scan(len, lane);
+  const int total = __shfl_sync(kFull, incl, 31);
+  sh.excl[warp][lane] = incl - len;
+  sh.a0[warp][lane] = a0;
+  __syncwarp();
+  const int* excl = sh.excl[warp];
+  for (int base = 0; base < total; base += kWarp * kIlp) {
+    int u[kIlp];
+    int j = base + lane;
+    int lo = 0, hi = c;  // last item whose first arc is <= j
+    while (lo < hi) {
+      const int mid = (lo + hi) >> 1;
+      if (excl[mid] <= j) lo = mid + 1;
+      else hi = mid;
+    }
+    int idx = lo > 0 ? lo - 1 : 0;
+#pragma unroll
+    for (int q = 0; q < kIlp; q++, j += kWarp) {
+      u[q] = -1;
+      if (j < total) {
+        while (idx + 1 < c && excl[idx + 1] <= j) idx++;
+        const long long arc = sh.a0[warp][idx] + (j - excl[idx]);
+        const int x = arc < a.m ? ld_stream_s32(a.adj + arc) : -1;
+        if ((unsigned)x < (unsigned)a.n) u[q] = x;
+        else raise_status(a, ST_NOT_SIMPLE);
+      }
+    }
+    // In a batch of many arcs, reading d~ first spares the atomics on
+    // neighbours at or below the level. A batch of one iteration is bound by
+    // its chain of dependent accesses instead: it decrements unconditionally.
+    // That is safe, as a neighbour at or below k never returns k + 1 and its
+    // d~ is not read again.
+    int dq[kIlp];
+    if (total > kWarp * kIlp) {
+#pragma unroll
+      for (int q = 0; q < kIlp; q++) dq[q] = u[q] >= 0 ? __ldcg(a.deg + u[q]) : INT_MIN;
+    } else {
+#pragma unroll
+      for (int q = 0; q < kIlp; q++) dq[q] = u[q] >= 0 ? INT_MAX : INT_MIN;
+    }
+    unsigned cross = 0;
+#pragma unroll
+    for (int q = 0; q < kIlp; q++)
+      if (dq[q] > t && atomicSub(a.deg + u[q], 1) == t + 1) cross |= 1u << q;
+    if (__any_sync(kFull, cross != 0)) {
+#pragma unroll
+      for (int q = 0; q < kIlp; q++) {
+        const bool f = (cross >> q) & 1u;
+        if (f) a.core[u[q]] = t;
+        if (__any_sync(kFull, f)) push_crossed(a, sh, pc, f, u[q], warp, lane);
+      }
+    }
+  }
+  __syncwarp();
+}
+
+// Runs up to `budget` batches from the warp's local queue (vertices that
+// crossed during this pass), then moves what is left to the queue.
+__device__ void drain_local(const PeelArgs& a, Shared& sh, const PassCtx& pc, int warp, int lane,
+                            long long& local_items, unsigned& local_batches) {
+  for (int b = 0;; b++) {
+    const int lqn = sh.lqn[warp];
+    if (lqn == 0) return;
+    if (b >= a.local_batches) {
+      // spill: one item per queued vertex
+      __syncwarp();
+      if (lane == 0) sh.lqn[warp] = 0;
+      unsigned long long base = 0;
+      if (lane == 0) base = pc.qbase + atomicAdd(&pc.R->tail, (unsigned long long)lqn);
+      base = __shfl_sync(kFull, base, 0);
+      if (base + (unsigned long long)lqn > (unsigned long long)a.qcap) {
+        if (lane == 0) raise_status(a, ST_CAPACITY);
+      } else {
+        for (int i = lane; i < lqn; i += kWarp) a.Q[base + i] = sh.lq[warp][i];
+      }
+      __syncwarp();
+      return;
+    }
+    const int c = min(lqn, kWarp);
+    const unsigned long long item = lane < c ? sh.lq[warp][lqn - c + lane] : 0;
+    __syncwarp();
+    if (lane == 0) sh.lqn[warp] = lqn - c;
+    __syncwarp();
+    process_items(a, sh, pc, item, c, warp, lane);
+    local_items += c;
+    if (lane == 0 && ((++local_batches) & 63) == 0) atomicAdd(&a.ctl->progress, 1ull);
+  }
+}
+
+// One subround: the queue range [qb, qe) is processed once, claimed in chunks
+// of `take` items from kClaimParts partitions (a warp starts in partition
+// gw % kClaimParts and moves on when it is drained).
+__device__ void run_pass(const PeelArgs& a, Shared& sh, const PassCtx& pc, ClaimSet* cs, unsigned long long qb,
+                         unsigned long long qe, long long& items, long long& local_items,
+                         unsigned& local_batches) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const unsigned long long gw = (unsigned long long)blockIdx.x * kWarps + warp;
+  const unsigned long long nw = (unsigned long long)gridDim.x * kWarps;
+  const unsigned long long len = qe - qb;
+  if (len <= nw) {
+    // one item per warp, no claims
+    if (gw < len) {
+      const unsigned long long item = lane == 0 ? __ldcg(a.Q + qb + gw) : 0;
+      process_items(a, sh, pc, item, 1, warp, lane);
+      items += 1;
+      drain_local(a, sh, pc, warp, lane, local_items, local_batches);
+    }
+    return;
+  }
+  unsigned long long take = len / (2 * nw);
+  take = take < 1 ? 1 : (take > (unsigned long long)kTake ? kTake : take);
+  int p = (int)(gw % kClaimParts);
+  for (;;) {
+    const unsigned long long pb = qb + len * p / kClaimParts, pe = qb + len * (p + 1) / kClaimParts;
+    unsigned long long pos = 0;
+    if (lane == 0) pos = pb + atomicAdd(&cs->part[p].next, take);
+    pos = __shfl_sync(kFull, pos, 0);
+    if (pos < pe) {
+      const int c = (int)min(take, pe - pos);
+      const unsigned long long item = lane < c ? __ldcg(a.Q + pos + lane) : 0;
+      process_items(a, sh, pc, item, c, warp, lane);
+      items += c;
+      drain_local(a, sh, pc, warp, lane, local_items, local_batches);
+      continue;
+    }
+    // partition p is drained: look at all partitions at once, move to the
+    // next one (cyclically) that still has items
+    const unsigned long long lb = qb + len * lane / kClaimParts, le = qb + len * (lane + 1) / kClaimParts;
+    const bool open = lb + ld_relaxed_u64(&cs->part[lane].next) < le;
+    const unsigned m = __ballot_sync(kFull, open);
+    if (!m) return;
+    const int s = (p + 1) & 31;
+    const unsigned rot = (m >> s) | (m << ((32 - s) & 31));
+    p = (s + __ffs(rot) - 1) & 31;
+  }
+}
+
+__global__ void __launch_bounds__(kBlock, 2) peel_bsp(PeelArgs a) {
+  __shared__ Shared sh;
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const bool lead = blockIdx.x == 0 && tid == 0;
+  if (lane == 0) sh.lqn[warp] = 0;
+  unsigned long long gen = 0;
+  long long phase = 0;  // RoundRec and ClaimSet (phase % 3) belong to phase `phase`
+  auto reset_next = [&]() {
+    // the records of the next phase were last used two phases ago
+    const int r = (int)((phase + 1) % kClaimRing);
+    if (blockIdx.x == 0 && warp == 0) {
+      a.claims[r].part[lane].next = 0;
+      if (lane == 0) {
+        RoundRec* R = a.rounds + r;
+        R->alen = 0;
+        R->found = 0;
+        R->minkey = 0;
+        R->tail = 0;
+      }
+    }
+  };
+  auto nscan_of = [&](long long len) {
+    long long ns = (len + a.scan_min - 1) / a.scan_min;
+    return ns < 1 ? 1ll : (ns > (long long)gridDim.x ? (long long)gridDim.x : ns);
+  };
+  const int* Acur = nullptr;  // nullptr: the identity list 0..n-1
+  int* Afree = a.A0;
+  long long la = a.n;
+  int tp = -1, kmax = 0;
+  long long levels = 0, empty = 0, scanned = 0, passes = 0, items = 0, local_items = 0;
+  unsigned local_batches = 0;
+  unsigned long long qend = 0;  // items appended by all completed phases
+  for (;;) {
+    // ---- scan: keep d~ > tp+1, take d~ == tp+1
+    const int tk = tp + 1;
+    const uint64_t t_start = lead && a.trace ? globaltimer_ns() : 0;
+    reset_next();
+    RoundRec* R = a.rounds + (phase % kClaimRing);
+    long long nscan = nscan_of(la);
+    if (blockIdx.x < nscan) {
+      const long long lo = la * blockIdx.x / nscan, hi = la * (blockIdx.x + 1) / nscan;
+      const ScanOut o = scan_range(a, sh, R, qend, Acur, Afree, lo, hi, tk, tk);
+      if (tid == 0) {
+        if (o.found) atomicAdd(&R->found, o.found);
+        if (o.dmin != INT_MAX) atomicMax(&R->minkey, INT_MAX - o.dmin);
+      }
+    }
+    if (!grid_barrier(a, sh, gen)) break;
+    phase++;
+    scanned += la;
+    const unsigned long long found = ld_relaxed_u64(&R->found);
+    const long long alen = (long long)ld_relaxed_u64(&R->alen);
+    const int minkey = ld_relaxed_s32(&R->minkey);
+    unsigned long long qb = qend;
+    qend += ld_relaxed_u64(&R->tail);
+    {
+      int* prev = const_cast<int*>(Acur);
+      Acur = Afree;
+      Afree = prev ? prev : a.A1;
+    }
+    const long long la_scanned = la;
+    la = alen;
+    int t = tk;
+    unsigned long long nfound = found;
+    if (!found) {
+      if (alen == 0) break;  // nothing left
+      // level tk is empty: the least induced degree of the kept vertices is the next level
+      empty++;
+      t = INT_MAX - minkey;
+      reset_next();
+      R = a.rounds + (phase % kClaimRing);
+      nscan = nscan_of(la);
+      if (blockIdx.x < nscan) {
+        const long long lo = la * blockIdx.x / nscan, hi = la * (blockIdx.x + 1) / nscan;
+        const ScanOut o = scan_range(a, sh, R, qend, Acur, nullptr, lo, hi, INT_MAX, t);
+        if (tid == 0 && o.found) atomicAdd(&R->found, o.found);
+      }
+      if (!grid_barrier(a, sh, gen)) break;
+      phase++;
+      scanned += la;
+      nfound = ld_relaxed_u64(&R->found);
+      qend += ld_relaxed_u64(&R->tail);
+    }
+    kmax = t;
+    tp = t;
+    levels++;
+    const uint64_t t_scan = lead && a.trace ? globaltimer_ns() : 0;
+    const unsigned long long level_qb = qb;
+    long long level_passes = 0;
+    bool ok = true;
+    // ---- subround passes; with no vertex left above the level nothing can be decremented
+    if (la > 0) {
+      while (qend > qb) {
+        reset_next();
+        RoundRec* P = a.rounds + (phase % kClaimRing);
+        const PassCtx pc{P, qend, t};
+        run_pass(a, sh, pc, a.claims + (phase % kClaimRing), qb, qend, items, local_items, local_batches);
+        if (!(ok = grid_barrier(a, sh, gen))) break;
+        phase++;
+        passes++;
+        level_passes++;
+        qb = qend;
+        qend += ld_relaxed_u64(&P->tail);
+      }
+    } else {
+      qb = qend;
+    }
+    if (lead && a.trace && levels - 1 < a.max_rounds) {
+      unsigned long long* tr = a.trace + (size_t)(levels - 1) * kTraceFields;
+      tr[0] = t_start;
+      tr[1] = t_scan;
+      tr[2] = globaltimer_ns();
+      tr[3] = (unsigned long long)t;
+      tr[4] = (unsigned long long)la_scanned;
+      tr[5] = nfound;
+      tr[6] = qend - level_qb;
+      tr[7] = (unsigned long long)nscan;
+      tr[13] = (unsigned long long)level_passes;
+    }
+    if (!ok || la == 0) break;
+  }
+  if (lane == 0) {
+    if (items) atomicAdd(&a.ctl->items, (unsigned long long)items);
+    if (local_items) atomicAdd(&a.ctl->local_items, (unsigned long long)local_items);
+  }
+  if (lead) {
+    *a.kmax_out = kmax;
+    a.ctl->rounds = levels + empty;
+    a.ctl->empty_rounds = empty;
+    a.ctl->scanned = scanned;
+    a.ctl->kmax = kmax;
+    a.ctl->passes = passes;
+    a.ctl->barriers = (long long)gen;
+  }
+}
+
+}  // namespace
+
+int bsp_max_ctas_per_sm() {
+  int nb = 0;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, peel_bsp, kBlock, 0) != cudaSuccess) return 0;
+  return nb;
+}
+
+int bsp_block_size() { return kBlock; }
+
+cudaError_t bsp_launch(const PeelArgs& args, int grid, cudaStream_t stream) {
+  PeelArgs a = args;
+  void* params[] = {&a};
+  return cudaLaunchCooperativeKernel((const void*)peel_bsp, dim3(grid), dim3(kBlock), params, 0, stream);
+}
+
+}  // namespace kc

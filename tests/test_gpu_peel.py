@@ -1,6 +1,7 @@
 """Parity of the GPU peel (through the C ABI) with the CPU oracle: bit-exact
 coreness on closed forms, hand-derived fixtures, random graphs over many seeds,
-the ER n=10,000 workload, adversarial shapes and every tuning mode."""
+the ER n=10,000 workload, adversarial shapes and every tuning mode, in both
+schedules (1: asynchronous, 2: bulk-synchronous with grid barriers)."""
 import numpy as np
 import pytest
 
@@ -15,9 +16,12 @@ from paper_2502_08042_gb300 import KCore, KCoreError  # noqa: E402
 from tests.gpu_util import assert_parity, gpu_core, to_dev  # noqa: E402
 
 
-@pytest.fixture(scope="module")
-def kc():
-    with KCore(0) as k:
+MODES = [1, 2]
+
+
+@pytest.fixture(scope="module", params=MODES, ids=["async", "bsp"])
+def kc(request):
+    with KCore(0, sync_mode=request.param) as k:
         yield k
 
 
@@ -92,12 +96,13 @@ def test_union_of_shapes(kc):
     dict(local_queue=128),
     dict(ctas_per_sm=1), dict(min_ctas=1, vertices_per_cta=1 << 40), dict(vertices_per_cta=1),
 ])
-def test_tuning_modes(opts):
+@pytest.mark.parametrize("mode", MODES)
+def test_tuning_modes(opts, mode):
     n, s, d = gg.disjoint_union((30000, *gg.rmat_n(30000, 300000, seed=5)), gg.staircase(120),
                                 gg.path(2000), gg.star(3000))
     off, adj = _csr(n, s, d)
     want = oracle.bz(n, off, adj)
-    with KCore(0, **opts) as k:
+    with KCore(0, sync_mode=mode, **opts) as k:
         assert_parity(k, n, off, adj, want)
 
 
@@ -133,7 +138,8 @@ def test_each_vertex_processed_once(kc):
     assert_parity(kc, n, off, adj)
     st = kc.stats()
     deg = np.diff(off)
-    sl = kc.get_option("slice_arcs")
+    sl = st["slice_arcs"]
+    assert sl == (128 if st["sync_mode"] == 2 else 512)
     slices = int(np.sum((deg + sl - 1) // sl))
     # each vertex with arcs is taken once as a whole item (from the global or a
     # warp-local queue) and its list is split into ceil(deg / slice) slices
@@ -149,11 +155,12 @@ def test_host_entry_point(kc):
     assert km == want.max()
 
 
-def test_caller_workspace(kc):
+@pytest.mark.parametrize("mode", MODES)
+def test_caller_workspace(mode):
     n = 20000
     s, d = gg.rmat_n(n, 100000, seed=3)
     off, adj = _csr(n, s, d)
-    with KCore(0) as k:
+    with KCore(0, sync_mode=mode) as k:
         ws = torch.empty(k.workspace_size(n, len(adj)), dtype=torch.uint8, device="cuda:0")
         k.set_workspace(ws)
         assert_parity(k, n, off, adj)
@@ -165,15 +172,17 @@ def test_caller_workspace(kc):
         assert e.value.code == "OOM"
 
 
-def test_timeout_is_reported_and_context_survives():
+@pytest.mark.parametrize("mode", MODES)
+def test_timeout_is_reported_and_context_survives(mode):
     """A wait that can never be satisfied (CTA 0 withholds its completion
-    token) must end at the time limit with KCORE_ERR_TIMEOUT, and the same
-    context must then decompose normally."""
+    token, or its arrival at the first grid barrier) must end at the time
+    limit with KCORE_ERR_TIMEOUT, and the same context must then decompose
+    normally."""
     n = 5000
     s, d = gg.rmat_n(n, 40000, seed=1)
     off, adj = _csr(n, s, d)
     o, a = to_dev(off, adj)
-    with KCore(0, timeout_ms=200, test_stall=1) as k:
+    with KCore(0, timeout_ms=200, test_stall=1, sync_mode=mode) as k:
         with pytest.raises(KCoreError) as e:
             k.decompose(o, a)
         assert e.value.code == "TIMEOUT"
@@ -206,3 +215,38 @@ def test_argument_errors(kc):
     assert L.kcore_decompose(kc._h, 2, 2, None, a.data_ptr(), None, None, None) == 1
     with pytest.raises(KCoreError):
         kc.set_option("slice_arcs", 1)
+
+
+def test_bsp_counters_and_trace():
+    """Bulk-synchronous schedule: one barrier per scan and per subround pass
+    (plus the final scan that finds nothing left), one trace entry per
+    non-empty level, the levels of the trace being exactly the distinct
+    coreness values."""
+    n = 60000
+    s, d = gg.rmat_n(n, 500000, seed=21)
+    off, adj = _csr(n, s, d)
+    want = oracle.bz(n, off, adj)
+    with KCore(0, sync_mode=2, trace=1) as k:
+        assert_parity(k, n, off, adj, want)
+        st = k.stats()
+        tr = k.trace()
+    assert st["sync_mode"] == 2
+    assert st["passes"] > 0
+    assert st["barriers"] - (st["rounds"] + st["passes"]) in (0, 1)
+    levels = tr[:, 3].astype(np.int64)
+    assert len(levels) == st["rounds"] - st["empty_rounds"]
+    np.testing.assert_array_equal(levels, np.unique(want))
+    assert int(tr[:, 13].sum()) == st["passes"]
+    assert (tr[:, 2] >= tr[:, 1]).all() and (tr[:, 1] >= tr[:, 0]).all()
+
+
+@pytest.mark.parametrize("mode", MODES)
+def test_isolated_only_and_single_level(mode):
+    """Graphs whose vertices all share one coreness: isolated vertices only,
+    a perfect matching, one clique."""
+    with KCore(0, sync_mode=mode) as k:
+        for n, s, d in [(1000, np.zeros(0, np.int32), np.zeros(0, np.int32)),
+                        (2000, np.arange(0, 2000, 2, dtype=np.int32), np.arange(1, 2000, 2, dtype=np.int32)),
+                        gg.complete(300)]:
+            off, adj = _csr(n, s, d)
+            assert_parity(k, n, off, adj)
