@@ -49,3 +49,14 @@ def test_argument_errors_without_device():
 
 def test_build_targets_sm103a_only():
     assert _native.ARCH == ["-gencode", "arch=compute_103a,code=sm_103a"]
+
+
+def test_smoke_graph_is_well_formed():
+    """The input smoke() sends to the GPU builds on the CPU and holds the
+    staircase's top level."""
+    import __graft_entry__ as ge
+    import oracle
+    n, s, d = ge.smoke_graph()
+    off, adj = oracle.build_csr(n, s, d)
+    assert len(off) == n + 1 and oracle.check_simple(n, off, adj) == 0
+    assert int(oracle.bz(n, off, adj).max()) >= 40
