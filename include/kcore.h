@@ -90,7 +90,7 @@ typedef struct {
   int64_t rounds;          /* levels visited, empty speculative levels included */
   int64_t empty_rounds;    /* visited levels that held no vertex */
   int64_t items;           /* work items (vertex slices) processed through the global queue */
-  int64_t local_items;     /* vertices processed from warp-local queues */
+  int64_t local_items;     /* work items (slices) processed from warp-local queues */
   int64_t scanned;         /* sum over rounds of the active-set size scanned (Theorem 1) */
   int64_t kmax;            /* largest coreness */
   int64_t grid;            /* CTAs of the persistent kernel */
@@ -308,6 +308,8 @@ kcore_status kcore_get_stats(kcore_handle h, kcore_stats* out);
  * [7] CTAs that scanned, [8] arcs read, [9] decrements issued, [10] longest
  * scan of one CTA (ns), [11] latest round start of a CTA after CTA 0 (ns),
  * [12] summed time warps spent in work batches (ns), [13] work batches.
+ * In mode 2 there is one entry per non-empty level: [1] is when its scan
+ * phases ended, [10..12] are 0 and [13] counts its subround passes.
  * Tracing adds atomics and slows the run. At most max_rounds rounds are
  * copied; *rounds_out receives the number copied. */
 kcore_status kcore_get_trace(kcore_handle h, uint64_t* out, int64_t max_rounds, int64_t* rounds_out);

@@ -57,7 +57,8 @@ struct PeelCtl {
   unsigned long long qtail;
   char pad6[120];
   long long passes, barriers;
-  char pad7[112];
+  unsigned long long tr_arcs, tr_decs;  // bulk-synchronous mode, with tracing: running sums
+  char pad7[96];
 };
 
 // Claim counters of one bulk-synchronous phase: the pass's queue range is cut
@@ -104,7 +105,9 @@ struct PeelArgs {
 // active-list length scanned, frontier vertices found, items queued, the
 // scanning CTAs, arcs read, decrements issued, the longest scan of one CTA
 // (ns), the latest round start of a CTA after CTA 0's (ns), the summed time
-// warps spent in work batches (ns) and the number of batches.
+// warps spent in work batches (ns) and the number of batches. The
+// bulk-synchronous mode writes one record per non-empty level, with 0 in
+// fields 10..12 and its subround passes in field 13.
 constexpr int kTraceFields = 14;
 
 int peel_max_ctas_per_sm();

@@ -57,6 +57,7 @@ struct Shared {
   unsigned long long base_a, base_q;
   unsigned long long red_found[kWarps];
   int red_min[kWarps];
+  unsigned long long tr_arcs[kWarps], tr_decs[kWarps];  // trace only
   int flag;
 };
 
@@ -292,6 +293,7 @@ __device__ void process_items(const PeelArgs& a, Shared& sh, const PassCtx& pc, 
   sh.a0[warp][lane] = a0;
   __syncwarp();
   const int* excl = sh.excl[warp];
+  int ndec = 0;
   for (int base = 0; base < total; base += kWarp * kIlp) {
     int u[kIlp];
     int j = base + lane;
@@ -329,7 +331,10 @@ __device__ void process_items(const PeelArgs& a, Shared& sh, const PassCtx& pc, 
     unsigned cross = 0;
 #pragma unroll
     for (int q = 0; q < kIlp; q++)
-      if (dq[q] > t && atomicSub(a.deg + u[q], 1) == t + 1) cross |= 1u << q;
+      if (dq[q] > t) {
+        ndec++;
+        if (atomicSub(a.deg + u[q], 1) == t + 1) cross |= 1u << q;
+      }
     if (__any_sync(kFull, cross != 0)) {
 #pragma unroll
       for (int q = 0; q < kIlp; q++) {
@@ -337,6 +342,13 @@ __device__ void process_items(const PeelArgs& a, Shared& sh, const PassCtx& pc, 
         if (f) a.core[u[q]] = t;
         if (__any_sync(kFull, f)) push_crossed(a, sh, pc, f, u[q], warp, lane);
       }
+    }
+  }
+  if (a.trace) {
+    ndec = warp_sum(ndec);
+    if (lane == 0) {
+      sh.tr_arcs[warp] += total;
+      sh.tr_decs[warp] += ndec;
     }
   }
   __syncwarp();
@@ -427,7 +439,10 @@ __global__ void __launch_bounds__(kBlock, 2) peel_bsp(PeelArgs a) {
   __shared__ Shared sh;
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   const bool lead = blockIdx.x == 0 && tid == 0;
-  if (lane == 0) sh.lqn[warp] = 0;
+  if (lane == 0) {
+    sh.lqn[warp] = 0;
+    sh.tr_arcs[warp] = sh.tr_decs[warp] = 0;
+  }
   unsigned long long gen = 0;
   long long phase = 0;  // RoundRec and ClaimSet (phase % 3) belong to phase `phase`
   auto reset_next = [&]() {
@@ -511,6 +526,8 @@ __global__ void __launch_bounds__(kBlock, 2) peel_bsp(PeelArgs a) {
     levels++;
     const uint64_t t_scan = lead && a.trace ? globaltimer_ns() : 0;
     const unsigned long long level_qb = qb;
+    const unsigned long long arcs0 = lead && a.trace ? ld_relaxed_u64(&a.ctl->tr_arcs) : 0;
+    const unsigned long long decs0 = lead && a.trace ? ld_relaxed_u64(&a.ctl->tr_decs) : 0;
     long long level_passes = 0;
     bool ok = true;
     // ---- subround passes; with no vertex left above the level nothing can be decremented
@@ -520,6 +537,11 @@ __global__ void __launch_bounds__(kBlock, 2) peel_bsp(PeelArgs a) {
         RoundRec* P = a.rounds + (phase % kClaimRing);
         const PassCtx pc{P, qend, t};
         run_pass(a, sh, pc, a.claims + (phase % kClaimRing), qb, qend, items, local_items, local_batches);
+        if (a.trace && lane == 0) {
+          atomicAdd(&a.ctl->tr_arcs, sh.tr_arcs[warp]);
+          atomicAdd(&a.ctl->tr_decs, sh.tr_decs[warp]);
+          sh.tr_arcs[warp] = sh.tr_decs[warp] = 0;
+        }
         if (!(ok = grid_barrier(a, sh, gen))) break;
         phase++;
         passes++;
@@ -540,6 +562,8 @@ __global__ void __launch_bounds__(kBlock, 2) peel_bsp(PeelArgs a) {
       tr[5] = nfound;
       tr[6] = qend - level_qb;
       tr[7] = (unsigned long long)nscan;
+      tr[8] = ld_relaxed_u64(&a.ctl->tr_arcs) - arcs0;
+      tr[9] = ld_relaxed_u64(&a.ctl->tr_decs) - decs0;
       tr[13] = (unsigned long long)level_passes;
     }
     if (!ok || la == 0) break;
