@@ -61,7 +61,7 @@ typedef enum {
                                   overlaps across subrounds); 2 bulk-synchronous persistent kernel
                                   (a bounded grid barrier after the scan and after every subround) */
   KCORE_OPT_CTAS_PER_SM = 1,   /* CTAs per SM of the persistent kernel (0 = occupancy maximum) */
-  KCORE_OPT_SLICE_ARCS = 2,    /* arcs per work item (16 .. 2^20; 0 = auto: 128 in mode 2, 512 in
+  KCORE_OPT_SLICE_ARCS = 2,    /* arcs per work item (16 .. 2^20; 0 = auto: 64 in mode 2, 512 in
                                   mode 1): longer lists are split in slices */
   KCORE_OPT_LOCAL_QUEUE = 3,   /* per-warp local queue capacity (vertices), 0 disables it */
   KCORE_OPT_TIMEOUT_MS = 4,    /* limit for every device-side wait, milliseconds */
@@ -80,7 +80,7 @@ typedef enum {
                                          fit with the CTAs per SM below) */
   KCORE_OPT_BATCH_CTAS_PER_SM = 13,   /* batched peel: resident CTAs per SM (0 = occupancy limit) */
   KCORE_OPT_LOCAL_BATCHES = 14        /* mode 2: local-queue batches a warp may run after each chunk it
-                                         claims (0 .. 2^20, 0 = no limit); the rest of its local queue
+                                         takes (0 .. 2^20, 0 = no limit); the rest of its local queue
                                          then goes to the work queue, so a large cascade is shared by
                                          all warps in the next subround instead of one warp */
 } kcore_option;

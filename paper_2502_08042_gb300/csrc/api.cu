@@ -74,7 +74,7 @@ long long isqrt_ll(long long m) {
 }
 
 struct PeelLayout {
-  size_t deg, a0, a1, q, rounds, claims, ctl, trace, total;
+  size_t deg, a0, a1, q, rounds, ctl, trace, total;
   long long qcap;
   int max_rounds;
 };
@@ -82,8 +82,8 @@ struct PeelLayout {
 // Workspace of the single-graph peel: d~[n], two active lists [n], the work
 // queue (every vertex pushes ceil(deg/slice) slices once: <= n + m/slice), the
 // per-round records (levels <= k_max+1 <= sqrt(m)+1, each followed by at most
-// one empty speculative level), the claim counters of the bulk-synchronous
-// mode and the control block. Everything below `deg` is zeroed per call.
+// one empty speculative level) and the control block. Everything below `deg`
+// is zeroed per call.
 PeelLayout peel_layout(long long n, long long m, int slice) {
   PeelLayout L{};
   L.qcap = n + (m + slice - 1) / slice + 1;
@@ -95,8 +95,6 @@ PeelLayout peel_layout(long long n, long long m, int slice) {
   off = align_up(off + sizeof(kc::PeelCtl), 256);
   L.rounds = off;
   off = align_up(off + sizeof(kc::RoundRec) * (size_t)L.max_rounds, 256);
-  L.claims = off;
-  off = align_up(off + sizeof(kc::ClaimSet) * kc::kClaimRing, 256);
   L.deg = off;
   off = align_up(off + 4 * (size_t)n, 256);
   L.a0 = off;
@@ -115,7 +113,7 @@ PeelLayout peel_layout(long long n, long long m, int slice) {
 int effective_mode(const kcore_ctx* h) { return h->opt[KCORE_OPT_SYNC_MODE] == 1 ? 1 : 2; }
 int effective_slice(const kcore_ctx* h) {
   if (h->opt[KCORE_OPT_SLICE_ARCS] > 0) return (int)h->opt[KCORE_OPT_SLICE_ARCS];
-  return effective_mode(h) == 2 ? 128 : 512;
+  return effective_mode(h) == 2 ? 64 : 512;
 }
 
 kcore_status ensure_ws(kcore_ctx* h, size_t need) {
@@ -321,7 +319,6 @@ kcore_status kcore_decompose(kcore_handle h, int64_t n, int64_t m, const int64_t
   a.poll_sleep_ns = (int)h->opt[KCORE_OPT_POLL_SLEEP_NS];
   a.inject_stall = (int)h->opt[KCORE_OPT_TEST_STALL];
   a.trace = h->opt[KCORE_OPT_TRACE] ? (unsigned long long*)(ws + L.trace) : nullptr;
-  a.claims = (kc::ClaimSet*)(ws + L.claims);
   a.local_batches = h->opt[KCORE_OPT_LOCAL_BATCHES] > 0 ? (int)h->opt[KCORE_OPT_LOCAL_BATCHES] : INT32_MAX;
 
   const int mode = effective_mode(h);

@@ -61,16 +61,9 @@ struct PeelCtl {
   char pad7[96];
 };
 
-// Claim counters of one bulk-synchronous phase: the pass's queue range is cut
-// into kClaimParts partitions, each with its own counter on its own line.
-constexpr int kClaimParts = 32;
-struct ClaimSet {
-  struct {
-    unsigned long long next;
-    char pad[120];
-  } part[kClaimParts];
-};
-constexpr int kClaimRing = 3;  // phase p uses set p % 3
+// The bulk-synchronous mode uses round records 0..2 as a ring: phase p uses
+// record p % 3 (reset during phase p - 1, last read during phase p - 2).
+constexpr int kPhaseRing = 3;
 
 struct PeelArgs {
   long long n, m;
@@ -96,8 +89,7 @@ struct PeelArgs {
   int poll_sleep_ns;  // sleep of the CTA's round poller between polls
   int inject_stall;
   unsigned long long* trace;  // optional: kTraceFields words per round (nullptr = off)
-  ClaimSet* claims;           // bulk-synchronous mode: kClaimRing sets (zeroed)
-  int local_batches;          // bulk-synchronous mode: local batches per claimed chunk
+  int local_batches;          // bulk-synchronous mode: local batches per chunk taken
 };
 
 // Per-round trace record (KCORE_OPT_TRACE): globaltimer at round start (CTA 0),

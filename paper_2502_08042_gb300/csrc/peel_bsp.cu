@@ -10,8 +10,9 @@
 //            minimum induced degree of the kept vertices rides along: if level
 //            k is empty, it is the next non-empty level and a second scan
 //            collects its vertices.
-//   pass   - one subround over the queue range appended before it: warps claim
-//            up to 32 items at a time and process their arcs edge-balanced. A
+//   pass   - one subround over the queue range appended before it: each warp
+//            takes its own share of the items, 32 at a time, and processes
+//            their arcs edge-balanced. A
 //            decrement of a neighbour above k that returns k+1 is the crossing
 //            of Algorithm 3: the neighbour gets coreness k and is processed by
 //            the same warp in the same pass if its list fits one slice and the
@@ -19,14 +20,14 @@
 //            granularity control, Sec. 4.2); otherwise its slices go to the
 //            queue for the next pass. The level ends with a pass that appends
 //            nothing.
-// The queue range of a pass is fixed while it runs, so claims are plain
-// fetch-and-adds on counters spread over 32 partitions, pushes need no fences
-// and the pass ends at the barrier. A queue item is an arc range (first arc,
+// The queue range of a pass is fixed while it runs, so it is split into
+// static per-warp shares (no claim traffic), pushes need no fences and the
+// pass ends at the barrier. A queue item is an arc range (first arc,
 // length), so processing it needs no offset lookup. Each phase counts its own
 // appends, which land after everything appended before the phase, so the next
 // range is known to every CTA after the barrier. Every vertex is appended at
 // most once over the whole run, so the queue never wraps. A warp runs at most
-// `local_batches` batches from its local queue per chunk it claims and then
+// `local_batches` batches from its local queue per chunk it takes and then
 // moves the rest to the queue: a large cascade is shared by all warps in the
 // next pass instead of being walked by the warp that started it. Every wait is
 // bounded by the handle's time limit (KCORE_ERR_TIMEOUT).
@@ -41,9 +42,10 @@ namespace {
 
 constexpr int kBlock = 512;
 constexpr int kWarps = kBlock / kWarp;
-constexpr int kTile = 4;   // active-list entries per thread per scan tile
+constexpr int kTile = 8;   // active-list entries per thread per scan tile
+constexpr int kExpand = 4; // staged frontier vertices per thread per expansion round
 constexpr int kIlp = 8;    // arcs per lane in flight
-constexpr int kTake = 32;  // most queue items per claim
+constexpr int kTake = 32;  // queue items per chunk of a warp's share
 constexpr int kLenShift = 40;  // item = first arc | length << 40
 constexpr unsigned long long kArcMask = (1ull << kLenShift) - 1;
 constexpr unsigned long long kAbort = 1ull << 62;  // barrier word: a status was raised
@@ -51,12 +53,16 @@ constexpr unsigned long long kAbort = 1ull << 62;  // barrier word: a status was
 struct Shared {
   int excl[kWarps][kWarp];
   long long a0[kWarps][kWarp];
-  unsigned long long lq[kWarps][kLocalQueueMax];
+  union {
+    unsigned long long lq[kWarps][kLocalQueueMax];  // passes: the warps' local queues
+    int stage[kBlock * kTile];                      // scans (local queues are empty): frontier ids
+  };
   int lqn[kWarps];
-  unsigned long long part[kWarps];
+  int part_i[kWarps];
+  int total_i;
   unsigned long long base_a, base_q;
-  unsigned long long red_found[kWarps];
   int red_min[kWarps];
+  int red_cnt[kWarps];
   unsigned long long tr_arcs[kWarps], tr_decs[kWarps];  // trace only
   int flag;
 };
@@ -82,7 +88,7 @@ __device__ bool grid_barrier(const PeelArgs& a, Shared& sh, unsigned long long& 
   if (threadIdx.x == 0) {
     int ok = 1;
     const unsigned long long target = (gen + 1) * gridDim.x;
-    __threadfence();
+    // the CTA barrier above orders the CTA's writes before this release
     if (!(a.inject_stall && blockIdx.x == 0 && gen == 0))
       asm volatile("red.release.gpu.global.add.u64 [%0], 1;" ::"l"(&a.ctl->bar_count) : "memory");
     uint64_t t0 = 0;
@@ -120,114 +126,156 @@ struct ScanOut {
   int dmin;
 };
 
+// Block-wide exclusive prefix sum of x; *total receives the block's sum.
+// Ends with every thread past the barrier that published the partial sums.
+__device__ __forceinline__ int block_excl_scan(Shared& sh, int x, int* total) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int incl = warp_incl_scan(x, lane);
+  if (lane == 31) sh.part_i[warp] = incl;
+  __syncthreads();
+  if (warp == 0) {
+    const int y = lane < kWarps ? sh.part_i[lane] : 0;
+    const int yi = warp_incl_scan(y, lane);
+    if (lane < kWarps) sh.part_i[lane] = yi - y;
+    if (lane == kWarps - 1) sh.total_i = yi;
+  }
+  __syncthreads();
+  *total = sh.total_i;
+  return sh.part_i[warp] + incl - x;
+}
+
 // Scan of active-list entries [lo, hi) by one CTA: entries with d~ > keep_above
 // go to Aout (their minimum d~ is returned), entries with d~ == take_at get
 // coreness take_at and their slices are appended to the queue after position
 // qbase (count in R->tail). With Ain == nullptr the list is 0..n-1 and d~ is
-// initialised from the offsets.
+// initialised from the offsets. A tile is read in one step (list entries,
+// then their d~: kTile independent loads per thread each), its frontier
+// vertices are staged in shared memory and expanded into slices in a second
+// step, so the offsets of only those vertices are read.
 __device__ ScanOut scan_range(const PeelArgs& a, Shared& sh, RoundRec* R, unsigned long long qbase,
                               const int* Ain, int* Aout, long long lo, long long hi, int keep_above,
                               int take_at) {
-  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-  unsigned long long found = 0;
+  const int tid = threadIdx.x;
+  unsigned long long found = 0;  // staged frontier vertices (block-uniform)
+  int direct = 0;                // frontier vertices without arcs (this thread)
   int dmin = INT_MAX;
   for (long long tile = lo; tile < hi; tile += (long long)kBlock * kTile) {
     int v[kTile];
-    int keep[kTile];
-    int nsl[kTile];
-    long long e0[kTile], e1[kTile];
-    int cs = 0, ps = 0;
+    unsigned keep = 0, take = 0;
 #pragma unroll
     for (int q = 0; q < kTile; q++) {
       const long long i = tile + (long long)q * kBlock + tid;
-      v[q] = -1;
-      keep[q] = 0;
-      nsl[q] = 0;
-      e0[q] = e1[q] = 0;
-      if (i >= hi) continue;
-      const int x = Ain ? __ldcg(Ain + i) : (int)i;
+      v[q] = i < hi ? (Ain ? __ldcg(Ain + i) : (int)i) : -1;
+    }
+#pragma unroll
+    for (int q = 0; q < kTile; q++) {
+      const int x = v[q];
+      if (x < 0 && tile + (long long)q * kBlock + tid >= hi) continue;
       if ((unsigned)x >= (unsigned)a.n) {
         raise_status(a, ST_NOT_SIMPLE);
+        v[q] = -1;
         continue;
       }
       int d;
       if (!Ain) {
-        e0[q] = a.off[x];
-        e1[q] = a.off[x + 1];
-        if (e0[q] < 0 || e1[q] < e0[q] || e1[q] > a.m || e1[q] - e0[q] >= a.n) {
+        const long long e0 = a.off[x], e1 = a.off[x + 1];
+        if (e0 < 0 || e1 < e0 || e1 > a.m || e1 - e0 >= a.n) {
           raise_status(a, ST_NOT_SIMPLE);  // malformed offsets: no arc of x is ever read
-          e0[q] = e1[q] = 0;
+          d = -1;
+        } else {
+          d = (int)(e1 - e0);
         }
-        d = (int)(e1[q] - e0[q]);
-        a.deg[x] = d;
+        a.deg[x] = d < 0 ? 0 : d;
+        if (d < 0) {
+          // a malformed vertex is neither kept nor expanded; it takes level 0
+          a.core[x] = 0;
+          v[q] = -1;
+          continue;
+        }
       } else {
         d = __ldcg(a.deg + x);
       }
-      v[q] = x;
       if (d > keep_above) {
-        keep[q] = 1;
+        keep |= 1u << q;
         dmin = min(dmin, d);
       }
       if (d == take_at) {
-        found++;
-        a.core[x] = take_at;
-        if (Ain) {
-          e0[q] = a.off[x];
-          e1[q] = a.off[x + 1];
+        if (!Ain && d == 0) {
+          a.core[x] = 0;  // first scan: no arcs, nothing to expand
+          direct++;
+        } else {
+          take |= 1u << q;
         }
-        nsl[q] = (int)((e1[q] - e0[q] + a.slice - 1) / a.slice);
       }
-      cs += keep[q];
-      ps += nsl[q];
     }
-    // block-wide exclusive offsets of (kept, slices), one atomic pair per tile
-    const unsigned long long packed = ((unsigned long long)(unsigned)ps << 32) | (unsigned)cs;
-    const unsigned long long incl = warp_incl_scan(packed, lane);
-    if (lane == 31) sh.part[warp] = incl;
+    // block-wide offsets of (kept, taken): kept entries go to Aout after one
+    // atomic per tile, taken ones to the shared-memory stage
+    int tot;
+    const int ex = block_excl_scan(sh, (__popc(take) << 16) | __popc(keep), &tot);
+    if (tid == 0) sh.base_a = (tot & 0xffff) ? atomicAdd(&R->alen, (unsigned long long)(tot & 0xffff)) : 0;
     __syncthreads();
-    if (warp == 0) {
-      const unsigned long long x = lane < kWarps ? sh.part[lane] : 0;
-      const unsigned long long xi = warp_incl_scan(x, lane);
-      if (lane < kWarps) sh.part[lane] = xi - x;
-      if (lane == kWarps - 1) {
-        const unsigned long long tc = xi & 0xffffffffull, tq = xi >> 32;
-        sh.base_a = tc ? atomicAdd(&R->alen, tc) : 0;
-        unsigned long long bq = qbase + (tq ? atomicAdd(&R->tail, tq) : 0);
-        if (bq + tq > (unsigned long long)a.qcap) {
+    unsigned long long pa = sh.base_a + (ex & 0xffff);
+    int ps = ex >> 16;
+#pragma unroll
+    for (int q = 0; q < kTile; q++) {
+      if ((keep >> q) & 1u) Aout[pa++] = v[q];
+      if ((take >> q) & 1u) sh.stage[ps++] = v[q];
+    }
+    __syncthreads();
+    const int ntaken = tot >> 16;
+    found += ntaken;
+    // expand the staged frontier vertices into slices, kExpand per thread per round
+    for (int base = 0; base < ntaken; base += kBlock * kExpand) {
+      long long e0[kExpand], e1[kExpand];
+      int nsl = 0;
+#pragma unroll
+      for (int k = 0; k < kExpand; k++) {
+        const int i = base + k * kBlock + tid;
+        e0[k] = e1[k] = 0;
+        if (i < ntaken) {
+          const int x = sh.stage[i];
+          e0[k] = a.off[x];
+          e1[k] = a.off[x + 1];
+          a.core[x] = take_at;
+        }
+      }
+#pragma unroll
+      for (int k = 0; k < kExpand; k++) nsl += (int)((e1[k] - e0[k] + a.slice - 1) / a.slice);
+      int ntot;
+      const int exs = block_excl_scan(sh, nsl, &ntot);
+      if (tid == 0) {
+        unsigned long long bq = qbase + (ntot ? atomicAdd(&R->tail, (unsigned long long)ntot) : 0);
+        if (bq + (unsigned long long)ntot > (unsigned long long)a.qcap) {
           raise_status(a, ST_CAPACITY);
           bq = ~0ull;
         }
         sh.base_q = bq;
       }
-    }
-    __syncthreads();
-    const unsigned long long ex = sh.part[warp] + incl - packed;
-    unsigned long long pa = sh.base_a + (ex & 0xffffffffull);
-    unsigned long long pq = sh.base_q + (ex >> 32);
-    const bool qok = sh.base_q != ~0ull;
+      __syncthreads();
+      if (sh.base_q != ~0ull) {
+        unsigned long long pq = sh.base_q + exs;
 #pragma unroll
-    for (int q = 0; q < kTile; q++) {
-      if (keep[q]) Aout[pa++] = v[q];
-      if (nsl[q] && qok)
-        for (long long s0 = e0[q]; s0 < e1[q]; s0 += a.slice)
-          a.Q[pq++] = make_item(s0, min((long long)a.slice, e1[q] - s0));
+        for (int k = 0; k < kExpand; k++)
+          for (long long s0 = e0[k]; s0 < e1[k]; s0 += a.slice)
+            a.Q[pq++] = make_item(s0, min((long long)a.slice, e1[k] - s0));
+      }
+      __syncthreads();
     }
-    __syncthreads();
   }
-  const unsigned long long fw = warp_sum(found);
+  const int lane = tid & 31, warp = tid >> 5;
   const int mw = warp_min(dmin);
+  const int dw = warp_sum(direct);
   if (lane == 0) {
-    sh.red_found[warp] = fw;
     sh.red_min[warp] = mw;
+    sh.red_cnt[warp] = dw;
   }
   __syncthreads();
-  ScanOut o{0, INT_MAX};
-  if (tid == 0) {
+  ScanOut o{found, INT_MAX};
+  if (tid == 0)
     for (int w = 0; w < kWarps; w++) {
-      o.found += sh.red_found[w];
       o.dmin = min(o.dmin, sh.red_min[w]);
+      o.found += (unsigned long long)sh.red_cnt[w];
     }
-  }
   return o;
 }
 
@@ -387,51 +435,25 @@ __device__ void drain_local(const PeelArgs& a, Shared& sh, const PassCtx& pc, in
   }
 }
 
-// One subround: the queue range [qb, qe) is processed once, claimed in chunks
-// of `take` items from kClaimParts partitions (a warp starts in partition
-// gw % kClaimParts and moves on when it is drained).
-__device__ void run_pass(const PeelArgs& a, Shared& sh, const PassCtx& pc, ClaimSet* cs, unsigned long long qb,
+// One subround: the queue range [qb, qe) is processed once. Warp gw takes
+// its own contiguous share (len / warps items, one more for the first
+// len % warps warps) in chunks of up to 32 items, so a pass has no claim
+// traffic and ends for a warp as soon as its share and local queue are done.
+__device__ void run_pass(const PeelArgs& a, Shared& sh, const PassCtx& pc, unsigned long long qb,
                          unsigned long long qe, long long& items, long long& local_items,
                          unsigned& local_batches) {
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const unsigned long long gw = (unsigned long long)blockIdx.x * kWarps + warp;
   const unsigned long long nw = (unsigned long long)gridDim.x * kWarps;
-  const unsigned long long len = qe - qb;
-  if (len <= nw) {
-    // one item per warp, no claims
-    if (gw < len) {
-      const unsigned long long item = lane == 0 ? __ldcg(a.Q + qb + gw) : 0;
-      process_items(a, sh, pc, item, 1, warp, lane);
-      items += 1;
-      drain_local(a, sh, pc, warp, lane, local_items, local_batches);
-    }
-    return;
-  }
-  unsigned long long take = len / (2 * nw);
-  take = take < 1 ? 1 : (take > (unsigned long long)kTake ? kTake : take);
-  int p = (int)(gw % kClaimParts);
-  for (;;) {
-    const unsigned long long pb = qb + len * p / kClaimParts, pe = qb + len * (p + 1) / kClaimParts;
-    unsigned long long pos = 0;
-    if (lane == 0) pos = pb + atomicAdd(&cs->part[p].next, take);
-    pos = __shfl_sync(kFull, pos, 0);
-    if (pos < pe) {
-      const int c = (int)min(take, pe - pos);
-      const unsigned long long item = lane < c ? __ldcg(a.Q + pos + lane) : 0;
-      process_items(a, sh, pc, item, c, warp, lane);
-      items += c;
-      drain_local(a, sh, pc, warp, lane, local_items, local_batches);
-      continue;
-    }
-    // partition p is drained: look at all partitions at once, move to the
-    // next one (cyclically) that still has items
-    const unsigned long long lb = qb + len * lane / kClaimParts, le = qb + len * (lane + 1) / kClaimParts;
-    const bool open = lb + ld_relaxed_u64(&cs->part[lane].next) < le;
-    const unsigned m = __ballot_sync(kFull, open);
-    if (!m) return;
-    const int s = (p + 1) & 31;
-    const unsigned rot = (m >> s) | (m << ((32 - s) & 31));
-    p = (s + __ffs(rot) - 1) & 31;
+  const unsigned long long len = qe - qb, share = len / nw, rem = len % nw;
+  const unsigned long long b = qb + gw * share + (gw < rem ? gw : rem);
+  const unsigned long long e = b + share + (gw < rem ? 1 : 0);
+  for (unsigned long long pos = b; pos < e; pos += kTake) {
+    const int c = (int)min((unsigned long long)kTake, e - pos);
+    const unsigned long long item = lane < c ? __ldcg(a.Q + pos + lane) : 0;
+    process_items(a, sh, pc, item, c, warp, lane);
+    items += c;
+    drain_local(a, sh, pc, warp, lane, local_items, local_batches);
   }
 }
 
@@ -444,12 +466,11 @@ __global__ void __launch_bounds__(kBlock, 2) peel_bsp(PeelArgs a) {
     sh.tr_arcs[warp] = sh.tr_decs[warp] = 0;
   }
   unsigned long long gen = 0;
-  long long phase = 0;  // RoundRec and ClaimSet (phase % 3) belong to phase `phase`
+  long long phase = 0;  // RoundRec (phase % 3) belongs to phase `phase`
   auto reset_next = [&]() {
     // the records of the next phase were last used two phases ago
-    const int r = (int)((phase + 1) % kClaimRing);
+    const int r = (int)((phase + 1) % kPhaseRing);
     if (blockIdx.x == 0 && warp == 0) {
-      a.claims[r].part[lane].next = 0;
       if (lane == 0) {
         RoundRec* R = a.rounds + r;
         R->alen = 0;
@@ -475,7 +496,7 @@ __global__ void __launch_bounds__(kBlock, 2) peel_bsp(PeelArgs a) {
     const int tk = tp + 1;
     const uint64_t t_start = lead && a.trace ? globaltimer_ns() : 0;
     reset_next();
-    RoundRec* R = a.rounds + (phase % kClaimRing);
+    RoundRec* R = a.rounds + (phase % kPhaseRing);
     long long nscan = nscan_of(la);
     if (blockIdx.x < nscan) {
       const long long lo = la * blockIdx.x / nscan, hi = la * (blockIdx.x + 1) / nscan;
@@ -508,7 +529,7 @@ __global__ void __launch_bounds__(kBlock, 2) peel_bsp(PeelArgs a) {
       empty++;
       t = INT_MAX - minkey;
       reset_next();
-      R = a.rounds + (phase % kClaimRing);
+      R = a.rounds + (phase % kPhaseRing);
       nscan = nscan_of(la);
       if (blockIdx.x < nscan) {
         const long long lo = la * blockIdx.x / nscan, hi = la * (blockIdx.x + 1) / nscan;
@@ -534,9 +555,9 @@ __global__ void __launch_bounds__(kBlock, 2) peel_bsp(PeelArgs a) {
     if (la > 0) {
       while (qend > qb) {
         reset_next();
-        RoundRec* P = a.rounds + (phase % kClaimRing);
+        RoundRec* P = a.rounds + (phase % kPhaseRing);
         const PassCtx pc{P, qend, t};
-        run_pass(a, sh, pc, a.claims + (phase % kClaimRing), qb, qend, items, local_items, local_batches);
+        run_pass(a, sh, pc, qb, qend, items, local_items, local_batches);
         if (a.trace && lane == 0) {
           atomicAdd(&a.ctl->tr_arcs, sh.tr_arcs[warp]);
           atomicAdd(&a.ctl->tr_decs, sh.tr_decs[warp]);

@@ -139,7 +139,7 @@ def test_each_vertex_processed_once(kc):
     st = kc.stats()
     deg = np.diff(off)
     sl = st["slice_arcs"]
-    assert sl == (128 if st["sync_mode"] == 2 else 512)
+    assert sl == (64 if st["sync_mode"] == 2 else 512)
     slices = int(np.sum((deg + sl - 1) // sl))
     # each vertex with arcs is taken once as a whole item (from the global or a
     # warp-local queue) and its list is split into ceil(deg / slice) slices
