@@ -315,6 +315,8 @@ __device__ __forceinline__ void push_crossed(const PeelArgs& a, Shared& sh, cons
     e0 = a.off[u];
     e1 = a.off[u + 1];
     nsl = (int)((e1 - e0 + a.slice - 1) / a.slice);
+    // its first adjacency line is read next, here or by another warp
+    if (e1 > e0) asm volatile("prefetch.global.L2 [%0];" ::"l"(a.adj + e0));
   }
   const bool one = flag && nsl == 1;
   const unsigned om = __ballot_sync(kFull, one);
