@@ -222,6 +222,32 @@ kcore_status kcore_build_csr_batched(kcore_handle h, int64_t num_graphs, int64_t
 kcore_status kcore_batched_workspace_size(kcore_handle h, int64_t num_graphs, int64_t total_vertices,
                                           size_t* bytes);
 
+/* Result of kcore_autotune_batched. */
+typedef struct {
+  int32_t block;         /* threads per CTA chosen (KCORE_OPT_BATCH_BLOCK) */
+  int32_t ctas_per_sm;   /* resident CTAs per SM chosen (KCORE_OPT_BATCH_CTAS_PER_SM) */
+  int32_t smem_vertices; /* largest graph kept in shared memory under that shape */
+  int32_t candidates;    /* launch shapes timed */
+  double ms;             /* best time of one batched call with the chosen shape */
+} kcore_batch_tuning;
+
+/* Autotuner of the batched peel (not in the paper: the launch shape of the
+ * batched form). Times each candidate launch shape -- 1024, 512 or 256
+ * threads per CTA with 1..8 resident CTAs per SM, the shared-memory threshold
+ * following the shape -- on the caller's own batch (the arguments of
+ * kcore_decompose_batched), best of `repeats` (1..100) calls after one
+ * warm-up each, with CUDA events on `stream`. It then sets the handle's three
+ * batch options to the fastest shape, runs the batch once more with it and
+ * fills *best_out. Synchronous; the outputs hold that last, exact result.
+ * Errors: KCORE_ERR_INVALID (bad arguments; options unchanged), the first
+ * input or memory error any call reports (KCORE_ERR_NOT_SIMPLE, _OOM;
+ * options restored), KCORE_ERR_CUDA if no shape could run. */
+kcore_status kcore_autotune_batched(kcore_handle h, int64_t num_graphs, int64_t total_vertices,
+                                    int64_t total_arcs, const int64_t* graph_vertex_offsets,
+                                    const int64_t* offsets, const int32_t* adj, int32_t* coreness_out,
+                                    int32_t* kmax_out, int32_t repeats, kcore_batch_tuning* best_out,
+                                    kcore_stream_t stream);
+
 /* ------------------------------------------------------------------------
  * Served peel (the paper peels one graph at a time; this is the request-loop
  * form of the same peel). A server owns a device memory pool reserved at

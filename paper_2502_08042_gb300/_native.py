@@ -102,6 +102,12 @@ class Stats(ctypes.Structure):
                [("reserved", c_i64 * 3)]
 
 
+class BatchTuning(ctypes.Structure):
+    _fields_ = [("block", ctypes.c_int32), ("ctas_per_sm", ctypes.c_int32),
+                ("smem_vertices", ctypes.c_int32), ("candidates", ctypes.c_int32),
+                ("ms", ctypes.c_double)]
+
+
 # Every exported symbol of include/kcore.h with its ctypes signature.
 SIGNATURES = {
     "kcore_create": ([ctypes.POINTER(c_p), ctypes.c_int], ctypes.c_int),
@@ -122,6 +128,8 @@ SIGNATURES = {
     "kcore_decompose_batched": ([c_p, c_i64, c_i64, c_i64, c_p, c_p, c_p, c_p, c_p, c_p],
                                 ctypes.c_int),
     "kcore_batched_workspace_size": ([c_p, c_i64, c_i64, ctypes.POINTER(c_sz)], ctypes.c_int),
+    "kcore_autotune_batched": ([c_p, c_i64, c_i64, c_i64, c_p, c_p, c_p, c_p, c_p, ctypes.c_int32,
+                                ctypes.POINTER(BatchTuning), c_p], ctypes.c_int),
     "kcore_build_csr_batched": ([c_p, c_i64, c_i64, c_i64, c_i64, c_p, c_p, c_p, c_p, c_p, c_p, c_p,
                                  c_p], ctypes.c_int),
     "kcore_server_create": ([ctypes.POINTER(c_p), ctypes.c_int, c_p], ctypes.c_int),

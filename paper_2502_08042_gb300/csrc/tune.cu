@@ -1,0 +1,123 @@
+// Autotuner of the batched peel's launch shape (host code; declarations and
+// contract in include/kcore.h). It times the candidate shapes on the caller's
+// own batch through the public entry points, so what it measures is exactly
+// what later calls run.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <string>
+#include <vector>
+
+#include "kcore.h"
+
+namespace {
+
+struct Shape {
+  int block, ctas_per_sm;
+};
+
+// Candidate shapes: threads per CTA x resident CTAs per SM, within one SM's
+// 2048 threads. The shared-memory threshold follows each shape (-1: as many
+// vertices as fit with that many CTAs per SM).
+std::vector<Shape> candidates() {
+  std::vector<Shape> c;
+  for (int cps : {1, 2}) c.push_back({1024, cps});
+  for (int cps : {1, 2, 3, 4}) c.push_back({512, cps});
+  for (int cps : {2, 4, 6, 8}) c.push_back({256, cps});
+  return c;
+}
+
+struct OptionSnapshot {
+  kcore_handle h;
+  int64_t block = 0, sv = 0, cps = 0;
+  explicit OptionSnapshot(kcore_handle hh) : h(hh) {
+    kcore_get_option(h, KCORE_OPT_BATCH_BLOCK, &block);
+    kcore_get_option(h, KCORE_OPT_BATCH_SMEM_VERTICES, &sv);
+    kcore_get_option(h, KCORE_OPT_BATCH_CTAS_PER_SM, &cps);
+  }
+  void restore() const {
+    kcore_set_option(h, KCORE_OPT_BATCH_BLOCK, block);
+    kcore_set_option(h, KCORE_OPT_BATCH_SMEM_VERTICES, sv);
+    kcore_set_option(h, KCORE_OPT_BATCH_CTAS_PER_SM, cps);
+  }
+};
+
+kcore_status apply(kcore_handle h, const Shape& s) {
+  kcore_status st = kcore_set_option(h, KCORE_OPT_BATCH_BLOCK, s.block);
+  if (st == KCORE_OK) st = kcore_set_option(h, KCORE_OPT_BATCH_SMEM_VERTICES, -1);
+  if (st == KCORE_OK) st = kcore_set_option(h, KCORE_OPT_BATCH_CTAS_PER_SM, s.ctas_per_sm);
+  return st;
+}
+
+}  // namespace
+
+extern "C" kcore_status kcore_autotune_batched(kcore_handle h, int64_t num_graphs, int64_t total_vertices,
+                                               int64_t total_arcs, const int64_t* graph_vertex_offsets,
+                                               const int64_t* offsets, const int32_t* adj,
+                                               int32_t* coreness_out, int32_t* kmax_out, int32_t repeats,
+                                               kcore_batch_tuning* best_out, kcore_stream_t stream_) {
+  if (!h || !best_out || repeats < 1 || repeats > 100 || num_graphs < 1) return KCORE_ERR_INVALID;
+  cudaStream_t stream = (cudaStream_t)stream_;
+  *best_out = kcore_batch_tuning{};
+  OptionSnapshot saved(h);
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess) {
+    if (e0) cudaEventDestroy(e0);
+    cudaGetLastError();
+    return KCORE_ERR_CUDA;
+  }
+  Shape best{0, 0};
+  double best_ms = 0;
+  int timed = 0;
+  kcore_status result = KCORE_OK;
+  for (const Shape& s : candidates()) {
+    if (apply(h, s) != KCORE_OK) continue;  // not a valid shape on this device
+    // warm-up call: first launch of a shape sets its attributes; its status
+    // also tells whether the input is sound
+    kcore_status st = kcore_decompose_batched(h, num_graphs, total_vertices, total_arcs, graph_vertex_offsets,
+                                              offsets, adj, coreness_out, kmax_out, stream_);
+    if (st == KCORE_OK) st = kcore_sync_status(h);
+    if (st == KCORE_ERR_NOT_SIMPLE || st == KCORE_ERR_OOM || st == KCORE_ERR_INVALID) {
+      result = st;  // input or memory problem: no shape can fix it
+      break;
+    }
+    if (st != KCORE_OK) continue;  // this shape cannot launch here
+    double shape_ms = 1e30;
+    for (int r = 0; r < repeats && st == KCORE_OK; r++) {
+      cudaEventRecord(e0, stream);
+      st = kcore_decompose_batched(h, num_graphs, total_vertices, total_arcs, graph_vertex_offsets, offsets,
+                                   adj, coreness_out, kmax_out, stream_);
+      cudaEventRecord(e1, stream);
+      if (st == KCORE_OK) st = kcore_sync_status(h);
+      float ms = 0;
+      if (st == KCORE_OK && cudaEventElapsedTime(&ms, e0, e1) == cudaSuccess) shape_ms = std::min(shape_ms, (double)ms);
+    }
+    if (st != KCORE_OK) continue;
+    timed++;
+    if (best.block == 0 || shape_ms < best_ms) {
+      best = s;
+      best_ms = shape_ms;
+    }
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  cudaGetLastError();
+  if (result != KCORE_OK || best.block == 0) {
+    saved.restore();
+    return result != KCORE_OK ? result : KCORE_ERR_CUDA;
+  }
+  apply(h, best);
+  // leave the outputs computed with the chosen shape
+  kcore_status st = kcore_decompose_batched(h, num_graphs, total_vertices, total_arcs, graph_vertex_offsets,
+                                            offsets, adj, coreness_out, kmax_out, stream_);
+  if (st == KCORE_OK) st = kcore_sync_status(h);
+  if (st != KCORE_OK) return st;
+  kcore_stats stats{};
+  kcore_get_stats(h, &stats);
+  best_out->block = best.block;
+  best_out->ctas_per_sm = best.ctas_per_sm;
+  best_out->smem_vertices = (int32_t)stats.batch_smem_vertices;
+  best_out->candidates = timed;
+  best_out->ms = best_ms;
+  return KCORE_OK;
+}

@@ -171,6 +171,26 @@ class KCore:
             self.sync()
         return coreness, kmax
 
+    def autotune_batched(self, graph_vertex_offsets, offsets, adj, coreness=None, kmax=None,
+                         repeats: int = 2, stream=None):
+        """Times the batched peel's launch shapes on this batch, keeps the
+        fastest in the handle's options and returns (coreness, kmax, tuning
+        dict) computed with it."""
+        torch = _torch()
+        G = graph_vertex_offsets.numel() - 1
+        N = offsets.numel() - 1
+        M = adj.numel()
+        dev = offsets.device
+        if coreness is None:
+            coreness = torch.empty(max(N, 0), dtype=torch.int32, device=dev)
+        if kmax is None:
+            kmax = torch.empty(max(G, 0), dtype=torch.int32, device=dev)
+        t = _native.BatchTuning()
+        self._check(self._L.kcore_autotune_batched(
+            self._h, G, N, M, _ptr(graph_vertex_offsets), _ptr(offsets), _ptr(adj), _ptr(coreness),
+            _ptr(kmax), int(repeats), ctypes.byref(t), _stream_ptr(stream)))
+        return coreness, kmax, {f: getattr(t, f) for f, _ in t._fields_}
+
     def build_csr_batched(self, graph_vertex_offsets, graph_edge_offsets, src, dst,
                           max_graph_vertices: int, stream=None, sync: bool = True):
         """Segmented CSR of a batch of edge lists with graph-local ids (all CUDA

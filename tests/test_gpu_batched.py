@@ -167,3 +167,58 @@ def test_batched_full_workload_matches_oracle():
     bad = [g for g in range(G) if not np.array_equal(core[gv[g]:gv[g + 1]], want[g])]
     assert bad == []
     assert all(km[g] == want[g].max() for g in range(G))
+
+
+def test_autotune_picks_a_shape_and_stays_exact(small_batch):
+    """The autotuner times the launch shapes on the batch, keeps the fastest
+    in the handle's options, and every result along the way stays exact."""
+    gv, off, adj = small_batch
+    want_core, want_km = oracle.bz_batch(gv, off, adj)
+    with KCore(0) as k:
+        core, km, t = k.autotune_batched(_t(gv, np.int64), _t(off, np.int64), _t(adj, np.int32), repeats=1)
+        np.testing.assert_array_equal(core.cpu().numpy(), want_core)
+        np.testing.assert_array_equal(km.cpu().numpy(), want_km)
+        assert t["block"] in (256, 512, 1024) and t["candidates"] >= 2 and t["ms"] > 0
+        assert k.get_option("batch_block") == t["block"]
+        assert k.get_option("batch_ctas_per_sm") == t["ctas_per_sm"]
+        assert k.stats()["batch_block"] == t["block"]
+        check_batch(k, gv, off, adj)  # later calls run the tuned shape
+
+
+def _relabel(ns, lists, seed):
+    """Each graph with its vertex ids permuted: the same sizes, another CSR."""
+    rng = np.random.default_rng(seed)
+    out = []
+    for n, (s, d) in zip(ns, lists):
+        p = rng.permutation(n).astype(np.int32)
+        out.append((p[s], p[d]))
+    return out
+
+
+def test_batched_call_captured_in_cuda_graph():
+    """A batched call captured in a CUDA graph replays exactly, also after the
+    input buffers were refilled with other graphs of the same sizes."""
+    spec, eoff, s, d, ns, lists = spec_batch(32, nmin=50, nmax=4000, seed=33)
+    gv, off, adj = oracle_segmented(ns, lists)
+    gv2, off2, adj2 = oracle_segmented(ns, _relabel(ns, lists, 9))
+    assert len(adj2) == len(adj) and (gv2 == gv).all()
+    want1, km1 = oracle.bz_batch(gv, off, adj)
+    want2, km2 = oracle.bz_batch(gv2, off2, adj2)
+    with KCore(0) as k:
+        dgv, doff, dadj = _t(gv, np.int64), _t(off, np.int64), _t(adj, np.int32)
+        core = torch.empty(int(gv[-1]), dtype=torch.int32, device="cuda:0")
+        km = torch.empty(len(ns), dtype=torch.int32, device="cuda:0")
+        k.decompose_batched(dgv, doff, dadj, core, km)  # sizes the workspace outside the capture
+        graph = torch.cuda.CUDAGraph()
+        with torch.cuda.graph(graph):
+            k.decompose_batched(dgv, doff, dadj, core, km, sync=False)
+        for o, a, want, wkm in [(off, adj, want1, km1), (off2, adj2, want2, km2)]:
+            doff.copy_(_t(o, np.int64))
+            dadj.copy_(_t(a, np.int32))
+            core.fill_(-7)
+            km.fill_(-7)
+            graph.replay()
+            torch.cuda.synchronize()
+            k.sync()
+            np.testing.assert_array_equal(core.cpu().numpy(), want)
+            np.testing.assert_array_equal(km.cpu().numpy(), wkm)
