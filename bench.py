@@ -360,7 +360,7 @@ def run_batched(args):
     ws, rank, local = dist_env()
     torch.cuda.set_device(local)
     dev = torch.device("cuda", local)
-    G = WORKLOADS["batched"]["G"]
+    G = args.graphs or WORKLOADS["batched"]["G"]
     t0 = time.perf_counter()
     spec, gv, eoff, s, d = _batch_inputs(G)
     gen_s = time.perf_counter() - t0
@@ -642,6 +642,9 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
     ap.add_argument("--workload", default="rmat24", choices=sorted(WORKLOADS))
+    ap.add_argument("--graphs", type=int, default=0,
+                    help="batched workload: first G graphs of the distribution (default 4096; "
+                         "smaller batches are for profiling)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     args = ap.parse_args()
     if args.impl == "reference":

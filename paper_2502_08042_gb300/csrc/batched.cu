@@ -82,9 +82,12 @@ __device__ __forceinline__ int block_min(int x, BatchShared<BLOCK>& sh) {
 }
 
 // d~ read: shared memory, or L2 (atomics are performed in L2, so a global
-// d~ must not be read through L1).
-__device__ __forceinline__ int load_deg(const int* D, int v, bool in_smem) {
-  return in_smem ? D[v] : __ldcg(D + v);
+// d~ must not be read through L1). Global d~ accesses carry an evict-last
+// hint and the once-read lists (active list, frontiers, adjacency) stream
+// with evict-first loads and stores: with hundreds of large graphs in flight
+// their state exceeds L2, and the d~ lines are the ones that are hit again.
+__device__ __forceinline__ int load_deg(const int* D, int v, bool in_smem, uint64_t pol) {
+  return in_smem ? D[v] : ld_cg_keep(D + v, pol);
 }
 
 // One pass over the active list after level k: entries with D > k survive
@@ -93,7 +96,7 @@ __device__ __forceinline__ int load_deg(const int* D, int v, bool in_smem) {
 // Returns the survivors; *nf gets the number written to F.
 template <int BLOCK>
 __device__ int compact_active(const int* A, int la, int n, int* out, int* F, const int* D, bool in_smem,
-                              int k, BatchShared<BLOCK>& sh, int* dmin, int* nf) {
+                              int k, BatchShared<BLOCK>& sh, int* dmin, int* nf, uint64_t pol) {
   int written = 0, wf = 0, lmin = INT_MAX;
   for (int base = 0; base < la; base += BLOCK * kScanItems) {
     int v[kScanItems];
@@ -103,14 +106,14 @@ __device__ int compact_active(const int* A, int la, int n, int* out, int* F, con
       int i = base + q * BLOCK + threadIdx.x;
       v[q] = -1;
       if (i < la) {
-        int x = A[i];
+        int x = __ldcs(A + i);
         v[q] = (unsigned)x < (unsigned)n ? x : -1;  // ids are < n by construction; checked anyway
       }
     }
 #pragma unroll
     for (int q = 0; q < kScanItems; q++) {
       if (v[q] >= 0) {
-        int d = load_deg(D, v[q], in_smem);
+        int d = load_deg(D, v[q], in_smem, pol);
         if (d > k) {
           keep |= 1u << q;
           lmin = min(lmin, d);
@@ -124,8 +127,8 @@ __device__ int compact_active(const int* A, int la, int n, int* out, int* F, con
     int pk = written + (pos & 0xffff), pf = wf + (pos >> 16);
 #pragma unroll
     for (int q = 0; q < kScanItems; q++) {
-      if ((keep >> q) & 1u) out[pk++] = v[q];
-      if ((front >> q) & 1u) F[pf++] = v[q];
+      if ((keep >> q) & 1u) __stcs(out + pk++, v[q]);
+      if ((front >> q) & 1u) __stcs(F + pf++, v[q]);
     }
     written += tot & 0xffff;
     wf += tot >> 16;
@@ -138,7 +141,7 @@ __device__ int compact_active(const int* A, int la, int n, int* out, int* F, con
 // Selection of the frontier: entries of A with D[v] == k.
 template <int BLOCK>
 __device__ int select_frontier(const int* A, int la, int n, int* F, const int* D, bool in_smem, int k,
-                               BatchShared<BLOCK>& sh) {
+                               BatchShared<BLOCK>& sh, uint64_t pol) {
   int written = 0;
   for (int base = 0; base < la; base += BLOCK * kScanItems) {
     int v[kScanItems];
@@ -148,19 +151,19 @@ __device__ int select_frontier(const int* A, int la, int n, int* F, const int* D
       int i = base + q * BLOCK + threadIdx.x;
       v[q] = -1;
       if (i < la) {
-        int x = A[i];
+        int x = __ldcs(A + i);
         v[q] = (unsigned)x < (unsigned)n ? x : -1;  // ids are < n by construction; checked anyway
       }
     }
 #pragma unroll
     for (int q = 0; q < kScanItems; q++)
-      if (v[q] >= 0 && load_deg(D, v[q], in_smem) == k) take |= 1u << q;
+      if (v[q] >= 0 && load_deg(D, v[q], in_smem, pol) == k) take |= 1u << q;
     int tot;
     int pos = block_excl_scan(__popc(take), sh, &tot);
     int p = written + pos;
 #pragma unroll
     for (int q = 0; q < kScanItems; q++)
-      if ((take >> q) & 1u) F[p++] = v[q];
+      if ((take >> q) & 1u) __stcs(F + p++, v[q]);
     written += tot;
   }
   __syncthreads();  // the frontier is read by other threads next
@@ -179,6 +182,7 @@ __device__ void peel_one_graph(const GraphDesc& gd, int smem_deg_max, int* statu
   }
   const int n = (int)gd.n;
   const bool in_smem = n <= smem_deg_max;
+  const uint64_t pol = l2_evict_last_policy();
   int* D = in_smem ? sdeg : gd.deg;
   const long long* O = gd.off;
   const int* adj = gd.adj;
@@ -199,8 +203,9 @@ __device__ void peel_one_graph(const GraphDesc& gd, int smem_deg_max, int* statu
       o1 = o0;
     }
     int d = (int)(o1 - o0);
-    D[v] = d;
-    A0[v] = v;
+    if (in_smem) D[v] = d;
+    else st_keep(D + v, d, pol);
+    __stcs(A0 + v, v);
     lmin = min(lmin, d);
   }
   int k = block_min(lmin, sh);  // also orders the writes above
@@ -213,13 +218,13 @@ __device__ void peel_one_graph(const GraphDesc& gd, int smem_deg_max, int* statu
   int* An = A1;
   int la = n;
   int kmax = 0;
-  int nf = select_frontier<BLOCK>(A, la, n, F0, D, in_smem, k, sh);
+  int nf = select_frontier<BLOCK>(A, la, n, F0, D, in_smem, k, sh, pol);
   for (;;) {
     int* Fc = F0;
     int* Fn = F1;
     while (nf > 0) {
       for (int i = tid; i < nf; i += BLOCK) {
-        int v = Fc[i];
+        int v = __ldcs(Fc + i);
         if ((unsigned)v < (unsigned)n) core[v] = k;
         else flag_bad(status, 6, v, &sh.bad);
       }
@@ -230,7 +235,7 @@ __device__ void peel_one_graph(const GraphDesc& gd, int smem_deg_max, int* statu
         int len = 0;
         long long st = 0;
         if (tid < cnum) {
-          int v = Fc[c0 + tid];
+          int v = __ldcs(Fc + c0 + tid);
           if ((unsigned)v < (unsigned)n) {
             st = O[v];
             long long e = O[v + 1];
@@ -274,7 +279,15 @@ __device__ void peel_one_graph(const GraphDesc& gd, int smem_deg_max, int* statu
 #pragma unroll
           for (int q = 0; q < kBatchIlp; q++) {
             bool cross = false;
-            if (u[q] >= 0 && load_deg(D, u[q], in_smem) > k) cross = atomicSub(&D[u[q]], 1) == k + 1;
+            // induced degrees in shared memory: read first, decrement the live
+            // ones. In global memory each access is an L2 request, so the
+            // decrement goes unread: a vertex at or below k is already in a
+            // frontier (or peeled), never returns k + 1, and its d~ is only
+            // compared with levels above k afterwards.
+            if (u[q] >= 0) {
+              if (in_smem) cross = D[u[q]] > k && atomicSub(&D[u[q]], 1) == k + 1;
+              else cross = atom_add_keep(D + u[q], -1, pol) == k + 1;
+            }
             unsigned m = __ballot_sync(kFull, cross);
             if (m) {
               int base = 0;
@@ -282,7 +295,7 @@ __device__ void peel_one_graph(const GraphDesc& gd, int smem_deg_max, int* statu
               base = __shfl_sync(kFull, base, __ffs(m) - 1);
               int pos = base + __popc(m & lanemask_lt());
               if (cross) {
-                if (pos < n) Fn[pos] = u[q];
+                if (pos < n) __stcs(Fn + pos, u[q]);
                 else flag_bad(status, 7, pos, &sh.bad);
               }
             }
@@ -302,12 +315,12 @@ __device__ void peel_one_graph(const GraphDesc& gd, int smem_deg_max, int* statu
     // rest is the next non-empty level; vertices at k+1 are collected on the
     // way in case that level is the next one
     int dmin;
-    la = compact_active<BLOCK>(A, la, n, An, F0, D, in_smem, k, sh, &dmin, &nf);
+    la = compact_active<BLOCK>(A, la, n, An, F0, D, in_smem, k, sh, &dmin, &nf, pol);
     int* t = A;
     A = An;
     An = t;
     if (la == 0) break;
-    if (dmin != k + 1) nf = select_frontier<BLOCK>(A, la, n, F0, D, in_smem, dmin, sh);
+    if (dmin != k + 1) nf = select_frontier<BLOCK>(A, la, n, F0, D, in_smem, dmin, sh, pol);
     k = dmin;
   }
   if (tid == 0) *gd.kmax = kmax;

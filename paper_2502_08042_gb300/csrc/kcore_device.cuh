@@ -38,6 +38,31 @@ __device__ __forceinline__ int ld_acquire_s32(const int* p) {
 // evict-first in L2 so the induced-degree array stays resident.
 __device__ __forceinline__ int ld_stream_s32(const int* p) { return __ldcs(p); }
 
+// L2 eviction priority for data that should stay resident (e.g. induced
+// degrees updated by atomics while streamed data passes through L2).
+__device__ __forceinline__ uint64_t l2_evict_last_policy() {
+  uint64_t p;
+  asm volatile("createpolicy.fractional.L2::evict_last.b64 %0, 1.0;" : "=l"(p));
+  return p;
+}
+__device__ __forceinline__ int ld_cg_keep(const int* a, uint64_t pol) {
+  int v;
+  asm volatile("ld.global.cg.L2::cache_hint.s32 %0, [%1], %2;" : "=r"(v) : "l"(a), "l"(pol) : "memory");
+  return v;
+}
+__device__ __forceinline__ void st_keep(int* a, int v, uint64_t pol) {
+  asm volatile("st.global.L2::cache_hint.s32 [%0], %1, %2;" ::"l"(a), "r"(v), "l"(pol) : "memory");
+}
+// atomic add returning the old value, with an L2 eviction-priority hint
+__device__ __forceinline__ int atom_add_keep(int* a, int v, uint64_t pol) {
+  int old;
+  asm volatile("atom.global.L2::cache_hint.add.s32 %0, [%1], %2, %3;"
+               : "=r"(old)
+               : "l"(a), "r"(v), "l"(pol)
+               : "memory");
+  return old;
+}
+
 // Warp inclusive prefix sum.
 template <typename T>
 __device__ __forceinline__ T warp_incl_scan(T x, int lane) {
