@@ -304,7 +304,7 @@ kcore_status kcore_server_destroy(kcore_server s);
  * cannot accept the device-wide synchronisation an allocation can cause. This
  * call allocates nothing (no cudaMalloc, no cudaFree, no allocating library
  * routine) and needs no handle: its scratch memory is one fixed array in the
- * library's device memory (about 25 MB), present on every GPU that loads the
+ * library's device memory (about 26 MB), present on every GPU that loads the
  * library until the process exits. The caller still passes the graph and the
  * output arrays, exactly as for kcore_decompose (same layout and meaning):
  *   n <= KCORE_STATIC_MAX_VERTICES, m <= KCORE_STATIC_MAX_ARCS; larger graphs

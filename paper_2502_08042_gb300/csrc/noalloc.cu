@@ -23,7 +23,7 @@ namespace {
 
 constexpr long long kStaticMaxN = KCORE_STATIC_MAX_VERTICES;
 constexpr long long kStaticMaxM = KCORE_STATIC_MAX_ARCS;
-constexpr int kStaticSlice = 512;
+constexpr int kStaticSlice = 128;
 constexpr long long kStaticQcap = kStaticMaxN + (kStaticMaxM + kStaticSlice - 1) / kStaticSlice + 1;
 // levels: 2 * sqrt(m) + 8 rounds at most (see the handle's workspace layout)
 constexpr int kStaticMaxRounds = 2 * 4096 + 8;
@@ -82,7 +82,7 @@ extern "C" kcore_status kcore_decompose_static(int64_t n, int64_t m, const int64
         cudaGetLastError();
         return KCORE_ERR_CUDA;
       }
-      d.ctas_per_sm = kc::peel_max_ctas_per_sm();
+      d.ctas_per_sm = kc::bsp_max_ctas_per_sm();
       if (d.ctas_per_sm <= 0 || d.sms <= 0) return KCORE_ERR_CUDA;
       d.scratch = (char*)p;
       d.ready = true;
@@ -129,14 +129,15 @@ extern "C" kcore_status kcore_decompose_static(int64_t n, int64_t m, const int64
     long long gmax = (long long)d.sms * d.ctas_per_sm;
     long long want = (n + m / 8 + 2047) / 2048;
     int grid = (int)std::max<long long>(1, std::min(want, gmax));
-    a.take_div = grid * (kc::peel_block_size() / 32);
+    a.take_div = grid * (kc::bsp_block_size() / 32);
+    a.local_batches = 8;
     // the array keeps the previous call's contents: clear what must start at
-    // zero (control block, this call's round records) and mark the queue empty
+    // zero (control block, this call's round records); the bulk-synchronous
+    // peel reads only queue slots written earlier in the same call
     if ((e = cudaMemsetAsync(ws + kOffCtl, 0, kOffRounds + sizeof(kc::RoundRec) * (size_t)max_rounds,
                              stream)) != cudaSuccess)
       goto cuda_error;
-    if ((e = cudaMemsetAsync(ws + kOffQ, 0xff, 8 * (size_t)qcap, stream)) != cudaSuccess) goto cuda_error;
-    if ((e = kc::peel_launch(a, grid, stream)) != cudaSuccess) goto cuda_error;
+    if ((e = kc::bsp_launch(a, grid, stream)) != cudaSuccess) goto cuda_error;
     if ((e = cudaStreamSynchronize(stream)) != cudaSuccess) goto cuda_error;
     int status = 0;
     if ((e = cudaMemcpy(&status, &((kc::PeelCtl*)(ws + kOffCtl))->status, sizeof(int),

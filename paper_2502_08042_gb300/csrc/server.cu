@@ -157,7 +157,7 @@ struct LargeLayout {
   long long qcap;
   int max_rounds;
 };
-constexpr int kLargeSlice = 512;
+constexpr int kLargeSlice = 64;
 LargeLayout large_layout(long long n, long long m) {
   LargeLayout L{};
   L.qcap = n + (m + kLargeSlice - 1) / kLargeSlice + 1;
@@ -224,7 +224,7 @@ kcore_status kcore_server_create(kcore_server* out, int device, const kcore_serv
   }
   s->cfg = c;
   cudaDeviceGetAttribute(&s->sms, cudaDevAttrMultiProcessorCount, device);
-  s->peel_ctas_per_sm = kc::peel_max_ctas_per_sm();
+  s->peel_ctas_per_sm = kc::bsp_max_ctas_per_sm();
   if (cudaMalloc(&s->pool, c.pool_bytes) != cudaSuccess) {
     cudaGetLastError();
     delete s;
@@ -419,10 +419,10 @@ kcore_status kcore_server_poll(kcore_server s, int64_t* tickets_out, int32_t* km
     long long want = (r.n + r.m / 8 + 2047) / 2048;
     long long gmax = (long long)s->sms * s->peel_ctas_per_sm;
     int grid = (int)std::max<long long>(1, std::min(want, gmax));
-    a.take_div = grid * (kc::peel_block_size() / 32);
+    a.take_div = grid * (kc::bsp_block_size() / 32);
+    a.local_batches = 8;
     e = cudaMemsetAsync(ws, 0, L.deg, s->large);
-    if (e == cudaSuccess) e = cudaMemsetAsync(ws + L.q, 0xff, 8 * (size_t)L.qcap, s->large);
-    if (e == cudaSuccess) e = kc::peel_launch(a, grid, s->large);
+    if (e == cudaSuccess) e = kc::bsp_launch(a, grid, s->large);
     if (e == cudaSuccess) e = cudaEventRecord(r.ev, s->large);
     if (e != cudaSuccess) {
       cudaGetLastError();
