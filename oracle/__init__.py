@@ -57,6 +57,8 @@ def _L():
             lib.oc_alg1.restype = ctypes.c_int
             lib.oc_check.argtypes = [i64, p, p, p, p]
             lib.oc_check.restype = ctypes.c_int
+            lib.oc_kcore_mask.argtypes = [i64, p, p, ctypes.c_int32, p]
+            lib.oc_kcore_mask.restype = i64
             _lib = lib
     return _lib
 
@@ -125,6 +127,20 @@ def check(n: int, off, adj, core):
     if rc < 0:
         raise MemoryError("oracle.check")
     return int(rc), int(bad.value)
+
+
+def kcore_mask(n: int, off, adj, kprime: int):
+    """Membership of every vertex in the k'-core (App. B): int32 1/0 by
+    repeated deletion of vertices whose remaining degree is below kprime.
+    Returns (mask, size)."""
+    off = _c(off, np.int64)
+    adj = _c(adj, np.int32)
+    mask = np.zeros(max(n, 0), np.int32)
+    size = _L().oc_kcore_mask(n, off.ctypes.data, adj.ctypes.data if len(adj) else None, int(kprime),
+                              mask.ctypes.data)
+    if size < 0:
+        raise MemoryError("oracle.kcore_mask")
+    return mask, int(size)
 
 
 def kmax(core) -> int:

@@ -19,6 +19,8 @@
  *            those that land on k; after the round keep only vertices with
  *            induced degree above k. It also counts the quantities of
  *            Theorem 1 (sum of active-set sizes, frontier insertions).
+ *   oc_kcore_mask  The k'-core alone (App. B): repeated deletion of the
+ *            vertices whose remaining degree is below k'.
  *   oc_check A certificate check that needs no decomposition: (i) every v
  *            with value c has at least c neighbours with value >= c (so the
  *            set {value >= c} has minimum degree >= c and lies inside the
@@ -313,4 +315,47 @@ int oc_check(int64_t n, const int64_t* off, const int32_t* adj, const int32_t* v
   }
   free(bstart); free(byval); free(left); free(gone); free(queued); free(q);
   return rc;
+}
+
+/* ------------------------------------------------------------------------- */
+/* The k'-core (App. B, "Maximum k-Core Subgraph"; the k-core definition of
+ * Sec. 2): the largest subgraph in which every vertex has degree >= kp,
+ * obtained by deleting, as long as one exists, a vertex whose degree among the
+ * vertices not yet deleted is below kp. A vertex is queued when its remaining
+ * degree first drops below kp (or starts below it) and deleted when taken from
+ * the queue; deleting it lowers the remaining degree of its neighbours.
+ * mask[v] = 1 when v is in the k'-core, else 0. Returns the k'-core's vertex
+ * count, or -1 when out of memory. */
+int64_t oc_kcore_mask(int64_t n, const int64_t* off, const int32_t* adj, int32_t kp, int32_t* mask) {
+  if (n <= 0) return 0;
+  int64_t* left = (int64_t*)malloc(sizeof(int64_t) * (size_t)n);
+  int32_t* q = (int32_t*)malloc(sizeof(int32_t) * (size_t)n);
+  if (!left || !q) {
+    free(left);
+    free(q);
+    return -1;
+  }
+  int64_t qt = 0;
+  for (int64_t v = 0; v < n; v++) {
+    left[v] = off[v + 1] - off[v];
+    mask[v] = 1;
+    if (left[v] < kp) {
+      mask[v] = 0; /* queued = deleted once processed */
+      q[qt++] = (int32_t)v;
+    }
+  }
+  for (int64_t qh = 0; qh < qt; qh++) {
+    int32_t v = q[qh];
+    for (int64_t j = off[v]; j < off[v + 1]; j++) {
+      int32_t u = adj[j];
+      if (!mask[u]) continue; /* already deleted or queued */
+      if (--left[u] < kp) {
+        mask[u] = 0;
+        q[qt++] = u;
+      }
+    }
+  }
+  free(left);
+  free(q);
+  return n - qt;
 }

@@ -236,3 +236,82 @@ def test_bz_batch_matches_union():
     np.testing.assert_array_equal(core, want)
     for g in range(len(spec)):
         assert km[g] == want[gv[g]:gv[g + 1]].max()
+
+
+# ----------------------------------------------------------------- k'-core (App. B)
+def _nbrs(n, off, adj):
+    return [set(adj[off[v]:off[v + 1]].tolist()) for v in range(n)]
+
+
+def _subset_union_core(n, nbrs, kp):
+    """The k'-core from the definition by enumeration: the union of every
+    vertex set whose induced subgraph has minimum degree >= kp (that union is
+    itself such a set, the largest one)."""
+    members = set()
+    for bits in range(1, 1 << n):
+        S = [v for v in range(n) if bits >> v & 1]
+        Sset = set(S)
+        if all(len(nbrs[v] & Sset) >= kp for v in S):
+            members |= Sset
+    return members
+
+
+@pytest.mark.parametrize("seed", range(40))
+def test_kcore_mask_matches_subset_enumeration(seed):
+    rng = np.random.default_rng(seed)
+    n = int(rng.integers(1, 10))
+    n, s, d = gg.small_random(n, int(rng.integers(0, 3 * n + 1)), seed=seed)
+    off, adj = _csr(n, s, d)
+    nb = _nbrs(n, off, adj)
+    for kp in range(0, n + 1):
+        mask, size = oracle.kcore_mask(n, off, adj, kp)
+        want = _subset_union_core(n, nb, kp) if kp > 0 else set(range(n))
+        assert set(np.flatnonzero(mask).tolist()) == want, (seed, kp)
+        assert size == len(want)
+
+
+@pytest.mark.parametrize("seed", range(30))
+def test_kcore_mask_matches_definition_and_coreness(seed):
+    """Against the pure-Python deletion of the definition (brute.py) and
+    against Batagelj-Zaversnik coreness: v is in the k'-core iff coreness >= k'."""
+    rng = np.random.default_rng(100 + seed)
+    n = int(rng.integers(5, 60))
+    n, s, d = gg.small_random(n, int(rng.integers(n, 6 * n)), seed=100 + seed)
+    off, adj = _csr(n, s, d)
+    core = oracle.bz(n, off, adj)
+    nb = _nbrs(n, off, adj)
+    for kp in range(0, int(core.max()) + 3):
+        mask, size = oracle.kcore_mask(n, off, adj, kp)
+        np.testing.assert_array_equal(mask, (core >= kp).astype(np.int32))
+        assert set(np.flatnonzero(mask).tolist()) == oracle.brute.k_core_members(n, nb, kp)
+        assert size == int(mask.sum())
+
+
+@pytest.mark.parametrize("name,g,kp,inside", [
+    ("K12 k'=11", gg.complete(12), 11, True), ("K12 k'=12", gg.complete(12), 12, False),
+    ("C30 k'=2", gg.cycle(30), 2, True), ("C30 k'=3", gg.cycle(30), 3, False),
+    ("P50 k'=1", gg.path(50), 1, True), ("P50 k'=2", gg.path(50), 2, False),
+    ("star k'=1", gg.star(40), 1, True), ("star k'=2", gg.star(40), 2, False),
+    ("grid k'=2", gg.grid2d(9, 7), 2, True), ("grid k'=3", gg.grid2d(9, 7), 3, False),
+    ("K5,8 k'=5", gg.complete_bipartite(5, 8), 5, True), ("K5,8 k'=6", gg.complete_bipartite(5, 8), 6, False),
+], ids=lambda x: x if isinstance(x, str) else "")
+def test_kcore_mask_closed_forms(name, g, kp, inside):
+    """Closed forms: every vertex is in the k'-core or none is."""
+    n, s, d = g
+    off, adj = _csr(n, s, d)
+    mask, size = oracle.kcore_mask(n, off, adj, kp)
+    assert (mask == (1 if inside else 0)).all() and size == (n if inside else 0)
+
+
+def test_kcore_mask_staircase_levels():
+    """The staircase with K levels: its k'-core holds exactly the vertices of
+    coreness >= k', and every member keeps >= k' neighbours inside it."""
+    n, s, d = gg.staircase(40)
+    off, adj = _csr(n, s, d)
+    core = oracle.bz(n, off, adj)
+    for kp in (1, 7, 20, 39, 40, 41):
+        mask, size = oracle.kcore_mask(n, off, adj, kp)
+        np.testing.assert_array_equal(mask, (core >= kp).astype(np.int32))
+        inside = np.flatnonzero(mask)
+        for v in inside:
+            assert mask[adj[off[v]:off[v + 1]]].sum() >= kp
