@@ -8,7 +8,7 @@ HBM; the CSR build from the raw edge list is timed once beside it. The metric
 is undirected edges per second (each edge counted once per decomposition).
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--impl gb300|reference]
-                    [--workload rmat24|rmat22|er10k|knn|batched|served]
+                    [--workload rmat24|rmat22|er10k|knn|batched|served|kquery]
 
 Other workloads (one JSON line each): `knn` is the 10-NN graph of 2^24 uniform
 points plus 64 planted cliques; `batched` decomposes the 4,096-graph batch in
@@ -60,6 +60,7 @@ WORKLOADS = {
     "knn": dict(kind="knn", n=1 << 24, k=10, cliques=64),
     "batched": dict(kind="batched", G=4096),
     "served": dict(kind="served", requests=2000),
+    "kquery": dict(kind="kquery", scale=24, ef=16, kprimes=(16, 128, 1024)),
 }
 
 
@@ -173,6 +174,95 @@ def cpu_oracle_baseline(scale: int = 22, reps: int = 1):
     return {"value": (len(adj) // 2) / t, "unit": UNIT, "cores": 1, "kind": "oracle",
             "sample": f"Batagelj-Zaversnik on R-MAT scale {scale} (same generator, edge factor 16; "
                       f"{len(adj) // 2} undirected edges), best of {reps}, {t:.2f} s"}
+
+
+def run_kquery(args):
+    """The k'-core query (App. B) on R-MAT scale 24 at thresholds 16, 128 and
+    1024 (the paper's range is 16..2048), beside the full decomposition of the
+    same graph; value = undirected edges per second at the middle threshold."""
+    import torch
+
+    import graphgen as gg
+    from paper_2502_08042_gb300 import KCore
+
+    ws, rank, local = dist_env()
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    w = WORKLOADS["kquery"]
+    n = 1 << w["scale"]
+    s, d = gg.rmat(w["scale"], w["ef"], seed=1, perm_seed=2)
+    k = KCore(local)
+    off, adj_buf, m_t = k.build_csr(n, torch.from_numpy(s).to(dev), torch.from_numpy(d).to(dev), sync=False)
+    k.sync()
+    del s, d
+    m = int(m_t.item())
+    adj = adj_buf[:m].clone()
+    del adj_buf
+    torch.cuda.empty_cache()
+    mu = m // 2
+    flush = torch.empty(2 * L2_BYTES // 4, dtype=torch.int32, device=dev)
+    mask = torch.empty(n, dtype=torch.int32, device=dev)
+    size = torch.empty(1, dtype=torch.int64, device=dev)
+    core = torch.empty(n, dtype=torch.int32, device=dev)
+    kmax = torch.empty(1, dtype=torch.int32, device=dev)
+
+    def timed(fn):
+        for _ in range(args.warmup):
+            fn()
+            k.sync()
+        evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+               for _ in range(args.steps)]
+        torch.cuda.synchronize()
+        for i in range(args.steps):
+            flush.zero_()
+            evs[i][0].record()
+            fn()
+            evs[i][1].record()
+        torch.cuda.synchronize()
+        k.sync()
+        return sum(a.elapsed_time(b) for a, b in evs) / args.steps
+
+    with ClockSampler(local) as clk:
+        full_ms = timed(lambda: k.decompose(off, adj, core, kmax, sync=False))
+        per = []
+        for kp in w["kprimes"]:
+            ms = timed(lambda: k.core_mask(off, adj, kp, mask, size, sync=False))
+            st = k.stats()
+            c = core.cpu().numpy()
+            same = bool((mask.cpu().numpy() == (c >= kp)).all())
+            per.append({"kprime": kp, "ms": ms, "core_size": int(size.item()), "passes": st["passes"],
+                        "matches_coreness_ge_kprime": same, "edges_per_s": mu / (ms / 1e3)})
+    mid = per[len(per) // 2]
+    cpu = None
+    if not args.no_cpu_baseline:
+        import oracle
+        ss, dd = gg.rmat(22, 16, seed=1, perm_seed=2)
+        o2, a2 = oracle.build_csr(1 << 22, ss, dd)
+        t0 = time.perf_counter()
+        oracle.kcore_mask(1 << 22, o2, a2, mid["kprime"])
+        t = time.perf_counter() - t0
+        cpu = {"value": (len(a2) // 2) / t, "unit": UNIT, "cores": 1, "kind": "oracle",
+               "sample": f"repeated deletion (k'={mid['kprime']}) on R-MAT scale 22, {len(a2) // 2} "
+                         f"undirected edges, {t:.2f} s"}
+    peak, peak_kind = load_peaks()
+    bmin = 8 * (n + 1) + 4 * m + 8 * n  # offsets, lists once, d~ written and read, mask written
+    out = {
+        "metric": METRIC, "value": mid["edges_per_s"], "unit": UNIT, "n_gpus": 1, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": mid["ms"], "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "int32", "data": "synthetic",
+        "config": {"workload": f"kquery: k'-core of R-MAT scale {w['scale']} edge factor {w['ef']}",
+                   "n": n, "arcs": m, "kprime": mid["kprime"], "per_kprime": per,
+                   "full_decomposition_ms": full_ms,
+                   "l2": "inputs larger than L2 and a 258 MB buffer written between timed steps"},
+        "roofline": {"bound": "hbm", "achieved": bmin / (mid["ms"] / 1e3) / 1e9, "peak": peak, "unit": "GB/s",
+                     "frac": bmin / (mid["ms"] / 1e3) / 1e9 / peak, "traffic": None, "peak_kind": peak_kind,
+                     "algorithmic_bytes": bmin, "kernel": "peel_bsp"},
+        "e2e": None, "gpu_launches": args.steps, "cpu_baseline": cpu,
+    }
+    cl = clk.summary()
+    if cl:
+        out["clocks"] = cl
+    print(json.dumps(out), flush=True)
 
 
 def run_reference(args):
@@ -651,6 +741,8 @@ def main():
         run_reference(args)
     elif args.workload == "batched":
         run_batched(args)
+    elif args.workload == "kquery":
+        run_kquery(args)
     elif args.workload == "served":
         run_served(args)
     else:

@@ -319,6 +319,19 @@ kcore_status kcore_server_destroy(kcore_server s);
 kcore_status kcore_decompose_static(int64_t n, int64_t m, const int64_t* offsets, const int32_t* adj,
                                     int32_t* coreness_out, int32_t* kmax_out, kcore_stream_t stream);
 
+/* The maximum k'-core query (App. B, "Maximum k-Core Subgraph": the peeling
+ * framework with a single threshold instead of increasing levels). mask_out[v]
+ * receives 1 when v lies in the k'-core -- the largest subgraph in which every
+ * vertex has degree >= kprime, i.e. the vertices of coreness >= kprime -- and
+ * 0 otherwise; *size_out (device int64, may be NULL) receives the k'-core's
+ * vertex count. One peel at level kprime - 1 on the bulk-synchronous kernel:
+ * a scan takes every vertex whose degree is below kprime, and subround passes
+ * remove the vertices whose decrement lands them below kprime. kprime <= 0
+ * keeps every vertex. Input layout, workspace and errors as kcore_decompose
+ * (asynchronous on `stream`; kcore_sync_status reports device errors). */
+kcore_status kcore_core_mask(kcore_handle h, int64_t n, int64_t m, const int64_t* offsets, const int32_t* adj,
+                             int32_t kprime, int32_t* mask_out, int64_t* size_out, kcore_stream_t stream);
+
 /* Waits for the stream of the handle's last call and returns the status the
  * device recorded (KCORE_OK, KCORE_ERR_TIMEOUT, ...). */
 kcore_status kcore_sync_status(kcore_handle h);

@@ -119,6 +119,7 @@ SIGNATURES = {
     "kcore_set_workspace": ([c_p, c_p, c_sz], ctypes.c_int),
     "kcore_decompose": ([c_p, c_i64, c_i64, c_p, c_p, c_p, c_p, c_p], ctypes.c_int),
     "kcore_decompose_host": ([c_p, c_i64, c_i64, c_p, c_p, c_p, c_p, c_p], ctypes.c_int),
+    "kcore_core_mask": ([c_p, c_i64, c_i64, c_p, c_p, ctypes.c_int32, c_p, c_p, c_p], ctypes.c_int),
     "kcore_sync_status": ([c_p], ctypes.c_int),
     "kcore_get_stats": ([c_p, ctypes.POINTER(Stats)], ctypes.c_int),
     "kcore_get_trace": ([c_p, c_p, c_i64, ctypes.POINTER(c_i64)], ctypes.c_int),

@@ -267,15 +267,15 @@ kcore_status kcore_set_workspace(kcore_handle h, void* ptr, size_t bytes) {
   return KCORE_OK;
 }
 
-kcore_status kcore_decompose(kcore_handle h, int64_t n, int64_t m, const int64_t* offsets,
-                             const int32_t* adj, int32_t* coreness_out, int32_t* kmax_out,
-                             kcore_stream_t stream_) {
-  if (!h) return KCORE_ERR_INVALID;
-  cudaStream_t stream = (cudaStream_t)stream_;
-  if (n < 0 || m < 0 || n > INT32_MAX - 1) return fail(h, KCORE_ERR_INVALID, "n or m out of range");
-  if (!kmax_out) return fail(h, KCORE_ERR_INVALID, "kmax_out is null");
-  if (n > 0 && (!offsets || !coreness_out)) return fail(h, KCORE_ERR_INVALID, "null offsets/coreness");
-  if (m > 0 && !adj) return fail(h, KCORE_ERR_INVALID, "null adj with m > 0");
+}  // extern "C"
+
+namespace {
+
+// One single-graph peel on the handle's workspace: the decomposition, or
+// (threshold) the k'-core query, which only the bulk-synchronous kernel runs.
+kcore_status peel_call(kcore_ctx* h, int64_t n, int64_t m, const int64_t* offsets, const int32_t* adj,
+                       int32_t* out, int32_t* kmax_out, cudaStream_t stream, bool threshold, int32_t kprime,
+                       int64_t* size_out) {
   DeviceGuard g(h->device);
   if (!g.ok) return fail(h, KCORE_ERR_CUDA, "cudaSetDevice failed");
   h->err.clear();
@@ -286,11 +286,14 @@ kcore_status kcore_decompose(kcore_handle h, int64_t n, int64_t m, const int64_t
   h->last_stream = stream;
   h->pending = true;
   if (n == 0) {
-    cudaError_t e = cudaMemsetAsync(kmax_out, 0, sizeof(int32_t), stream);
+    cudaError_t e = cudaSuccess;
+    if (kmax_out) e = cudaMemsetAsync(kmax_out, 0, sizeof(int32_t), stream);
+    if (e == cudaSuccess && size_out) e = cudaMemsetAsync(size_out, 0, sizeof(int64_t), stream);
     if (e != cudaSuccess) return cuda_fail(h, e, "cudaMemsetAsync");
     return KCORE_OK;
   }
-  const int slice = effective_slice(h);
+  const int mode = threshold ? 2 : effective_mode(h);
+  const int slice = h->opt[KCORE_OPT_SLICE_ARCS] > 0 ? (int)h->opt[KCORE_OPT_SLICE_ARCS] : (mode == 2 ? 64 : 512);
   PeelLayout L = peel_layout(n, m, slice);
   kcore_status st = ensure_ws(h, L.total);
   if (st != KCORE_OK) return st;
@@ -300,7 +303,7 @@ kcore_status kcore_decompose(kcore_handle h, int64_t n, int64_t m, const int64_t
   a.m = m;
   a.off = (const long long*)offsets;
   a.adj = adj;
-  a.core = coreness_out;
+  a.core = out;
   a.kmax_out = kmax_out;
   a.deg = (int*)(ws + L.deg);
   a.A0 = (int*)(ws + L.a0);
@@ -320,8 +323,10 @@ kcore_status kcore_decompose(kcore_handle h, int64_t n, int64_t m, const int64_t
   a.inject_stall = (int)h->opt[KCORE_OPT_TEST_STALL];
   a.trace = h->opt[KCORE_OPT_TRACE] ? (unsigned long long*)(ws + L.trace) : nullptr;
   a.local_batches = h->opt[KCORE_OPT_LOCAL_BATCHES] > 0 ? (int)h->opt[KCORE_OPT_LOCAL_BATCHES] : INT32_MAX;
+  a.threshold = threshold ? 1 : 0;
+  a.kprime = threshold ? std::max<int32_t>(kprime, 0) : 0;
+  a.size_out = (long long*)size_out;
 
-  const int mode = effective_mode(h);
   if (mode == 2 && m >= ((int64_t)1 << 40))
     return fail(h, KCORE_ERR_INVALID, "the bulk-synchronous mode takes at most 2^40 arcs");
   const int mode_max = mode == 2 ? h->bsp_max_ctas_per_sm : h->max_ctas_per_sm;
@@ -351,6 +356,30 @@ kcore_status kcore_decompose(kcore_handle h, int64_t n, int64_t m, const int64_t
   h->last_mode = mode;
   h->last_slice = slice;
   return KCORE_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+kcore_status kcore_decompose(kcore_handle h, int64_t n, int64_t m, const int64_t* offsets,
+                             const int32_t* adj, int32_t* coreness_out, int32_t* kmax_out,
+                             kcore_stream_t stream_) {
+  if (!h) return KCORE_ERR_INVALID;
+  if (n < 0 || m < 0 || n > INT32_MAX - 1) return fail(h, KCORE_ERR_INVALID, "n or m out of range");
+  if (!kmax_out) return fail(h, KCORE_ERR_INVALID, "kmax_out is null");
+  if (n > 0 && (!offsets || !coreness_out)) return fail(h, KCORE_ERR_INVALID, "null offsets/coreness");
+  if (m > 0 && !adj) return fail(h, KCORE_ERR_INVALID, "null adj with m > 0");
+  return peel_call(h, n, m, offsets, adj, coreness_out, kmax_out, (cudaStream_t)stream_, false, 0, nullptr);
+}
+
+kcore_status kcore_core_mask(kcore_handle h, int64_t n, int64_t m, const int64_t* offsets, const int32_t* adj,
+                             int32_t kprime, int32_t* mask_out, int64_t* size_out, kcore_stream_t stream_) {
+  if (!h) return KCORE_ERR_INVALID;
+  if (n < 0 || m < 0 || n > INT32_MAX - 1) return fail(h, KCORE_ERR_INVALID, "n or m out of range");
+  if (n > 0 && (!offsets || !mask_out)) return fail(h, KCORE_ERR_INVALID, "null offsets/mask");
+  if (m > 0 && !adj) return fail(h, KCORE_ERR_INVALID, "null adj with m > 0");
+  return peel_call(h, n, m, offsets, adj, mask_out, nullptr, (cudaStream_t)stream_, true, kprime, size_out);
 }
 
 kcore_status kcore_build_csr_workspace_size(kcore_handle h, int64_t n, int64_t num_edges, size_t* bytes) {

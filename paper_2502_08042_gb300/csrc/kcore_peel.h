@@ -58,7 +58,8 @@ struct PeelCtl {
   char pad6[120];
   long long passes, barriers;
   unsigned long long tr_arcs, tr_decs;  // bulk-synchronous mode, with tracing: running sums
-  char pad7[96];
+  unsigned long long crossed;           // k'-core query: vertices removed by a decrement
+  char pad7[88];
 };
 
 // The bulk-synchronous mode uses round records 0..2 as a ring: phase p uses
@@ -90,6 +91,11 @@ struct PeelArgs {
   int inject_stall;
   unsigned long long* trace;  // optional: kTraceFields words per round (nullptr = off)
   int local_batches;          // bulk-synchronous mode: local batches per chunk taken
+  // k'-core query (bulk-synchronous mode only): one peel at level kprime - 1
+  // taking every vertex below kprime; core[] receives 1 (in the k'-core) or 0
+  int threshold;
+  int kprime;
+  long long* size_out;  // optional: the k'-core's vertex count
 };
 
 // Per-round trace record (KCORE_OPT_TRACE): globaltimer at round start (CTA 0),

@@ -64,6 +64,7 @@ struct Shared {
   int red_min[kWarps];
   int red_cnt[kWarps];
   unsigned long long tr_arcs[kWarps], tr_decs[kWarps];  // trace only
+  unsigned ncross[kWarps];                               // k'-core query: crossings
   int flag;
 };
 
@@ -154,7 +155,11 @@ __device__ __forceinline__ int block_excl_scan(Shared& sh, int x, int* total) {
 // step, so the offsets of only those vertices are read.
 __device__ ScanOut scan_range(const PeelArgs& a, Shared& sh, RoundRec* R, unsigned long long qbase,
                               const int* Ain, int* Aout, long long lo, long long hi, int keep_above,
-                              int take_at) {
+                              int take_at, bool take_le = false, int take_val = -1, int keep_val = -1) {
+  // take_le: take every entry with d~ <= take_at (k'-core query); take_val /
+  // keep_val: the value written to core[] for taken / kept entries (-1: the
+  // level take_at for taken ones, nothing for kept ones)
+  if (take_val < 0) take_val = take_at;
   const int tid = threadIdx.x;
   unsigned long long found = 0;  // staged frontier vertices (block-uniform)
   int direct = 0;                // frontier vertices without arcs (this thread)
@@ -198,10 +203,11 @@ __device__ ScanOut scan_range(const PeelArgs& a, Shared& sh, RoundRec* R, unsign
       if (d > keep_above) {
         keep |= 1u << q;
         dmin = min(dmin, d);
+        if (keep_val >= 0) a.core[x] = keep_val;
       }
-      if (d == take_at) {
+      if (take_le ? d <= take_at : d == take_at) {
         if (!Ain && d == 0) {
-          a.core[x] = 0;  // first scan: no arcs, nothing to expand
+          a.core[x] = take_val;  // first scan: no arcs, nothing to expand
           direct++;
         } else {
           take |= 1u << q;
@@ -236,7 +242,7 @@ __device__ ScanOut scan_range(const PeelArgs& a, Shared& sh, RoundRec* R, unsign
           const int x = sh.stage[i];
           e0[k] = a.off[x];
           e1[k] = a.off[x + 1];
-          a.core[x] = take_at;
+          a.core[x] = take_val;
         }
       }
 #pragma unroll
@@ -284,6 +290,7 @@ struct PassCtx {
   RoundRec* R;              // R->tail counts this phase's appends
   unsigned long long qbase; // appends start here
   int t;
+  int val;                  // written to core[] of a vertex that crosses (t, or 0 in a k'-core query)
 };
 
 // Appends `cnt` items per lane (lane-owned arc ranges [e0, e1) cut in
@@ -389,8 +396,12 @@ __device__ void process_items(const PeelArgs& a, Shared& sh, const PassCtx& pc, 
 #pragma unroll
       for (int q = 0; q < kIlp; q++) {
         const bool f = (cross >> q) & 1u;
-        if (f) a.core[u[q]] = t;
-        if (__any_sync(kFull, f)) push_crossed(a, sh, pc, f, u[q], warp, lane);
+        if (f) a.core[u[q]] = pc.val;
+        const unsigned fb = __ballot_sync(kFull, f);
+        if (fb) {
+          if (lane == 0) sh.ncross[warp] += __popc(fb);
+          push_crossed(a, sh, pc, f, u[q], warp, lane);
+        }
       }
     }
   }
@@ -466,6 +477,7 @@ __global__ void __launch_bounds__(kBlock, 2) peel_bsp(PeelArgs a) {
   if (lane == 0) {
     sh.lqn[warp] = 0;
     sh.tr_arcs[warp] = sh.tr_decs[warp] = 0;
+    sh.ncross[warp] = 0;
   }
   unsigned long long gen = 0;
   long long phase = 0;  // RoundRec (phase % 3) belongs to phase `phase`
@@ -494,15 +506,17 @@ __global__ void __launch_bounds__(kBlock, 2) peel_bsp(PeelArgs a) {
   unsigned local_batches = 0;
   unsigned long long qend = 0;  // items appended by all completed phases
   for (;;) {
-    // ---- scan: keep d~ > tp+1, take d~ == tp+1
-    const int tk = tp + 1;
+    // ---- scan: keep d~ > tp+1, take d~ == tp+1 (a k'-core query: one level,
+    // kprime - 1, taking every d~ below kprime and marking the rest 1)
+    const int tk = a.threshold ? a.kprime - 1 : tp + 1;
     const uint64_t t_start = lead && a.trace ? globaltimer_ns() : 0;
     reset_next();
     RoundRec* R = a.rounds + (phase % kPhaseRing);
     long long nscan = nscan_of(la);
     if (blockIdx.x < nscan) {
       const long long lo = la * blockIdx.x / nscan, hi = la * (blockIdx.x + 1) / nscan;
-      const ScanOut o = scan_range(a, sh, R, qend, Acur, Afree, lo, hi, tk, tk);
+      const ScanOut o = a.threshold ? scan_range(a, sh, R, qend, Acur, Afree, lo, hi, tk, tk, true, 0, 1)
+                                    : scan_range(a, sh, R, qend, Acur, Afree, lo, hi, tk, tk);
       if (tid == 0) {
         if (o.found) atomicAdd(&R->found, o.found);
         if (o.dmin != INT_MAX) atomicMax(&R->minkey, INT_MAX - o.dmin);
@@ -525,7 +539,7 @@ __global__ void __launch_bounds__(kBlock, 2) peel_bsp(PeelArgs a) {
     la = alen;
     int t = tk;
     unsigned long long nfound = found;
-    if (!found) {
+    if (!found && !a.threshold) {
       if (alen == 0) break;  // nothing left
       // level tk is empty: the least induced degree of the kept vertices is the next level
       empty++;
@@ -558,8 +572,12 @@ __global__ void __launch_bounds__(kBlock, 2) peel_bsp(PeelArgs a) {
       while (qend > qb) {
         reset_next();
         RoundRec* P = a.rounds + (phase % kPhaseRing);
-        const PassCtx pc{P, qend, t};
+        const PassCtx pc{P, qend, t, a.threshold ? 0 : t};
         run_pass(a, sh, pc, qb, qend, items, local_items, local_batches);
+        if (a.threshold && lane == 0 && sh.ncross[warp]) {
+          atomicAdd(&a.ctl->crossed, (unsigned long long)sh.ncross[warp]);
+          sh.ncross[warp] = 0;
+        }
         if (a.trace && lane == 0) {
           atomicAdd(&a.ctl->tr_arcs, sh.tr_arcs[warp]);
           atomicAdd(&a.ctl->tr_decs, sh.tr_decs[warp]);
@@ -589,6 +607,11 @@ __global__ void __launch_bounds__(kBlock, 2) peel_bsp(PeelArgs a) {
       tr[9] = ld_relaxed_u64(&a.ctl->tr_decs) - decs0;
       tr[13] = (unsigned long long)level_passes;
     }
+    if (a.threshold) {
+      // the k'-core: the vertices kept by the scan that no decrement removed
+      if (ok && lead && a.size_out) *a.size_out = la - (long long)ld_relaxed_u64(&a.ctl->crossed);
+      break;
+    }
     if (!ok || la == 0) break;
   }
   if (lane == 0) {
@@ -596,7 +619,7 @@ __global__ void __launch_bounds__(kBlock, 2) peel_bsp(PeelArgs a) {
     if (local_items) atomicAdd(&a.ctl->local_items, (unsigned long long)local_items);
   }
   if (lead) {
-    *a.kmax_out = kmax;
+    if (a.kmax_out) *a.kmax_out = kmax;
     a.ctl->rounds = levels + empty;
     a.ctl->empty_rounds = empty;
     a.ctl->scanned = scanned;

@@ -150,6 +150,24 @@ class KCore:
             self.sync()
         return coreness, kmax
 
+    def core_mask(self, offsets, adj, kprime: int, mask=None, size=None, stream=None, sync: bool = True):
+        """Membership of every vertex in the k'-core (int32 1/0 CUDA tensor
+        [n]) and the k'-core's vertex count (int64 CUDA tensor [1])."""
+        torch = _torch()
+        n = offsets.numel() - 1
+        m = adj.numel()
+        assert offsets.dtype == torch.int64 and adj.dtype == torch.int32
+        assert offsets.is_cuda and adj.is_cuda and offsets.is_contiguous() and adj.is_contiguous()
+        if mask is None:
+            mask = torch.empty(max(n, 0), dtype=torch.int32, device=offsets.device)
+        if size is None:
+            size = torch.empty(1, dtype=torch.int64, device=offsets.device)
+        self._check(self._L.kcore_core_mask(self._h, n, m, _ptr(offsets), _ptr(adj), int(kprime), _ptr(mask),
+                                            _ptr(size), _stream_ptr(stream)))
+        if sync:
+            self.sync()
+        return mask, size
+
     def decompose_batched(self, graph_vertex_offsets, offsets, adj, coreness=None, kmax=None,
                           stream=None, sync: bool = True):
         """Coreness of every graph of a segmented CSR on the GPU (graph-local
