@@ -63,7 +63,8 @@ typedef enum {
   KCORE_OPT_CTAS_PER_SM = 1,   /* CTAs per SM of the persistent kernel (0 = occupancy maximum) */
   KCORE_OPT_SLICE_ARCS = 2,    /* arcs per work item (16 .. 2^20; 0 = auto: 64 in mode 2, 512 in
                                   mode 1): longer lists are split in slices */
-  KCORE_OPT_LOCAL_QUEUE = 3,   /* per-warp local queue capacity (vertices), 0 disables it */
+  KCORE_OPT_LOCAL_QUEUE = 3,   /* per-warp local queue capacity (work items, 0 .. 128; 0 disables
+                                  it; -1 = auto: 128 in mode 2, 32 in mode 1) */
   KCORE_OPT_TIMEOUT_MS = 4,    /* limit for every device-side wait, milliseconds */
   KCORE_OPT_MIN_CTAS = 5,      /* lower bound of the grid for small graphs */
   KCORE_OPT_VERTICES_PER_CTA = 6, /* grid sizing: about one CTA per this many vertices+arcs/8 */
@@ -80,7 +81,7 @@ typedef enum {
                                          fit with the CTAs per SM below) */
   KCORE_OPT_BATCH_CTAS_PER_SM = 13,   /* batched peel: resident CTAs per SM (0 = occupancy limit) */
   KCORE_OPT_LOCAL_BATCHES = 14        /* mode 2: local-queue batches a warp may run after each chunk it
-                                         takes (0 .. 2^20, 0 = no limit); the rest of its local queue
+                                         takes (0 .. 2^20, 0 = no limit; default 32); the rest of its local queue
                                          then goes to the work queue, so a large cascade is shared by
                                          all warps in the next subround instead of one warp */
 } kcore_option;

@@ -22,7 +22,7 @@ struct kcore_ctx {
   size_t ws_bytes = 0;
   bool ws_external = false;
   std::string err;
-  int64_t opt[15] = {0, 0, 0, 32, 2000, 1, 2048, 0, 0, 192, 64, 1024, -1, 0, 8};  // indexed by kcore_option
+  int64_t opt[15] = {0, 0, 0, -1, 2000, 1, 2048, 0, 0, 192, 64, 1024, -1, 0, 32};  // indexed by kcore_option
   cudaStream_t last_stream = nullptr;
   bool pending = false;
   kc::PeelCtl* last_ctl = nullptr;
@@ -224,8 +224,8 @@ kcore_status kcore_set_option(kcore_handle h, kcore_option opt, int64_t value) {
         return fail(h, KCORE_ERR_INVALID, "slice must be 0 (auto) or in [16, 2^20]");
       break;
     case KCORE_OPT_LOCAL_QUEUE:
-      if (value < 0 || value > kc::kLocalQueueMax)
-        return fail(h, KCORE_ERR_INVALID, "local queue must be in [0, 128]");
+      if (value < -1 || value > kc::kLocalQueueMax)
+        return fail(h, KCORE_ERR_INVALID, "local queue must be -1 (auto) or in [0, 128]");
       break;
     case KCORE_OPT_TIMEOUT_MS:
       if (value < 1 || value > 600000) return fail(h, KCORE_ERR_INVALID, "timeout must be in [1, 600000] ms");
@@ -314,7 +314,7 @@ kcore_status peel_call(kcore_ctx* h, int64_t n, int64_t m, const int64_t* offset
   a.max_rounds = L.max_rounds;
   a.ctl = (kc::PeelCtl*)(ws + L.ctl);
   a.slice = slice;
-  a.lq_cap = (int)h->opt[KCORE_OPT_LOCAL_QUEUE];
+  a.lq_cap = h->opt[KCORE_OPT_LOCAL_QUEUE] >= 0 ? (int)h->opt[KCORE_OPT_LOCAL_QUEUE] : (mode == 2 ? 128 : 32);
   a.max_take = 256;
   a.timeout_ns = (unsigned long long)h->opt[KCORE_OPT_TIMEOUT_MS] * 1000000ull;
   a.scan_min = 2048;

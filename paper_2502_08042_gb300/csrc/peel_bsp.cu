@@ -397,11 +397,11 @@ __device__ void process_items(const PeelArgs& a, Shared& sh, const PassCtx& pc, 
       for (int q = 0; q < kIlp; q++) {
         const bool f = (cross >> q) & 1u;
         if (f) a.core[u[q]] = pc.val;
-        const unsigned fb = __ballot_sync(kFull, f);
-        if (fb) {
-          if (lane == 0) sh.ncross[warp] += __popc(fb);
-          push_crossed(a, sh, pc, f, u[q], warp, lane);
-        }
+        if (__any_sync(kFull, f)) push_crossed(a, sh, pc, f, u[q], warp, lane);
+      }
+      if (a.threshold) {
+        const int nc = warp_sum(__popc(cross));
+        if (lane == 0) sh.ncross[warp] += nc;
       }
     }
   }
