@@ -46,6 +46,7 @@ constexpr int kTile = 8;   // active-list entries per thread per scan tile
 constexpr int kExpand = 4; // staged frontier vertices per thread per expansion round
 constexpr int kIlp = 8;    // arcs per lane in flight
 constexpr int kTake = 32;  // queue items per chunk of a warp's share
+constexpr int kPrecheckShare = 64;  // per-warp share from which a pass reads d~ before decrementing
 constexpr int kLenShift = 40;  // item = first arc | length << 40
 constexpr unsigned long long kArcMask = (1ull << kLenShift) - 1;
 constexpr unsigned long long kAbort = 1ull << 62;  // barrier word: a status was raised
@@ -291,6 +292,7 @@ struct PassCtx {
   unsigned long long qbase; // appends start here
   int t;
   int val;                  // written to core[] of a vertex that crosses (t, or 0 in a k'-core query)
+  bool precheck;            // long pass: read d~ before decrementing (see process_items)
 };
 
 // Appends `cnt` items per lane (lane-owned arc ranges [e0, e1) cut in
@@ -372,13 +374,15 @@ __device__ void process_items(const PeelArgs& a, Shared& sh, const PassCtx& pc, 
         else raise_status(a, ST_NOT_SIMPLE);
       }
     }
-    // In a batch of many arcs, reading d~ first spares the atomics on
-    // neighbours at or below the level. A batch of one iteration is bound by
-    // its chain of dependent accesses instead: it decrements unconditionally.
-    // That is safe, as a neighbour at or below k never returns k + 1 and its
-    // d~ is not read again.
+    // Reading d~ first spares the atomics on neighbours at or below the
+    // level, at the price of one more dependent access per iteration. It pays
+    // in a long pass, where warps have enough work to hide latency and
+    // atomic throughput counts (pc.precheck), and only for batches of more
+    // than one iteration; otherwise the warp decrements unconditionally. That
+    // is safe, as a neighbour at or below k never returns k + 1 and its d~ is
+    // not read again.
     int dq[kIlp];
-    if (total > kWarp * kIlp) {
+    if (pc.precheck && total > kWarp * kIlp) {
 #pragma unroll
       for (int q = 0; q < kIlp; q++) dq[q] = u[q] >= 0 ? __ldcg(a.deg + u[q]) : INT_MIN;
     } else {
@@ -572,7 +576,11 @@ __global__ void __launch_bounds__(kBlock, 2) peel_bsp(PeelArgs a) {
       while (qend > qb) {
         reset_next();
         RoundRec* P = a.rounds + (phase % kPhaseRing);
-        const PassCtx pc{P, qend, t, a.threshold ? 0 : t};
+        // a pass whose per-warp share is at least kPrecheckShare items is
+        // throughput-bound (measured: kNN's largest level 1,700 items per
+        // warp; R-MAT passes a few)
+        const bool pre = (qend - qb) >= (unsigned long long)kPrecheckShare * gridDim.x * kWarps;
+        const PassCtx pc{P, qend, t, a.threshold ? 0 : t, pre};
         run_pass(a, sh, pc, qb, qend, items, local_items, local_batches);
         if (a.threshold && lane == 0 && sh.ncross[warp]) {
           atomicAdd(&a.ctl->crossed, (unsigned long long)sh.ncross[warp]);
