@@ -310,7 +310,7 @@ def run_gpu(args):
     w = WORKLOADS[args.workload]
     n, s, d = make_edges(w)
     E = len(s)
-    k = KCore(local)
+    k = KCore(local, sync_mode=args.sync_mode)
     S = torch.from_numpy(s).to(dev)
     D = torch.from_numpy(d).to(dev)
     del s, d
@@ -732,6 +732,8 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
     ap.add_argument("--workload", default="rmat24", choices=sorted(WORKLOADS))
+    ap.add_argument("--sync-mode", type=int, default=0, choices=[0, 1, 2, 3],
+                    help="single-graph schedule (0: the library's default)")
     ap.add_argument("--graphs", type=int, default=0,
                     help="batched workload: first G graphs of the distribution (default 4096; "
                          "smaller batches are for profiling)")

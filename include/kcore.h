@@ -59,7 +59,11 @@ typedef enum {
   KCORE_OPT_SYNC_MODE = 0,     /* single-graph peel schedule: 0 auto (= 2); 1 asynchronous
                                   persistent kernel (rounds end on device-wide counters, work
                                   overlaps across subrounds); 2 bulk-synchronous persistent kernel
-                                  (a bounded grid barrier after the scan and after every subround) */
+                                  (a bounded grid barrier after the scan and after every subround);
+                                  3 the offline peel of Algorithm 2 on the same kernel: each subround
+                                  counts the frontier's decrements per neighbour (histogram), then
+                                  applies them in one step per vertex, so every crossing is decided
+                                  by one owner; no local queues (its subrounds are Algorithm 1's) */
   KCORE_OPT_CTAS_PER_SM = 1,   /* CTAs per SM of the persistent kernel (0 = occupancy maximum) */
   KCORE_OPT_SLICE_ARCS = 2,    /* arcs per work item (16 .. 2^20; 0 = auto: 64 in mode 2, 512 in
                                   mode 1): longer lists are split in slices */
@@ -95,8 +99,8 @@ typedef struct {
   int64_t scanned;         /* sum over rounds of the active-set size scanned (Theorem 1) */
   int64_t kmax;            /* largest coreness */
   int64_t grid;            /* CTAs of the persistent kernel */
-  int64_t sync_mode;       /* mode actually used: 1 asynchronous, 2 bulk-synchronous */
-  int64_t passes;          /* bulk-synchronous mode: subround passes over the work queue */
+  int64_t sync_mode;       /* mode actually used: 1 asynchronous, 2 bulk-synchronous, 3 offline */
+  int64_t passes;          /* modes 2 and 3: subround passes over the work queue */
   int64_t barriers;        /* bulk-synchronous mode: grid barriers taken */
   int64_t batch_block;     /* batched calls: threads per CTA used */
   int64_t batch_smem_vertices; /* batched calls: largest graph kept in shared memory */

@@ -74,7 +74,7 @@ long long isqrt_ll(long long m) {
 }
 
 struct PeelLayout {
-  size_t deg, a0, a1, q, rounds, ctl, trace, total;
+  size_t deg, a0, a1, q, rounds, ctl, trace, hcnt, touched, total;
   long long qcap;
   int max_rounds;
 };
@@ -84,7 +84,7 @@ struct PeelLayout {
 // per-round records (levels <= k_max+1 <= sqrt(m)+1, each followed by at most
 // one empty speculative level) and the control block. Everything below `deg`
 // is zeroed per call.
-PeelLayout peel_layout(long long n, long long m, int slice) {
+PeelLayout peel_layout(long long n, long long m, int slice, bool offline = false) {
   PeelLayout L{};
   L.qcap = n + (m + slice - 1) / slice + 1;
   long long mr = 2 * isqrt_ll(m) + 8;
@@ -105,15 +105,26 @@ PeelLayout peel_layout(long long n, long long m, int slice) {
   off = align_up(off + 8 * (size_t)L.qcap, 256);
   L.trace = off;
   off = align_up(off + 8 * (size_t)kc::kTraceFields * (size_t)L.max_rounds, 256);
+  // offline subrounds (mode 3): decrement counts and the touched list
+  L.hcnt = L.touched = off;
+  if (offline) {
+    L.hcnt = off;
+    off = align_up(off + 4 * (size_t)n, 256);
+    L.touched = off;
+    off = align_up(off + 4 * (size_t)n, 256);
+  }
   L.total = off;
   return L;
 }
 
 // Schedule and slice length a call on this handle uses (option value 0 = auto).
-int effective_mode(const kcore_ctx* h) { return h->opt[KCORE_OPT_SYNC_MODE] == 1 ? 1 : 2; }
+int effective_mode(const kcore_ctx* h) {
+  const int64_t m = h->opt[KCORE_OPT_SYNC_MODE];
+  return m == 1 ? 1 : (m == 3 ? 3 : 2);
+}
 int effective_slice(const kcore_ctx* h) {
   if (h->opt[KCORE_OPT_SLICE_ARCS] > 0) return (int)h->opt[KCORE_OPT_SLICE_ARCS];
-  return effective_mode(h) == 2 ? 64 : 512;
+  return effective_mode(h) == 1 ? 512 : 64;
 }
 
 kcore_status ensure_ws(kcore_ctx* h, size_t need) {
@@ -213,7 +224,7 @@ kcore_status kcore_set_option(kcore_handle h, kcore_option opt, int64_t value) {
       if (value < 0 || value > 1) return fail(h, KCORE_ERR_INVALID, "test stall must be 0 or 1");
       break;
     case KCORE_OPT_SYNC_MODE:
-      if (value < 0 || value > 2) return fail(h, KCORE_ERR_INVALID, "sync mode must be 0, 1 or 2");
+      if (value < 0 || value > 3) return fail(h, KCORE_ERR_INVALID, "sync mode must be 0, 1, 2 or 3");
       break;
     case KCORE_OPT_CTAS_PER_SM:
       if (value < 0 || value > h->max_ctas_per_sm)
@@ -249,7 +260,7 @@ kcore_status kcore_get_option(kcore_handle h, kcore_option opt, int64_t* value) 
 
 kcore_status kcore_workspace_size(kcore_handle h, int64_t n, int64_t m, size_t* bytes) {
   if (!h || !bytes || n < 0 || m < 0 || n > INT32_MAX - 1) return KCORE_ERR_INVALID;
-  *bytes = peel_layout(n, m, effective_slice(h)).total;
+  *bytes = peel_layout(n, m, effective_slice(h), effective_mode(h) == 3).total;
   return KCORE_OK;
 }
 
@@ -293,8 +304,8 @@ kcore_status peel_call(kcore_ctx* h, int64_t n, int64_t m, const int64_t* offset
     return KCORE_OK;
   }
   const int mode = threshold ? 2 : effective_mode(h);
-  const int slice = h->opt[KCORE_OPT_SLICE_ARCS] > 0 ? (int)h->opt[KCORE_OPT_SLICE_ARCS] : (mode == 2 ? 64 : 512);
-  PeelLayout L = peel_layout(n, m, slice);
+  const int slice = h->opt[KCORE_OPT_SLICE_ARCS] > 0 ? (int)h->opt[KCORE_OPT_SLICE_ARCS] : (mode == 1 ? 512 : 64);
+  PeelLayout L = peel_layout(n, m, slice, mode == 3);
   kcore_status st = ensure_ws(h, L.total);
   if (st != KCORE_OK) return st;
   char* ws = (char*)h->ws;
@@ -314,7 +325,7 @@ kcore_status peel_call(kcore_ctx* h, int64_t n, int64_t m, const int64_t* offset
   a.max_rounds = L.max_rounds;
   a.ctl = (kc::PeelCtl*)(ws + L.ctl);
   a.slice = slice;
-  a.lq_cap = h->opt[KCORE_OPT_LOCAL_QUEUE] >= 0 ? (int)h->opt[KCORE_OPT_LOCAL_QUEUE] : (mode == 2 ? 128 : 32);
+  a.lq_cap = h->opt[KCORE_OPT_LOCAL_QUEUE] >= 0 ? (int)h->opt[KCORE_OPT_LOCAL_QUEUE] : (mode == 1 ? 32 : 128);
   a.max_take = 256;
   a.timeout_ns = (unsigned long long)h->opt[KCORE_OPT_TIMEOUT_MS] * 1000000ull;
   a.scan_min = 2048;
@@ -324,12 +335,15 @@ kcore_status peel_call(kcore_ctx* h, int64_t n, int64_t m, const int64_t* offset
   a.trace = h->opt[KCORE_OPT_TRACE] ? (unsigned long long*)(ws + L.trace) : nullptr;
   a.local_batches = h->opt[KCORE_OPT_LOCAL_BATCHES] > 0 ? (int)h->opt[KCORE_OPT_LOCAL_BATCHES] : INT32_MAX;
   a.threshold = threshold ? 1 : 0;
+  a.offline = mode == 3 ? 1 : 0;
+  a.hcnt = (int*)(ws + L.hcnt);
+  a.touched = (int*)(ws + L.touched);
   a.kprime = threshold ? std::max<int32_t>(kprime, 0) : 0;
   a.size_out = (long long*)size_out;
 
-  if (mode == 2 && m >= ((int64_t)1 << 40))
-    return fail(h, KCORE_ERR_INVALID, "the bulk-synchronous mode takes at most 2^40 arcs");
-  const int mode_max = mode == 2 ? h->bsp_max_ctas_per_sm : h->max_ctas_per_sm;
+  if (mode != 1 && m >= ((int64_t)1 << 40))
+    return fail(h, KCORE_ERR_INVALID, "the bulk-synchronous modes take at most 2^40 arcs");
+  const int mode_max = mode != 1 ? h->bsp_max_ctas_per_sm : h->max_ctas_per_sm;
   int per_sm = h->opt[KCORE_OPT_CTAS_PER_SM] > 0 ? (int)h->opt[KCORE_OPT_CTAS_PER_SM] : mode_max;
   per_sm = std::min(per_sm, mode_max);
   long long gmax = (long long)h->sms * per_sm;
@@ -345,9 +359,12 @@ kcore_status peel_call(kcore_ctx* h, int64_t n, int64_t m, const int64_t* offset
   // bulk-synchronous mode reads only slots written before its barrier
   if (mode == 1 && (e = cudaMemsetAsync(ws + L.q, 0xff, 8 * (size_t)L.qcap, stream)) != cudaSuccess)
     return cuda_fail(h, e, "memset queue");
-  if (a.trace && (e = cudaMemsetAsync(a.trace, 0, L.total - L.trace, stream)) != cudaSuccess)
+  if (a.trace && (e = cudaMemsetAsync(a.trace, 0, 8 * (size_t)kc::kTraceFields * (size_t)L.max_rounds,
+                                      stream)) != cudaSuccess)
     return cuda_fail(h, e, "memset trace");
-  e = mode == 2 ? kc::bsp_launch(a, (int)grid, stream) : kc::peel_launch(a, (int)grid, stream);
+  if (mode == 3 && (e = cudaMemsetAsync(a.hcnt, 0, 4 * (size_t)n, stream)) != cudaSuccess)
+    return cuda_fail(h, e, "memset counts");
+  e = mode != 1 ? kc::bsp_launch(a, (int)grid, stream) : kc::peel_launch(a, (int)grid, stream);
   if (e != cudaSuccess) return cuda_fail(h, e, "peel launch");
   h->last_ctl = a.ctl;
   h->last_trace = a.trace;
@@ -640,8 +657,8 @@ kcore_status kcore_get_trace(kcore_handle h, uint64_t* out, int64_t max_rounds, 
   *rounds_out = 0;
   if (!h->last_trace) return fail(h, KCORE_ERR_INVALID, "the last decomposition ran without tracing");
   DeviceGuard g(h->device);
-  // the bulk-synchronous mode records one entry per non-empty level
-  const int64_t have = h->last_mode == 2 ? h->stats.rounds - h->stats.empty_rounds : h->stats.rounds;
+  // the bulk-synchronous modes record one entry per non-empty level
+  const int64_t have = h->last_mode != 1 ? h->stats.rounds - h->stats.empty_rounds : h->stats.rounds;
   int64_t r = std::min<int64_t>(std::min<int64_t>(max_rounds, have), h->last_max_rounds);
   if (r > 0) {
     cudaError_t e = cudaMemcpy(out, h->last_trace, sizeof(uint64_t) * kc::kTraceFields * (size_t)r,

@@ -96,6 +96,11 @@ struct PeelArgs {
   int threshold;
   int kprime;
   long long* size_out;  // optional: the k'-core's vertex count
+  // offline subrounds (sync mode 3, Algorithm 2): per-vertex decrement
+  // counts (zero at launch, left zero) and the touched list of a subround
+  int offline;
+  int* hcnt;
+  int* touched;
 };
 
 // Per-round trace record (KCORE_OPT_TRACE): globaltimer at round start (CTA 0),

@@ -474,6 +474,121 @@ __device__ void run_pass(const PeelArgs& a, Shared& sh, const PassCtx& pc, unsig
   }
 }
 
+// ---- offline subrounds (sync mode 3): Algorithm 2 -------------------------
+// A subround is two phases. The histogram phase walks the arcs of the
+// frontier items (edge-balanced over each warp, as process_items) and counts,
+// per neighbour still above the level, how many frontier arcs reach it; the
+// first count of a neighbour appends it to the touched list. The apply phase
+// gives each touched vertex to one thread, which subtracts its count from d~
+// in one step and, when d~ dropped from above k to k or below, gives it
+// coreness k and appends its slices as the next frontier. No decision depends
+// on the order of concurrent updates.
+__device__ void hist_items(const PeelArgs& a, Shared& sh, const PassCtx& pc, unsigned long long item, int c,
+                           int warp, int lane) {
+  const int t = pc.t;
+  const long long a0 = lane < c ? (long long)(item & kArcMask) : 0;
+  const int len = lane < c ? (int)(item >> kLenShift) : 0;
+  const int incl = warp_incl_scan(len, lane);
+  const int total = __shfl_sync(kFull, incl, 31);
+  sh.excl[warp][lane] = incl - len;
+  sh.a0[warp][lane] = a0;
+  __syncwarp();
+  const int* excl = sh.excl[warp];
+  for (int base = 0; base < total; base += kWarp * kIlp) {
+    int u[kIlp];
+    int j = base + lane;
+    int lo = 0, hi = c;
+    while (lo < hi) {
+      const int mid = (lo + hi) >> 1;
+      if (excl[mid] <= j) lo = mid + 1;
+      else hi = mid;
+    }
+    int idx = lo > 0 ? lo - 1 : 0;
+#pragma unroll
+    for (int q = 0; q < kIlp; q++, j += kWarp) {
+      u[q] = -1;
+      if (j < total) {
+        while (idx + 1 < c && excl[idx + 1] <= j) idx++;
+        const long long arc = sh.a0[warp][idx] + (j - excl[idx]);
+        const int x = arc < a.m ? ld_stream_s32(a.adj + arc) : -1;
+        if ((unsigned)x < (unsigned)a.n) u[q] = x;
+        else raise_status(a, ST_NOT_SIMPLE);
+      }
+    }
+    int dq[kIlp];
+#pragma unroll
+    for (int q = 0; q < kIlp; q++) dq[q] = u[q] >= 0 ? __ldcg(a.deg + u[q]) : INT_MIN;
+#pragma unroll
+    for (int q = 0; q < kIlp; q++) {
+      // d~ does not change during this phase: only neighbours above k count
+      const bool first = dq[q] > t && atomicAdd(a.hcnt + u[q], 1) == 0;
+      const unsigned fm = __ballot_sync(kFull, first);
+      if (fm) {
+        unsigned long long base = 0;
+        if (lane == 0) base = atomicAdd(&pc.R->head, (unsigned long long)__popc(fm));
+        base = __shfl_sync(kFull, base, 0);
+        const unsigned long long p = base + __popc(fm & lanemask_lt());
+        if (first) {
+          if (p < (unsigned long long)a.n) a.touched[p] = u[q];
+          else raise_status(a, ST_CAPACITY);
+        }
+      }
+    }
+  }
+  __syncwarp();
+}
+
+__device__ void run_hist(const PeelArgs& a, Shared& sh, const PassCtx& pc, unsigned long long qb,
+                         unsigned long long qe, long long& items) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const unsigned long long gw = (unsigned long long)blockIdx.x * kWarps + warp;
+  const unsigned long long nw = (unsigned long long)gridDim.x * kWarps;
+  const unsigned long long len = qe - qb, share = len / nw, rem = len % nw;
+  const unsigned long long b = qb + gw * share + (gw < rem ? gw : rem);
+  const unsigned long long e = b + share + (gw < rem ? 1 : 0);
+  for (unsigned long long pos = b; pos < e; pos += kTake) {
+    const int c = (int)min((unsigned long long)kTake, e - pos);
+    const unsigned long long item = lane < c ? __ldcg(a.Q + pos + lane) : 0;
+    hist_items(a, sh, pc, item, c, warp, lane);
+    items += c;
+  }
+}
+
+// Apply phase over touched[0, nt): a warp handles 32 touched vertices at a time.
+__device__ void run_apply(const PeelArgs& a, const PassCtx& pc, unsigned long long nt) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const unsigned long long gw = (unsigned long long)blockIdx.x * kWarps + warp;
+  const unsigned long long nw = (unsigned long long)gridDim.x * kWarps;
+  const int t = pc.t;
+  for (unsigned long long base = gw * kWarp; base < nt; base += nw * kWarp) {
+    const unsigned long long i = base + lane;
+    int u = -1;
+    bool cross = false;
+    long long e0 = 0, e1 = 0;
+    int nsl = 0;
+    if (i < nt) {
+      u = __ldcg(a.touched + i);
+      if ((unsigned)u < (unsigned)a.n) {
+        const int f = __ldcg(a.hcnt + u);
+        a.hcnt[u] = 0;
+        const int old = __ldcg(a.deg + u);
+        a.deg[u] = old - f;
+        cross = old > t && old - f <= t;
+        if (cross) {
+          a.core[u] = pc.val;
+          e0 = a.off[u];
+          e1 = a.off[u + 1];
+          nsl = (int)((e1 - e0 + a.slice - 1) / a.slice);
+        }
+      } else {
+        raise_status(a, ST_CAPACITY);
+      }
+    }
+    append_ranges(a, pc, cross ? nsl : 0, e0, e1, lane);
+  }
+}
+
+template <bool kOffline>
 __global__ void __launch_bounds__(kBlock, 2) peel_bsp(PeelArgs a) {
   __shared__ Shared sh;
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
@@ -495,6 +610,7 @@ __global__ void __launch_bounds__(kBlock, 2) peel_bsp(PeelArgs a) {
         R->found = 0;
         R->minkey = 0;
         R->tail = 0;
+        R->head = 0;
       }
     }
   };
@@ -572,7 +688,35 @@ __global__ void __launch_bounds__(kBlock, 2) peel_bsp(PeelArgs a) {
     long long level_passes = 0;
     bool ok = true;
     // ---- subround passes; with no vertex left above the level nothing can be decremented
-    if (la > 0) {
+    if (kOffline) {
+      // Algorithm 1's subrounds exactly: also the last level (nothing left
+      // above it) and a frontier without arcs count as one subround each
+      while (qend > qb) {
+        // histogram phase: counts and the touched list (count in P->head)
+        reset_next();
+        RoundRec* P = a.rounds + (phase % kPhaseRing);
+        const PassCtx hc{P, qend, t, t, false};
+        run_hist(a, sh, hc, qb, qend, items);
+        if (!(ok = grid_barrier(a, sh, gen))) break;
+        phase++;
+        const unsigned long long nt = ld_relaxed_u64(&P->head);
+        // apply phase: crossings append the next frontier (count in P2->tail)
+        reset_next();
+        RoundRec* P2 = a.rounds + (phase % kPhaseRing);
+        const PassCtx pc{P2, qend, t, t, false};
+        run_apply(a, pc, nt);
+        if (!(ok = grid_barrier(a, sh, gen))) break;
+        phase++;
+        passes++;
+        level_passes++;
+        qb = qend;
+        qend += ld_relaxed_u64(&P2->tail);
+      }
+      if (ok && level_passes == 0 && nfound > 0) {
+        passes++;
+        level_passes++;
+      }
+    } else if (la > 0) {
       while (qend > qb) {
         reset_next();
         RoundRec* P = a.rounds + (phase % kPhaseRing);
@@ -640,9 +784,10 @@ __global__ void __launch_bounds__(kBlock, 2) peel_bsp(PeelArgs a) {
 }  // namespace
 
 int bsp_max_ctas_per_sm() {
-  int nb = 0;
-  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, peel_bsp, kBlock, 0) != cudaSuccess) return 0;
-  return nb;
+  int nb = 0, nb2 = 0;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, peel_bsp<false>, kBlock, 0) != cudaSuccess) return 0;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb2, peel_bsp<true>, kBlock, 0) != cudaSuccess) return 0;
+  return nb < nb2 ? nb : nb2;
 }
 
 int bsp_block_size() { return kBlock; }
@@ -650,7 +795,8 @@ int bsp_block_size() { return kBlock; }
 cudaError_t bsp_launch(const PeelArgs& args, int grid, cudaStream_t stream) {
   PeelArgs a = args;
   void* params[] = {&a};
-  return cudaLaunchCooperativeKernel((const void*)peel_bsp, dim3(grid), dim3(kBlock), params, 0, stream);
+  const void* fn = a.offline ? (const void*)peel_bsp<true> : (const void*)peel_bsp<false>;
+  return cudaLaunchCooperativeKernel(fn, dim3(grid), dim3(kBlock), params, 0, stream);
 }
 
 }  // namespace kc

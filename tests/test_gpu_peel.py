@@ -1,7 +1,8 @@
 """Parity of the GPU peel (through the C ABI) with the CPU oracle: bit-exact
 coreness on closed forms, hand-derived fixtures, random graphs over many seeds,
-the ER n=10,000 workload, adversarial shapes and every tuning mode, in both
-schedules (1: asynchronous, 2: bulk-synchronous with grid barriers)."""
+the ER n=10,000 workload, adversarial shapes and every tuning mode, in all
+schedules (1: asynchronous, 2: bulk-synchronous with grid barriers, 3: the
+offline peel of Algorithm 2 on the same kernel)."""
 import numpy as np
 import pytest
 
@@ -16,10 +17,10 @@ from paper_2502_08042_gb300 import KCore, KCoreError  # noqa: E402
 from tests.gpu_util import assert_parity, gpu_core, to_dev  # noqa: E402
 
 
-MODES = [1, 2]
+MODES = [1, 2, 3]
 
 
-@pytest.fixture(scope="module", params=MODES, ids=["async", "bsp"])
+@pytest.fixture(scope="module", params=MODES, ids=["async", "bsp", "offline"])
 def kc(request):
     with KCore(0, sync_mode=request.param) as k:
         yield k
@@ -139,7 +140,7 @@ def test_each_vertex_processed_once(kc):
     st = kc.stats()
     deg = np.diff(off)
     sl = st["slice_arcs"]
-    assert sl == (64 if st["sync_mode"] == 2 else 512)
+    assert sl == (512 if st["sync_mode"] == 1 else 64)
     slices = int(np.sum((deg + sl - 1) // sl))
     # each vertex with arcs is taken once as a whole item (from the global or a
     # warp-local queue) and its list is split into ceil(deg / slice) slices
@@ -250,3 +251,23 @@ def test_isolated_only_and_single_level(mode):
                         gg.complete(300)]:
             off, adj = _csr(n, s, d)
             assert_parity(k, n, off, adj)
+
+
+@pytest.mark.parametrize("seed", range(6))
+def test_offline_subrounds_are_algorithm_1s(seed):
+    """Mode 3 applies each subround's decrements in one batch (Algorithm 2),
+    so its subrounds are exactly those of Algorithm 1 with the sequential Peel
+    (the oracle counts them), and its non-empty levels are the oracle's."""
+    n = 4000 + 3000 * seed
+    s, d = gg.rmat_n(n, 10 * n, seed=40 + seed)
+    n2, s2, d2 = gg.disjoint_union((n, s, d), gg.staircase(60), gg.complete(30), gg.path(500),
+                                   (20, np.zeros(0, np.int32), np.zeros(0, np.int32)))
+    off, adj = _csr(n2, s2, d2)
+    core, st = oracle.alg1(n2, off, adj)
+    with KCore(0, sync_mode=3) as k:
+        got = assert_parity(k, n2, off, adj, core)
+        gs = k.stats()
+    assert gs["sync_mode"] == 3
+    assert gs["passes"] == st["subrounds"]
+    assert gs["rounds"] - gs["empty_rounds"] == st["nonempty_rounds"]
+    assert gs["local_items"] == 0
