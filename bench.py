@@ -392,7 +392,10 @@ def run_gpu(args):
     achieved = bmin / (ms_per_step / 1e3) / 1e9
     kname, ksrc = PEEL_KERNELS[st["sync_mode"]]
     traffic = None
+    # recorded traffic belongs to the default schedule of its kernel
     tp = os.path.join(ROOT, "profiles", f"{kname}_{args.workload}_traffic.json")
+    if st["sync_mode"] == 3:
+        tp = ""
     if os.path.exists(tp):
         with open(tp) as f:
             tj = json.load(f)
@@ -714,7 +717,7 @@ def run_served(args):
 
 
 # single-graph schedule (stats "sync_mode") -> (kernel name, its source file)
-PEEL_KERNELS = {1: ("peel_persistent", "peel.cu"), 2: ("peel_bsp", "peel_bsp.cu")}
+PEEL_KERNELS = {1: ("peel_persistent", "peel.cu"), 2: ("peel_bsp", "peel_bsp.cu"), 3: ("peel_bsp", "peel_bsp.cu")}
 
 
 def kernel_revision(src: str = "peel_bsp.cu") -> str:
