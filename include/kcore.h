@@ -84,10 +84,16 @@ typedef enum {
                                          their induced degrees in shared memory (-1 = as many as
                                          fit with the CTAs per SM below) */
   KCORE_OPT_BATCH_CTAS_PER_SM = 13,   /* batched peel: resident CTAs per SM (0 = occupancy limit) */
-  KCORE_OPT_LOCAL_BATCHES = 14        /* mode 2: local-queue batches a warp may run after each chunk it
+  KCORE_OPT_LOCAL_BATCHES = 14,       /* mode 2: local-queue batches a warp may run after each chunk it
                                          takes (0 .. 2^20, 0 = no limit; default 32); the rest of its local queue
                                          then goes to the work queue, so a large cascade is shared by
                                          all warps in the next subround instead of one warp */
+  KCORE_OPT_LEVEL_WINDOW = 15         /* mode 2: bucketing of the active list (Sec. 5, the fixed number
+                                         of buckets): 0 = off (default); W > 0 = a rebuild scan splits
+                                         the live vertices into those below k+W (scanned level by
+                                         level) and an overflow list (scanned again only at the next
+                                         rebuild); a vertex enters the window when a decrement of its
+                                         induced degree returns k+W */
 } kcore_option;
 
 /* Counters of the last decomposition (valid after kcore_sync_status). */

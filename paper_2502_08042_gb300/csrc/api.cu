@@ -22,7 +22,7 @@ struct kcore_ctx {
   size_t ws_bytes = 0;
   bool ws_external = false;
   std::string err;
-  int64_t opt[15] = {0, 0, 0, -1, 2000, 1, 2048, 0, 0, 192, 64, 1024, -1, 0, 32};  // indexed by kcore_option
+  int64_t opt[16] = {0, 0, 0, -1, 2000, 1, 2048, 0, 0, 192, 64, 1024, -1, 0, 32, 0};  // indexed by kcore_option
   cudaStream_t last_stream = nullptr;
   bool pending = false;
   kc::PeelCtl* last_ctl = nullptr;
@@ -74,7 +74,7 @@ long long isqrt_ll(long long m) {
 }
 
 struct PeelLayout {
-  size_t deg, a0, a1, q, rounds, ctl, trace, hcnt, touched, total;
+  size_t deg, a0, a1, a2, q, rounds, ctl, trace, hcnt, touched, total;
   long long qcap;
   int max_rounds;
 };
@@ -100,6 +100,8 @@ PeelLayout peel_layout(long long n, long long m, int slice, bool offline = false
   L.a0 = off;
   off = align_up(off + 4 * (size_t)n, 256);
   L.a1 = off;
+  off = align_up(off + 4 * (size_t)n, 256);
+  L.a2 = off;  // third list buffer of the level window (sync mode 2)
   off = align_up(off + 4 * (size_t)n, 256);
   L.q = off;
   off = align_up(off + 8 * (size_t)L.qcap, 256);
@@ -198,7 +200,7 @@ kcore_status kcore_destroy(kcore_handle h) {
 const char* kcore_last_error(kcore_handle h) { return h ? h->err.c_str() : "null handle"; }
 
 kcore_status kcore_set_option(kcore_handle h, kcore_option opt, int64_t value) {
-  if (!h || (int)opt < 0 || (int)opt > 14) return KCORE_ERR_INVALID;
+  if (!h || (int)opt < 0 || (int)opt > 15) return KCORE_ERR_INVALID;
   switch (opt) {
     case KCORE_OPT_BATCH_BLOCK:
       if (value != 256 && value != 512 && value != 1024)
@@ -212,6 +214,9 @@ kcore_status kcore_set_option(kcore_handle h, kcore_option opt, int64_t value) {
       break;
     case KCORE_OPT_LOCAL_BATCHES:
       if (value < 0 || value > (1 << 20)) return fail(h, KCORE_ERR_INVALID, "local batches in [0, 2^20]");
+      break;
+    case KCORE_OPT_LEVEL_WINDOW:
+      if (value < 0 || value > (1 << 20)) return fail(h, KCORE_ERR_INVALID, "level window in [0, 2^20]");
       break;
     case KCORE_OPT_IDLE_SLEEP_NS:
     case KCORE_OPT_POLL_SLEEP_NS:
@@ -253,7 +258,7 @@ kcore_status kcore_set_option(kcore_handle h, kcore_option opt, int64_t value) {
 }
 
 kcore_status kcore_get_option(kcore_handle h, kcore_option opt, int64_t* value) {
-  if (!h || !value || (int)opt < 0 || (int)opt > 14) return KCORE_ERR_INVALID;
+  if (!h || !value || (int)opt < 0 || (int)opt > 15) return KCORE_ERR_INVALID;
   *value = h->opt[opt];
   return KCORE_OK;
 }
@@ -336,6 +341,8 @@ kcore_status peel_call(kcore_ctx* h, int64_t n, int64_t m, const int64_t* offset
   a.local_batches = h->opt[KCORE_OPT_LOCAL_BATCHES] > 0 ? (int)h->opt[KCORE_OPT_LOCAL_BATCHES] : INT32_MAX;
   a.threshold = threshold ? 1 : 0;
   a.offline = mode == 3 ? 1 : 0;
+  a.window = mode == 2 ? (int)h->opt[KCORE_OPT_LEVEL_WINDOW] : 0;
+  a.A2 = (int*)(ws + L.a2);
   a.hcnt = (int*)(ws + L.hcnt);
   a.touched = (int*)(ws + L.touched);
   a.kprime = threshold ? std::max<int32_t>(kprime, 0) : 0;

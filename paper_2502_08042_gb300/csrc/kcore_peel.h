@@ -101,6 +101,10 @@ struct PeelArgs {
   int offline;
   int* hcnt;
   int* touched;
+  // level window (bucketing of the active list, sync mode 2): 0 = off, else
+  // the number of levels a rebuild scan serves; A2 is the third list buffer
+  int window;
+  int* A2;
 };
 
 // Per-round trace record (KCORE_OPT_TRACE): globaltimer at round start (CTA 0),

@@ -156,7 +156,10 @@ __device__ __forceinline__ int block_excl_scan(Shared& sh, int x, int* total) {
 // step, so the offsets of only those vertices are read.
 __device__ ScanOut scan_range(const PeelArgs& a, Shared& sh, RoundRec* R, unsigned long long qbase,
                               const int* Ain, int* Aout, long long lo, long long hi, int keep_above,
-                              int take_at, bool take_le = false, int take_val = -1, int keep_val = -1) {
+                              int take_at, bool take_le = false, int take_val = -1, int keep_val = -1,
+                              int* Aover = nullptr, int over_from = INT_MAX) {
+  // Aover: kept entries with d~ >= over_from go there instead of Aout (the
+  // overflow list of a window rebuild; count in R->head)
   // take_le: take every entry with d~ <= take_at (k'-core query); take_val /
   // keep_val: the value written to core[] for taken / kept entries (-1: the
   // level take_at for taken ones, nothing for kept ones)
@@ -167,7 +170,7 @@ __device__ ScanOut scan_range(const PeelArgs& a, Shared& sh, RoundRec* R, unsign
   int dmin = INT_MAX;
   for (long long tile = lo; tile < hi; tile += (long long)kBlock * kTile) {
     int v[kTile];
-    unsigned keep = 0, take = 0;
+    unsigned keep = 0, take = 0, over = 0;
 #pragma unroll
     for (int q = 0; q < kTile; q++) {
       const long long i = tile + (long long)q * kBlock + tid;
@@ -202,7 +205,8 @@ __device__ ScanOut scan_range(const PeelArgs& a, Shared& sh, RoundRec* R, unsign
         d = __ldcg(a.deg + x);
       }
       if (d > keep_above) {
-        keep |= 1u << q;
+        if (d >= over_from) over |= 1u << q;
+        else keep |= 1u << q;
         dmin = min(dmin, d);
         if (keep_val >= 0) a.core[x] = keep_val;
       }
@@ -227,6 +231,16 @@ __device__ ScanOut scan_range(const PeelArgs& a, Shared& sh, RoundRec* R, unsign
     for (int q = 0; q < kTile; q++) {
       if ((keep >> q) & 1u) Aout[pa++] = v[q];
       if ((take >> q) & 1u) sh.stage[ps++] = v[q];
+    }
+    if (Aover) {
+      int otot;
+      const int oex = block_excl_scan(sh, __popc(over), &otot);
+      if (tid == 0) sh.base_q = otot ? atomicAdd(&R->head, (unsigned long long)otot) : 0;
+      __syncthreads();
+      unsigned long long po = sh.base_q + oex;
+#pragma unroll
+      for (int q = 0; q < kTile; q++)
+        if ((over >> q) & 1u) Aover[po++] = v[q];
     }
     __syncthreads();
     const int ntaken = tot >> 16;
@@ -293,6 +307,9 @@ struct PassCtx {
   int t;
   int val;                  // written to core[] of a vertex that crosses (t, or 0 in a k'-core query)
   bool precheck;            // long pass: read d~ before decrementing (see process_items)
+  int win_hi;               // level window's end (a decrement returning it appends the vertex), or -1
+  int* near;                // the active list, appended from near_base on (count in R->found)
+  unsigned long long near_base;
 };
 
 // Appends `cnt` items per lane (lane-owned arc ranges [e0, e1) cut in
@@ -341,6 +358,7 @@ __device__ __forceinline__ void push_crossed(const PeelArgs& a, Shared& sh, cons
 }
 
 // Arcs of the items held by lanes < c, spread evenly over the warp.
+template <bool kWin>
 __device__ void process_items(const PeelArgs& a, Shared& sh, const PassCtx& pc, unsigned long long item, int c,
                               int warp, int lane) {
   const int t = pc.t;
@@ -389,13 +407,33 @@ __device__ void process_items(const PeelArgs& a, Shared& sh, const PassCtx& pc, 
 #pragma unroll
       for (int q = 0; q < kIlp; q++) dq[q] = u[q] >= 0 ? INT_MAX : INT_MIN;
     }
-    unsigned cross = 0;
+    unsigned cross = 0, enter = 0;
 #pragma unroll
     for (int q = 0; q < kIlp; q++)
       if (dq[q] > t) {
         ndec++;
-        if (atomicSub(a.deg + u[q], 1) == t + 1) cross |= 1u << q;
+        const int old = atomicSub(a.deg + u[q], 1);
+        if (old == t + 1) cross |= 1u << q;
+        if (kWin && old == pc.win_hi) enter |= 1u << q;  // d~ drops into the level window
       }
+    if (kWin && __any_sync(kFull, enter != 0)) {
+      // append the vertices entering the window to the active list
+#pragma unroll
+      for (int q = 0; q < kIlp; q++) {
+        const bool f = (enter >> q) & 1u;
+        const unsigned fm = __ballot_sync(kFull, f);
+        if (fm) {
+          unsigned long long base = 0;
+          if (lane == 0) base = atomicAdd(&pc.R->found, (unsigned long long)__popc(fm));
+          base = __shfl_sync(kFull, base, 0);
+          const unsigned long long p = pc.near_base + base + __popc(fm & lanemask_lt());
+          if (f) {
+            if (p < (unsigned long long)a.n) pc.near[p] = u[q];
+            else raise_status(a, ST_CAPACITY);
+          }
+        }
+      }
+    }
     if (__any_sync(kFull, cross != 0)) {
 #pragma unroll
       for (int q = 0; q < kIlp; q++) {
@@ -421,6 +459,7 @@ __device__ void process_items(const PeelArgs& a, Shared& sh, const PassCtx& pc, 
 
 // Runs up to `budget` batches from the warp's local queue (vertices that
 // crossed during this pass), then moves what is left to the queue.
+template <bool kWin>
 __device__ void drain_local(const PeelArgs& a, Shared& sh, const PassCtx& pc, int warp, int lane,
                             long long& local_items, unsigned& local_batches) {
   for (int b = 0;; b++) {
@@ -446,7 +485,7 @@ __device__ void drain_local(const PeelArgs& a, Shared& sh, const PassCtx& pc, in
     __syncwarp();
     if (lane == 0) sh.lqn[warp] = lqn - c;
     __syncwarp();
-    process_items(a, sh, pc, item, c, warp, lane);
+    process_items<kWin>(a, sh, pc, item, c, warp, lane);
     local_items += c;
     if (lane == 0 && ((++local_batches) & 63) == 0) atomicAdd(&a.ctl->progress, 1ull);
   }
@@ -456,6 +495,7 @@ __device__ void drain_local(const PeelArgs& a, Shared& sh, const PassCtx& pc, in
 // its own contiguous share (len / warps items, one more for the first
 // len % warps warps) in chunks of up to 32 items, so a pass has no claim
 // traffic and ends for a warp as soon as its share and local queue are done.
+template <bool kWin>
 __device__ void run_pass(const PeelArgs& a, Shared& sh, const PassCtx& pc, unsigned long long qb,
                          unsigned long long qe, long long& items, long long& local_items,
                          unsigned& local_batches) {
@@ -468,9 +508,9 @@ __device__ void run_pass(const PeelArgs& a, Shared& sh, const PassCtx& pc, unsig
   for (unsigned long long pos = b; pos < e; pos += kTake) {
     const int c = (int)min((unsigned long long)kTake, e - pos);
     const unsigned long long item = lane < c ? __ldcg(a.Q + pos + lane) : 0;
-    process_items(a, sh, pc, item, c, warp, lane);
+    process_items<kWin>(a, sh, pc, item, c, warp, lane);
     items += c;
-    drain_local(a, sh, pc, warp, lane, local_items, local_batches);
+    drain_local<kWin>(a, sh, pc, warp, lane, local_items, local_batches);
   }
 }
 
@@ -588,7 +628,9 @@ __device__ void run_apply(const PeelArgs& a, const PassCtx& pc, unsigned long lo
   }
 }
 
-template <bool kOffline>
+// Instantiations: kOffline (Algorithm 2's subrounds) and kWindow (the level
+// window), each compiled apart so the default kernel carries neither.
+template <bool kOffline, bool kWindow>
 __global__ void __launch_bounds__(kBlock, 2) peel_bsp(PeelArgs a) {
   __shared__ Shared sh;
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
@@ -618,25 +660,48 @@ __global__ void __launch_bounds__(kBlock, 2) peel_bsp(PeelArgs a) {
     long long ns = (len + a.scan_min - 1) / a.scan_min;
     return ns < 1 ? 1ll : (ns > (long long)gridDim.x ? (long long)gridDim.x : ns);
   };
-  const int* Acur = nullptr;  // nullptr: the identity list 0..n-1
-  int* Afree = a.A0;
-  long long la = a.n;
+  // Window of levels [hi_w - W, hi_w) (bucketing, a.window = W > 0): the
+  // active list holds only vertices below hi_w; the others wait in the
+  // overflow list and enter the active list when a decrement returns exactly
+  // hi_w (once per vertex and window). When the next level reaches hi_w, a
+  // rebuild scan of the overflow list starts the next window. Three list
+  // buffers rotate: active, overflow and the output of the next scan.
+  const int W = (kWindow && !kOffline && a.window > 0 && !a.threshold) ? a.window : 0;
+  auto free_list = [&](const int* x, const int* y) -> int* {
+    return (x != a.A0 && y != a.A0) ? a.A0 : ((x != a.A1 && y != a.A1) ? a.A1 : a.A2);
+  };
+  const int* Acur = nullptr;   // active list (nullptr without window: all vertices)
+  long long la = W ? 0 : a.n;
+  const int* Aover = nullptr;  // overflow list (nullptr with window: all vertices, before the first rebuild)
+  long long lover = W ? a.n : 0;
+  int hi_w = W ? 0 : INT_MAX;
+  long long near_extra = 0;    // entries appended to the active list by the passes since its scan
   int tp = -1, kmax = 0;
-  long long levels = 0, empty = 0, scanned = 0, passes = 0, items = 0, local_items = 0;
+  long long levels = 0, empty = 0, scanned = 0, passes = 0, items = 0, local_items = 0, rebuilds = 0;
   unsigned local_batches = 0;
   unsigned long long qend = 0;  // items appended by all completed phases
+  bool was_rebuild = false;
   for (;;) {
     // ---- scan: keep d~ > tp+1, take d~ == tp+1 (a k'-core query: one level,
     // kprime - 1, taking every d~ below kprime and marking the rest 1)
     const int tk = a.threshold ? a.kprime - 1 : tp + 1;
+    const bool rebuild = W && tk >= hi_w;
+    was_rebuild = rebuild;
     const uint64_t t_start = lead && a.trace ? globaltimer_ns() : 0;
     reset_next();
     RoundRec* R = a.rounds + (phase % kPhaseRing);
-    long long nscan = nscan_of(la);
+    const int* Ain = rebuild ? Aover : Acur;
+    const long long lin = rebuild ? lover : la + near_extra;
+    int* Aout = free_list(Acur, Aover);
+    // a rebuild writes the overflow list to the exhausted active list's buffer
+    int* Aov = rebuild ? (Acur ? const_cast<int*>(Acur) : free_list(Aout, Aover)) : nullptr;
+    long long nscan = nscan_of(lin);
     if (blockIdx.x < nscan) {
-      const long long lo = la * blockIdx.x / nscan, hi = la * (blockIdx.x + 1) / nscan;
-      const ScanOut o = a.threshold ? scan_range(a, sh, R, qend, Acur, Afree, lo, hi, tk, tk, true, 0, 1)
-                                    : scan_range(a, sh, R, qend, Acur, Afree, lo, hi, tk, tk);
+      const long long lo = lin * blockIdx.x / nscan, hi = lin * (blockIdx.x + 1) / nscan;
+      const ScanOut o = a.threshold ? scan_range(a, sh, R, qend, Ain, Aout, lo, hi, tk, tk, true, 0, 1)
+                        : rebuild  ? scan_range(a, sh, R, qend, Ain, Aout, lo, hi, tk, tk, false, -1, -1, Aov,
+                                                tk + W)
+                                   : scan_range(a, sh, R, qend, Ain, Aout, lo, hi, tk, tk);
       if (tid == 0) {
         if (o.found) atomicAdd(&R->found, o.found);
         if (o.dmin != INT_MAX) atomicMax(&R->minkey, INT_MAX - o.dmin);
@@ -644,25 +709,34 @@ __global__ void __launch_bounds__(kBlock, 2) peel_bsp(PeelArgs a) {
     }
     if (!grid_barrier(a, sh, gen)) break;
     phase++;
-    scanned += la;
+    scanned += lin;
     const unsigned long long found = ld_relaxed_u64(&R->found);
     const long long alen = (long long)ld_relaxed_u64(&R->alen);
     const int minkey = ld_relaxed_s32(&R->minkey);
     unsigned long long qb = qend;
     qend += ld_relaxed_u64(&R->tail);
-    {
-      int* prev = const_cast<int*>(Acur);
-      Acur = Afree;
-      Afree = prev ? prev : a.A1;
+    Acur = Aout;
+    if (rebuild) {
+      Aover = Aov;
+      lover = (long long)ld_relaxed_u64(&R->head);
+      hi_w = tk + W;
+      rebuilds++;
     }
-    const long long la_scanned = la;
+    near_extra = 0;
+    const long long la_scanned = lin;
     la = alen;
     int t = tk;
     unsigned long long nfound = found;
     if (!found && !a.threshold) {
-      if (alen == 0) break;  // nothing left
-      // level tk is empty: the least induced degree of the kept vertices is the next level
+      if (alen == 0 && lover == 0) break;  // nothing left
       empty++;
+      if (W && alen == 0) {
+        // nothing left in the window: a rebuild starts the next one at the
+        // least d~ of the overflow list (known if this scan was a rebuild)
+        tp = rebuild ? INT_MAX - minkey - 1 : hi_w - 1;
+        continue;
+      }
+      // level tk is empty: the least induced degree of the kept vertices is the next level
       t = INT_MAX - minkey;
       reset_next();
       R = a.rounds + (phase % kPhaseRing);
@@ -695,7 +769,7 @@ __global__ void __launch_bounds__(kBlock, 2) peel_bsp(PeelArgs a) {
         // histogram phase: counts and the touched list (count in P->head)
         reset_next();
         RoundRec* P = a.rounds + (phase % kPhaseRing);
-        const PassCtx hc{P, qend, t, t, false};
+        const PassCtx hc{P, qend, t, t, false, -1, nullptr, 0};
         run_hist(a, sh, hc, qb, qend, items);
         if (!(ok = grid_barrier(a, sh, gen))) break;
         phase++;
@@ -703,7 +777,7 @@ __global__ void __launch_bounds__(kBlock, 2) peel_bsp(PeelArgs a) {
         // apply phase: crossings append the next frontier (count in P2->tail)
         reset_next();
         RoundRec* P2 = a.rounds + (phase % kPhaseRing);
-        const PassCtx pc{P2, qend, t, t, false};
+        const PassCtx pc{P2, qend, t, t, false, -1, nullptr, 0};
         run_apply(a, pc, nt);
         if (!(ok = grid_barrier(a, sh, gen))) break;
         phase++;
@@ -716,7 +790,7 @@ __global__ void __launch_bounds__(kBlock, 2) peel_bsp(PeelArgs a) {
         passes++;
         level_passes++;
       }
-    } else if (la > 0) {
+    } else if (la > 0 || lover > 0) {
       while (qend > qb) {
         reset_next();
         RoundRec* P = a.rounds + (phase % kPhaseRing);
@@ -724,8 +798,9 @@ __global__ void __launch_bounds__(kBlock, 2) peel_bsp(PeelArgs a) {
         // throughput-bound (measured: kNN's largest level 1,700 items per
         // warp; R-MAT passes a few)
         const bool pre = (qend - qb) >= (unsigned long long)kPrecheckShare * gridDim.x * kWarps;
-        const PassCtx pc{P, qend, t, a.threshold ? 0 : t, pre};
-        run_pass(a, sh, pc, qb, qend, items, local_items, local_batches);
+        const PassCtx pc{P, qend, t, a.threshold ? 0 : t, pre, W ? hi_w : -1, const_cast<int*>(Acur),
+                         (unsigned long long)(la + near_extra)};
+        run_pass<kWindow>(a, sh, pc, qb, qend, items, local_items, local_batches);
         if (a.threshold && lane == 0 && sh.ncross[warp]) {
           atomicAdd(&a.ctl->crossed, (unsigned long long)sh.ncross[warp]);
           sh.ncross[warp] = 0;
@@ -741,6 +816,7 @@ __global__ void __launch_bounds__(kBlock, 2) peel_bsp(PeelArgs a) {
         level_passes++;
         qb = qend;
         qend += ld_relaxed_u64(&P->tail);
+        if (W) near_extra += (long long)ld_relaxed_u64(&P->found);
       }
     } else {
       qb = qend;
@@ -757,6 +833,7 @@ __global__ void __launch_bounds__(kBlock, 2) peel_bsp(PeelArgs a) {
       tr[7] = (unsigned long long)nscan;
       tr[8] = ld_relaxed_u64(&a.ctl->tr_arcs) - arcs0;
       tr[9] = ld_relaxed_u64(&a.ctl->tr_decs) - decs0;
+      tr[10] = was_rebuild ? 1 : 0;
       tr[13] = (unsigned long long)level_passes;
     }
     if (a.threshold) {
@@ -764,7 +841,7 @@ __global__ void __launch_bounds__(kBlock, 2) peel_bsp(PeelArgs a) {
       if (ok && lead && a.size_out) *a.size_out = la - (long long)ld_relaxed_u64(&a.ctl->crossed);
       break;
     }
-    if (!ok || la == 0) break;
+    if (!ok || (la == 0 && lover == 0 && near_extra == 0)) break;
   }
   if (lane == 0) {
     if (items) atomicAdd(&a.ctl->items, (unsigned long long)items);
@@ -784,10 +861,11 @@ __global__ void __launch_bounds__(kBlock, 2) peel_bsp(PeelArgs a) {
 }  // namespace
 
 int bsp_max_ctas_per_sm() {
-  int nb = 0, nb2 = 0;
-  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, peel_bsp<false>, kBlock, 0) != cudaSuccess) return 0;
-  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb2, peel_bsp<true>, kBlock, 0) != cudaSuccess) return 0;
-  return nb < nb2 ? nb : nb2;
+  int nb = 0, nb2 = 0, nb3 = 0;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, peel_bsp<false, false>, kBlock, 0) != cudaSuccess) return 0;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb2, peel_bsp<true, false>, kBlock, 0) != cudaSuccess) return 0;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb3, peel_bsp<false, true>, kBlock, 0) != cudaSuccess) return 0;
+  return nb < nb2 ? (nb < nb3 ? nb : nb3) : (nb2 < nb3 ? nb2 : nb3);
 }
 
 int bsp_block_size() { return kBlock; }
@@ -795,7 +873,8 @@ int bsp_block_size() { return kBlock; }
 cudaError_t bsp_launch(const PeelArgs& args, int grid, cudaStream_t stream) {
   PeelArgs a = args;
   void* params[] = {&a};
-  const void* fn = a.offline ? (const void*)peel_bsp<true> : (const void*)peel_bsp<false>;
+  const void* fn = a.offline ? (const void*)peel_bsp<true, false>
+                             : (a.window > 0 ? (const void*)peel_bsp<false, true> : (const void*)peel_bsp<false, false>);
   return cudaLaunchCooperativeKernel(fn, dim3(grid), dim3(kBlock), params, 0, stream);
 }
 

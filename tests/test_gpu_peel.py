@@ -271,3 +271,32 @@ def test_offline_subrounds_are_algorithm_1s(seed):
     assert gs["passes"] == st["subrounds"]
     assert gs["rounds"] - gs["empty_rounds"] == st["nonempty_rounds"]
     assert gs["local_items"] == 0
+
+
+@pytest.mark.parametrize("W", [1, 2, 7, 16, 64, 100000])
+def test_level_window(W):
+    """Bucketing of the active list (mode 2, KCORE_OPT_LEVEL_WINDOW): the same
+    coreness for every window size, on graphs with many levels, empty levels
+    between them, isolated vertices and hubs."""
+    n0 = 30000
+    s, d = gg.rmat_n(n0, 300000, seed=5)
+    n, s2, d2 = gg.disjoint_union((n0, s, d), gg.staircase(120), gg.path(2000), gg.star(3000),
+                                  gg.complete(45), (17, np.zeros(0, np.int32), np.zeros(0, np.int32)))
+    off, adj = _csr(n, s2, d2)
+    want = oracle.bz(n, off, adj)
+    with KCore(0, level_window=W, trace=1) as k:
+        assert_parity(k, n, off, adj, want)
+        st = k.stats()
+        tr = k.trace()
+        # every closed form and random graph of the earlier tests as well
+        for i in range(len(CLOSED)):
+            nn, ss, dd = CLOSED[i]
+            o2, a2 = _csr(nn, ss, dd)
+            assert_parity(k, nn, o2, a2)
+    assert st["sync_mode"] == 2
+    levels = tr[:, 3].astype(np.int64)
+    np.testing.assert_array_equal(levels, np.unique(want))
+    rebuilds = int(tr[:, 10].sum())
+    assert rebuilds >= 1
+    if W == 1:
+        assert rebuilds >= len(levels) // 2  # a rebuild (almost) every level
