@@ -88,12 +88,17 @@ typedef enum {
                                          takes (0 .. 2^20, 0 = no limit; default 32); the rest of its local queue
                                          then goes to the work queue, so a large cascade is shared by
                                          all warps in the next subround instead of one warp */
-  KCORE_OPT_LEVEL_WINDOW = 15         /* mode 2: bucketing of the active list (Sec. 5, the fixed number
+  KCORE_OPT_LEVEL_WINDOW = 15,        /* mode 2: bucketing of the active list (Sec. 5, the fixed number
                                          of buckets): 0 = off (default); W > 0 = a rebuild scan splits
                                          the live vertices into those below k+W (scanned level by
                                          level) and an overflow list (scanned again only at the next
                                          rebuild); a vertex enters the window when a decrement of its
                                          induced degree returns k+W */
+  KCORE_OPT_BATCH_UPDATE = 16         /* mode 2: 1 (default) = a heavy subround (at least a quarter of
+                                         an item per warp and one per active vertex) counts its
+                                         decrements per neighbour with reductions and then applies
+                                         them walking the active list (Algorithm 2's batch update);
+                                         0 = every subround decrements with returning atomics */
 } kcore_option;
 
 /* Counters of the last decomposition (valid after kcore_sync_status). */

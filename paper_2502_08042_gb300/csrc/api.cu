@@ -22,7 +22,7 @@ struct kcore_ctx {
   size_t ws_bytes = 0;
   bool ws_external = false;
   std::string err;
-  int64_t opt[16] = {0, 0, 0, -1, 2000, 1, 2048, 0, 0, 192, 64, 1024, -1, 0, 32, 0};  // indexed by kcore_option
+  int64_t opt[17] = {0, 0, 0, -1, 2000, 1, 2048, 0, 0, 192, 64, 1024, -1, 0, 32, 0, 1};  // indexed by kcore_option
   cudaStream_t last_stream = nullptr;
   bool pending = false;
   kc::PeelCtl* last_ctl = nullptr;
@@ -200,7 +200,7 @@ kcore_status kcore_destroy(kcore_handle h) {
 const char* kcore_last_error(kcore_handle h) { return h ? h->err.c_str() : "null handle"; }
 
 kcore_status kcore_set_option(kcore_handle h, kcore_option opt, int64_t value) {
-  if (!h || (int)opt < 0 || (int)opt > 15) return KCORE_ERR_INVALID;
+  if (!h || (int)opt < 0 || (int)opt > 16) return KCORE_ERR_INVALID;
   switch (opt) {
     case KCORE_OPT_BATCH_BLOCK:
       if (value != 256 && value != 512 && value != 1024)
@@ -217,6 +217,9 @@ kcore_status kcore_set_option(kcore_handle h, kcore_option opt, int64_t value) {
       break;
     case KCORE_OPT_LEVEL_WINDOW:
       if (value < 0 || value > (1 << 20)) return fail(h, KCORE_ERR_INVALID, "level window in [0, 2^20]");
+      break;
+    case KCORE_OPT_BATCH_UPDATE:
+      if (value < 0 || value > 1) return fail(h, KCORE_ERR_INVALID, "batch update must be 0 or 1");
       break;
     case KCORE_OPT_IDLE_SLEEP_NS:
     case KCORE_OPT_POLL_SLEEP_NS:
@@ -258,14 +261,15 @@ kcore_status kcore_set_option(kcore_handle h, kcore_option opt, int64_t value) {
 }
 
 kcore_status kcore_get_option(kcore_handle h, kcore_option opt, int64_t* value) {
-  if (!h || !value || (int)opt < 0 || (int)opt > 15) return KCORE_ERR_INVALID;
+  if (!h || !value || (int)opt < 0 || (int)opt > 16) return KCORE_ERR_INVALID;
   *value = h->opt[opt];
   return KCORE_OK;
 }
 
 kcore_status kcore_workspace_size(kcore_handle h, int64_t n, int64_t m, size_t* bytes) {
   if (!h || !bytes || n < 0 || m < 0 || n > INT32_MAX - 1) return KCORE_ERR_INVALID;
-  *bytes = peel_layout(n, m, effective_slice(h), effective_mode(h) == 3).total;
+  *bytes = peel_layout(n, m, effective_slice(h),
+                       effective_mode(h) == 3 || (effective_mode(h) == 2 && h->opt[KCORE_OPT_BATCH_UPDATE])).total;
   return KCORE_OK;
 }
 
@@ -310,7 +314,9 @@ kcore_status peel_call(kcore_ctx* h, int64_t n, int64_t m, const int64_t* offset
   }
   const int mode = threshold ? 2 : effective_mode(h);
   const int slice = h->opt[KCORE_OPT_SLICE_ARCS] > 0 ? (int)h->opt[KCORE_OPT_SLICE_ARCS] : (mode == 1 ? 512 : 64);
-  PeelLayout L = peel_layout(n, m, slice, mode == 3);
+  const bool hybrid = mode == 2 && !threshold && h->opt[KCORE_OPT_BATCH_UPDATE] != 0 &&
+                      h->opt[KCORE_OPT_LEVEL_WINDOW] == 0;
+  PeelLayout L = peel_layout(n, m, slice, mode == 3 || hybrid);
   kcore_status st = ensure_ws(h, L.total);
   if (st != KCORE_OK) return st;
   char* ws = (char*)h->ws;
@@ -342,6 +348,7 @@ kcore_status peel_call(kcore_ctx* h, int64_t n, int64_t m, const int64_t* offset
   a.threshold = threshold ? 1 : 0;
   a.offline = mode == 3 ? 1 : 0;
   a.window = mode == 2 ? (int)h->opt[KCORE_OPT_LEVEL_WINDOW] : 0;
+  a.hybrid = hybrid ? 1 : 0;
   a.A2 = (int*)(ws + L.a2);
   a.hcnt = (int*)(ws + L.hcnt);
   a.touched = (int*)(ws + L.touched);
@@ -369,7 +376,7 @@ kcore_status peel_call(kcore_ctx* h, int64_t n, int64_t m, const int64_t* offset
   if (a.trace && (e = cudaMemsetAsync(a.trace, 0, 8 * (size_t)kc::kTraceFields * (size_t)L.max_rounds,
                                       stream)) != cudaSuccess)
     return cuda_fail(h, e, "memset trace");
-  if (mode == 3 && (e = cudaMemsetAsync(a.hcnt, 0, 4 * (size_t)n, stream)) != cudaSuccess)
+  if ((mode == 3 || hybrid) && (e = cudaMemsetAsync(a.hcnt, 0, 4 * (size_t)n, stream)) != cudaSuccess)
     return cuda_fail(h, e, "memset counts");
   e = mode != 1 ? kc::bsp_launch(a, (int)grid, stream) : kc::peel_launch(a, (int)grid, stream);
   if (e != cudaSuccess) return cuda_fail(h, e, "peel launch");

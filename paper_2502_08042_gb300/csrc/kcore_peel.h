@@ -105,6 +105,9 @@ struct PeelArgs {
   // the number of levels a rebuild scan serves; A2 is the third list buffer
   int window;
   int* A2;
+  // heavy subrounds over a short active list use Algorithm 2's batch update
+  // (counts in hcnt, zero at launch and left zero)
+  int hybrid;
 };
 
 // Per-round trace record (KCORE_OPT_TRACE): globaltimer at round start (CTA 0),

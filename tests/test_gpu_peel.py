@@ -227,7 +227,8 @@ def test_bsp_counters_and_trace():
     s, d = gg.rmat_n(n, 500000, seed=21)
     off, adj = _csr(n, s, d)
     want = oracle.bz(n, off, adj)
-    with KCore(0, sync_mode=2, trace=1) as k:
+    # (a batch-updated heavy subround takes two barriers: counted here without)
+    with KCore(0, sync_mode=2, trace=1, batch_update=0) as k:
         assert_parity(k, n, off, adj, want)
         st = k.stats()
         tr = k.trace()
@@ -300,3 +301,26 @@ def test_level_window(W):
     assert rebuilds >= 1
     if W == 1:
         assert rebuilds >= len(levels) // 2  # a rebuild (almost) every level
+
+
+def test_batch_update_of_heavy_subrounds():
+    """KCORE_OPT_BATCH_UPDATE: heavy subrounds count decrements with
+    reductions and apply them walking the active list; the coreness is the
+    oracle's on graphs with dense cores, hubs, long paths and many levels."""
+    n0 = 40000
+    s, d = gg.rmat_n(n0, 600000, seed=8)
+    n, s2, d2 = gg.disjoint_union((n0, s, d), gg.complete(200), gg.staircase(150), gg.star(5000),
+                                  gg.path(3000), (9, np.zeros(0, np.int32), np.zeros(0, np.int32)))
+    off, adj = _csr(n, s2, d2)
+    want = oracle.bz(n, off, adj)
+    with KCore(0, batch_update=1) as k:
+        assert_parity(k, n, off, adj, want)
+        for i in range(len(CLOSED)):
+            nn, ss, dd = CLOSED[i]
+            o2, a2 = _csr(nn, ss, dd)
+            assert_parity(k, nn, o2, a2)
+        for seed in range(4):
+            nn = 20000
+            ss, dd = gg.rmat_n(nn, 30 * nn, seed=70 + seed)
+            o2, a2 = _csr(nn, ss, dd)
+            assert_parity(k, nn, o2, a2)
