@@ -44,6 +44,39 @@ UNIT = "undirected edges/s"
 L2_BYTES = 129 * 1024 * 1024
 
 
+NOMINAL_PEAK = {"GB/s": 7900.0, "TFLOP/s": 2250.0}  # GB300 datasheet: HBM3e, dense bf16
+
+
+def host_cpu() -> dict:
+    """Model, architecture and logical cores of the host the CPU legs ran on."""
+    import platform
+    model = None
+    try:
+        with open("/proc/cpuinfo") as f:
+            for line in f:
+                key = line.split(":")[0].strip().lower()
+                if key in ("model name", "hardware", "cpu model"):
+                    model = line.split(":", 1)[1].strip()
+                    break
+    except OSError:
+        pass
+    return {"model": model or platform.processor() or None, "arch": platform.machine(),
+            "logical_cores": os.cpu_count()}
+
+
+def emit(out: dict) -> None:
+    """Prints the bench line, adding the roofline fraction of the nominal peak
+    beside the measured one and the host CPU beside the CPU baseline."""
+    rf = out.get("roofline")
+    if rf and rf.get("achieved") is not None and rf.get("unit") in NOMINAL_PEAK:
+        rf["peak_nominal"] = NOMINAL_PEAK[rf["unit"]]
+        rf["frac_nominal"] = rf["achieved"] / NOMINAL_PEAK[rf["unit"]]
+    cb = out.get("cpu_baseline")
+    if cb:
+        cb["host"] = host_cpu()
+    print(json.dumps(out), flush=True)
+
+
 def load_peaks():
     p = os.path.join(ROOT, "MEASURED_PEAKS.json")
     if os.path.exists(p):
@@ -281,7 +314,7 @@ def run_kquery(args):
     cl = clk.summary()
     if cl:
         out["clocks"] = cl
-    print(json.dumps(out), flush=True)
+    emit(out)
 
 
 def run_reference(args):
@@ -304,7 +337,7 @@ def run_reference(args):
     value = mu * args.steps / dt
     sample = (f"each step: Batagelj-Zaversnik on R-MAT scale {scale} (same generator as "
               f"{args.workload}, {mu} undirected edges), 1 host core")
-    print(json.dumps({
+    emit({
         "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": dt * 1e3 / args.steps,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "int32",
@@ -312,7 +345,7 @@ def run_reference(args):
         "config": {"workload": f"{args.workload} (CPU sample: rmat{scale})", "parallelism": "none"},
         "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample},
         "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
-    }), flush=True)
+    })
 
 
 def run_gpu(args):
@@ -443,7 +476,7 @@ def run_gpu(args):
     clocks = clk.summary()
     if clocks:
         out["clocks"] = clocks
-    print(json.dumps(out), flush=True)
+    emit(out)
     if ws > 1:
         dist.barrier()
 
@@ -588,7 +621,7 @@ def run_batched(args):
     c = clk.summary()
     if c:
         out["clocks"] = c
-    print(json.dumps(out), flush=True)
+    emit(out)
 
 
 def cpu_batch_baseline(spec, gv, G, sample: int = 256):
@@ -728,7 +761,7 @@ def run_served(args):
                 "d2h_bytes_per_step": int(sum(4 * (len(o) - 1) + 4 for o, _ in reqs))},
         "gpu_launches": None,
     }
-    print(json.dumps(out), flush=True)
+    emit(out)
 
 
 # single-graph schedule (stats "sync_mode") -> (kernel name, its source file)

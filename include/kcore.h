@@ -101,7 +101,8 @@ typedef enum {
                                          0 = every subround decrements with returning atomics */
 } kcore_option;
 
-/* Counters of the last decomposition (valid after kcore_sync_status). */
+/* Counters of the last decomposition, or of the last CSR check (the three
+ * invalid_* fields), valid after kcore_sync_status. */
 typedef struct {
   int64_t rounds;          /* levels visited, empty speculative levels included */
   int64_t empty_rounds;    /* visited levels that held no vertex */
@@ -116,7 +117,10 @@ typedef struct {
   int64_t batch_block;     /* batched calls: threads per CTA used */
   int64_t batch_smem_vertices; /* batched calls: largest graph kept in shared memory */
   int64_t slice_arcs;      /* arcs per work item the last decomposition used */
-  int64_t reserved[3];
+  int64_t invalid_check;   /* kcore_validate_csr: first failed check (1..6), 0 if the CSR is simple */
+  int64_t invalid_vertex;  /* kcore_validate_csr: the vertex of that failure */
+  int64_t invalid_arc;     /* kcore_validate_csr: the failing arc (index into adj); for codes 1
+                              and 2 the offending offset value instead */
 } kcore_stats;
 
 /* Creates a handle on `device` (CUDA ordinal). The handle owns a workspace
@@ -165,6 +169,25 @@ kcore_status kcore_decompose(kcore_handle h, int64_t n, int64_t m, const int64_t
 kcore_status kcore_decompose_host(kcore_handle h, int64_t n, int64_t m, const int64_t* offsets_host,
                                   const int32_t* adj_host, int32_t* coreness_host,
                                   int32_t* kmax_host, kcore_stream_t stream);
+
+/* Checks that a CSR is the simple undirected graph every decomposition entry
+ * point requires (Sec. 2: undirected, no self-loops, no parallel edges) and
+ * that kcore_build_csr produces. Optional: the decompositions assume it and do
+ * not check it (a malformed graph gives undefined coreness, never an access
+ * outside the arrays described by offsets). Checks, in this order of codes:
+ *   1  offsets monotone and within [0, m]      2  offsets[0] = 0, offsets[n] = m
+ *   3  every neighbour id in [0, n)            4  no self-loop
+ *   5  each list strictly ascending (no repeated arc)
+ *   6  symmetry: u in list(v) implies v in list(u) (binary search in list(u))
+ *   n, m         vertices and arcs (0 <= n <= 2^31 - 2; m = 0 when n = 0)
+ *   offsets, adj device int64[n+1], int32[m], borrowed, read only
+ * Asynchronous: two kernels on `stream`, O(m log d_max) work. kcore_sync_status
+ * returns KCORE_OK for a simple CSR, else KCORE_ERR_NOT_SIMPLE with the first
+ * failure recorded (which one, when several threads fail at once, is
+ * unspecified) in kcore_stats.invalid_check / invalid_vertex / invalid_arc and
+ * in kcore_last_error. Uses 64 bytes of the handle's workspace. */
+kcore_status kcore_validate_csr(kcore_handle h, int64_t n, int64_t m, const int64_t* offsets,
+                                const int32_t* adj, kcore_stream_t stream);
 
 /* Simple undirected CSR of an edge list (a1 of the pipeline; the paper
  * symmetrises directed inputs, Sec. 6.1 "Datasets"): every pair (src[i],

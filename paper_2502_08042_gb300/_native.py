@@ -98,8 +98,8 @@ c_i64, c_i32, c_p, c_sz = ctypes.c_int64, ctypes.c_int32, ctypes.c_void_p, ctype
 class Stats(ctypes.Structure):
     _fields_ = [(name, c_i64) for name in ("rounds", "empty_rounds", "items", "local_items",
                                            "scanned", "kmax", "grid", "sync_mode", "passes",
-                                           "barriers", "batch_block", "batch_smem_vertices", "slice_arcs")] + \
-               [("reserved", c_i64 * 3)]
+                                           "barriers", "batch_block", "batch_smem_vertices", "slice_arcs",
+                                           "invalid_check", "invalid_vertex", "invalid_arc")]
 
 
 class BatchTuning(ctypes.Structure):
@@ -120,6 +120,7 @@ SIGNATURES = {
     "kcore_decompose": ([c_p, c_i64, c_i64, c_p, c_p, c_p, c_p, c_p], ctypes.c_int),
     "kcore_decompose_host": ([c_p, c_i64, c_i64, c_p, c_p, c_p, c_p, c_p], ctypes.c_int),
     "kcore_core_mask": ([c_p, c_i64, c_i64, c_p, c_p, ctypes.c_int32, c_p, c_p, c_p], ctypes.c_int),
+    "kcore_validate_csr": ([c_p, c_i64, c_i64, c_p, c_p, c_p], ctypes.c_int),
     "kcore_sync_status": ([c_p], ctypes.c_int),
     "kcore_get_stats": ([c_p, ctypes.POINTER(Stats)], ctypes.c_int),
     "kcore_get_trace": ([c_p, c_p, c_i64, ctypes.POINTER(c_i64)], ctypes.c_int),

@@ -28,6 +28,7 @@ struct kcore_ctx {
   kc::PeelCtl* last_ctl = nullptr;
   int* last_csr_status = nullptr;  // device status word of the last CSR build
   int* last_batch_status = nullptr;  // device status word of the last batched call
+  int* last_validate_status = nullptr;  // device status words of the last CSR check
   int last_batch_block = 0, last_batch_grid = 0, last_batch_smem_vertices = 0;
   unsigned long long* last_trace = nullptr;
   int last_max_rounds = 0;
@@ -305,6 +306,7 @@ kcore_status peel_call(kcore_ctx* h, int64_t n, int64_t m, const int64_t* offset
   h->last_trace = nullptr;
   h->last_stream = stream;
   h->pending = true;
+  h->last_validate_status = nullptr;
   if (n == 0) {
     cudaError_t e = cudaSuccess;
     if (kmax_out) e = cudaMemsetAsync(kmax_out, 0, sizeof(int32_t), stream);
@@ -413,6 +415,35 @@ kcore_status kcore_core_mask(kcore_handle h, int64_t n, int64_t m, const int64_t
   return peel_call(h, n, m, offsets, adj, mask_out, nullptr, (cudaStream_t)stream_, true, kprime, size_out);
 }
 
+kcore_status kcore_validate_csr(kcore_handle h, int64_t n, int64_t m, const int64_t* offsets, const int32_t* adj,
+                               kcore_stream_t stream_) {
+  if (!h) return KCORE_ERR_INVALID;
+  if (n < 0 || m < 0 || n > INT32_MAX - 1) return fail(h, KCORE_ERR_INVALID, "n or m out of range");
+  if (n == 0 && m > 0) return fail(h, KCORE_ERR_INVALID, "arcs given for an empty vertex set");
+  if (n > 0 && !offsets) return fail(h, KCORE_ERR_INVALID, "null offsets");
+  if (m > 0 && !adj) return fail(h, KCORE_ERR_INVALID, "null adj with m > 0");
+  cudaStream_t stream = (cudaStream_t)stream_;
+  DeviceGuard g(h->device);
+  if (!g.ok) return fail(h, KCORE_ERR_CUDA, "cudaSetDevice failed");
+  h->err.clear();
+  h->stats = kcore_stats{};
+  h->last_ctl = nullptr;
+  h->last_csr_status = nullptr;
+  h->last_batch_status = nullptr;
+  h->last_trace = nullptr;
+  h->last_validate_status = nullptr;
+  h->last_stream = stream;
+  h->pending = true;
+  h->last_validate_status = nullptr;
+  if (n == 0) return KCORE_OK;
+  kcore_status st = ensure_ws(h, 64);
+  if (st != KCORE_OK) return st;
+  cudaError_t e = kc::validate_launch(n, m, (const long long*)offsets, adj, (int*)h->ws, h->sms, stream);
+  if (e != cudaSuccess) return cuda_fail(h, e, "CSR check launch");
+  h->last_validate_status = (int*)h->ws;
+  return KCORE_OK;
+}
+
 kcore_status kcore_build_csr_workspace_size(kcore_handle h, int64_t n, int64_t num_edges, size_t* bytes) {
   if (!h || !bytes || n < 0 || n > INT32_MAX - 1 || num_edges < 0) return KCORE_ERR_INVALID;
   *bytes = kc::csr_layout(n, num_edges, h->sms).total;
@@ -437,6 +468,7 @@ kcore_status kcore_build_csr(kcore_handle h, int64_t n, int64_t num_edges, const
   h->last_batch_status = nullptr;
   h->last_stream = stream;
   h->pending = true;
+  h->last_validate_status = nullptr;
   kc::CsrLayout L = kc::csr_layout(n, num_edges, h->sms);
   kcore_status st = ensure_ws(h, L.total);
   if (st != KCORE_OK) return st;
@@ -534,6 +566,7 @@ kcore_status kcore_decompose_batched(kcore_handle h, int64_t num_graphs, int64_t
   h->last_batch_status = nullptr;
   h->last_stream = stream;
   h->pending = true;
+  h->last_validate_status = nullptr;
   if (num_graphs == 0) return KCORE_OK;
   BatchLayout L = batch_layout(num_graphs, total_vertices);
   kcore_status st = ensure_ws(h, L.total);
@@ -593,6 +626,7 @@ kcore_status kcore_build_csr_batched(kcore_handle h, int64_t num_graphs, int64_t
   h->last_batch_status = nullptr;
   h->last_stream = stream;
   h->pending = true;
+  h->last_validate_status = nullptr;
   kc::CsrLayout L = kc::csr_layout(total_vertices, num_edges, h->sms, max_graph_vertices);
   kcore_status st = ensure_ws(h, L.total);
   if (st != KCORE_OK) return st;
@@ -628,6 +662,28 @@ kcore_status kcore_sync_status(kcore_handle h) {
     }
     if (bs[0] != 0) return fail(h, KCORE_ERR_CUDA, "unknown device status " + std::to_string(bs[0]));
     return KCORE_OK;
+  }
+  if (h->last_validate_status) {
+    long long vs[4] = {0, 0, 0, 0};
+    e = cudaMemcpy(vs, h->last_validate_status, sizeof(vs), cudaMemcpyDeviceToHost);
+    h->last_validate_status = nullptr;
+    if (e != cudaSuccess) return cuda_fail(h, e, "read status");
+    const int code = (int)(vs[0] & 0xffffffff);
+    static const char* what[] = {"",
+                                 "offsets not monotone or outside [0, m]",
+                                 "offsets[0] != 0 or offsets[n] != m",
+                                 "neighbour id outside [0, n)",
+                                 "self-loop",
+                                 "list not strictly ascending (repeated arc or unsorted)",
+                                 "arc without its reverse (not symmetric)"};
+    if (code == 0) return KCORE_OK;
+    if (code < 0 || code > 6) return fail(h, KCORE_ERR_CUDA, "unknown check code " + std::to_string(code));
+    h->stats.invalid_check = code;
+    h->stats.invalid_vertex = vs[1];
+    h->stats.invalid_arc = vs[2];
+    return fail(h, KCORE_ERR_NOT_SIMPLE,
+                std::string("CSR is not simple: ") + what[code] + " (vertex " + std::to_string(vs[1]) +
+                    ", arc " + std::to_string(vs[2]) + ")");
   }
   if (h->last_csr_status) {
     int cs = 0;

@@ -129,4 +129,9 @@ int bsp_max_ctas_per_sm();
 int bsp_block_size();
 cudaError_t bsp_launch(const PeelArgs& args, int grid, cudaStream_t stream);
 
+// Simple-CSR check (validate.cu). st: device int[8] (code, pad, vertex, arc as
+// int64); zeroed by the launch, code 0 when the CSR is simple.
+cudaError_t validate_launch(long long n, long long m, const long long* off, const int* adj, int* st, int sms,
+                            cudaStream_t stream);
+
 }  // namespace kc

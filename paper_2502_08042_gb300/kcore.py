@@ -117,7 +117,7 @@ class KCore:
     def stats(self) -> dict:
         s = _native.Stats()
         self._check(self._L.kcore_get_stats(self._h, ctypes.byref(s)))
-        return {f: int(getattr(s, f)) for f, _ in _native.Stats._fields_ if f != "reserved"}
+        return {f: int(getattr(s, f)) for f, _ in _native.Stats._fields_}
 
     def trace(self) -> np.ndarray:
         """Per-round timeline of the last decomposition (needs trace=1):
@@ -168,6 +168,20 @@ class KCore:
         if sync:
             self.sync()
         return mask, size
+
+    def validate_csr(self, offsets, adj, stream=None, sync: bool = True) -> None:
+        """Checks on the GPU that (offsets, adj) is a simple undirected CSR
+        (offsets sound, ids in range, no self-loops, ascending lists,
+        symmetric). With sync, raises KCoreError (code NOT_SIMPLE) naming the
+        first failure; stats() then holds invalid_check/_vertex/_arc."""
+        torch = _torch()
+        n = offsets.numel() - 1
+        m = adj.numel()
+        assert offsets.dtype == torch.int64 and adj.dtype == torch.int32
+        assert offsets.is_cuda and adj.is_cuda and offsets.is_contiguous() and adj.is_contiguous()
+        self._check(self._L.kcore_validate_csr(self._h, n, m, _ptr(offsets), _ptr(adj), _stream_ptr(stream)))
+        if sync:
+            self.sync()
 
     def decompose_batched(self, graph_vertex_offsets, offsets, adj, coreness=None, kmax=None,
                           stream=None, sync: bool = True):

@@ -7,7 +7,7 @@ import pytest
 
 import graphgen as gg
 import oracle
-from tests import golden_io
+from tests import csr_defects, golden_io
 
 
 def _csr(n, s, d):
@@ -209,6 +209,19 @@ def test_check_simple_rejects_bad_csr():
     a3 = adj.copy()
     a3[off[2]] = 2  # self-loop
     assert oracle.check_simple(n, off, a3) != 0
+
+
+@pytest.mark.parametrize("kind", csr_defects.KINDS)
+def test_check_simple_finds_each_planted_defect(kind):
+    # each planted defect is the only failure, so the oracle's first failed
+    # check is the one planted
+    rng = np.random.default_rng(7)
+    for seed in range(4):
+        n = 400
+        s, d = gg.er(n, 1600, seed=seed) if seed % 2 == 0 else gg.rmat_n(n, 3000, seed=seed)
+        off, adj = oracle.build_csr(n, s, d)
+        o, a, code, v, arc = csr_defects.plant(n, off, adj, kind, rng)
+        assert oracle.check_simple(n, o, a) == csr_defects.ORACLE_CODE[code]
 
 
 def test_build_csr_rejects_out_of_range():
