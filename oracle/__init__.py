@@ -6,8 +6,9 @@ it shares no code with the CUDA path.
 
 Coreness (Sec. 2, "Notations"): the k-core is the largest subgraph with minimum
 degree >= k; the coreness of v is the largest k with v in the k-core. The C
-routines (``kcore_oracle.c``) compute it by Batagelj-Zaversnik and by
-Algorithm 1 with the sequential Peel, and check any claimed answer with a
+routines (``kcore_oracle.c``) compute it by Batagelj-Zaversnik, by
+Algorithm 1 with the sequential Peel and by Algorithm 4 with the sampling Peel
+of Algorithm 5 (Philox coins), and check any claimed answer with a
 certificate; ``brute.py`` recomputes it from the definition for tiny graphs.
 """
 from __future__ import annotations
@@ -59,6 +60,10 @@ def _L():
             lib.oc_check.restype = ctypes.c_int
             lib.oc_kcore_mask.argtypes = [i64, p, p, ctypes.c_int32, p]
             lib.oc_kcore_mask.restype = i64
+            lib.oc_philox4x32_10.argtypes = [p, p, p]
+            lib.oc_philox4x32_10.restype = None
+            lib.oc_kcore_sampled.argtypes = [i64, p, p, i64, i64, ctypes.c_uint64, p, p]
+            lib.oc_kcore_sampled.restype = ctypes.c_int
             _lib = lib
     return _lib
 
@@ -141,6 +146,36 @@ def kcore_mask(n: int, off, adj, kprime: int):
     if size < 0:
         raise MemoryError("oracle.kcore_mask")
     return mask, int(size)
+
+
+def philox4x32_10(ctr, key):
+    """Philox4x32-10 (Salmon et al., SC 2011) of a 4-word counter and a 2-word
+    key: the four output words."""
+    c = (ctypes.c_uint32 * 4)(*[int(x) & 0xFFFFFFFF for x in ctr])
+    k = (ctypes.c_uint32 * 2)(*[int(x) & 0xFFFFFFFF for x in key])
+    o = (ctypes.c_uint32 * 4)()
+    _L().oc_philox4x32_10(c, k, o)
+    return tuple(int(x) for x in o)
+
+
+SAMPLED_STATS = ("sampled_at_start", "recounts", "bag_inserts", "failed_validations", "heads",
+                 "miss_round", "miss_vertex", "rounds")
+
+
+def kcore_sampled(n: int, off, adj, mu: int, threshold: int, seed: int = 0):
+    """Algorithm 4 with the sampling Peel of Algorithm 5 (Sec. 4.1), round by
+    round. Returns (ok, core, stats): ok False when the recovery check found a
+    vertex that missed an earlier round (core is then incomplete)."""
+    off = _c(off, np.int64)
+    adj = _c(adj, np.int32)
+    core = np.full(max(n, 0), -1, np.int32)
+    st = np.zeros(8, np.int64)
+    rc = _L().oc_kcore_sampled(n, off.ctypes.data, adj.ctypes.data if len(adj) else None, int(mu),
+                               int(threshold), ctypes.c_uint64(int(seed) & (2**64 - 1)), core.ctypes.data,
+                               st.ctypes.data)
+    if rc < 0:
+        raise MemoryError("oracle.kcore_sampled")
+    return rc == 0, core, dict(zip(SAMPLED_STATS, (int(x) for x in st)))
 
 
 def kmax(core) -> int:

@@ -21,6 +21,13 @@
  *            Theorem 1 (sum of active-set sizes, frontier insertions).
  *   oc_kcore_mask  The k'-core alone (App. B): repeated deletion of the
  *            vertices whose remaining degree is below k'.
+ *   oc_kcore_sampled  Algorithm 4 with the sampling Peel of Algorithm 5
+ *            (Sec. 4.1), round by round, with the recovery check of "Recover
+ *            from Errors"; its coins are Philox4x32-10 (oc_philox4x32_10) of
+ *            the arc index, so the GPU and this code draw the same coin for the
+ *            same arc. Pinned by the generator's published known answers, the
+ *            binomial law of the heads on a star, Algorithm 1 when nothing is
+ *            sampled, and exactness whenever no miss is reported.
  *   oc_check A certificate check that needs no decomposition: (i) every v
  *            with value c has at least c neighbours with value >= c (so the
  *            set {value >= c} has minimum degree >= c and lies inside the
@@ -358,4 +365,224 @@ int64_t oc_kcore_mask(int64_t n, const int64_t* off, const int32_t* adj, int32_t
   free(left);
   free(q);
   return n - qt;
+}
+
+/* ------------------------------------------------------------------------- */
+/* Philox4x32-10 (Salmon, Moraes, Dror and Shaw, "Parallel Random Numbers: As
+ * Easy as 1, 2, 3", SC 2011): ten rounds over a 4-word counter with a 2-word
+ * key. A round multiplies counter words 0 and 2 by the two Philox constants,
+ * keeps the low halves and xors the high halves with the other two counter
+ * words and the key; the key is bumped by the two Weyl constants between
+ * rounds. Used for the sampling coins, which are a pure function of the arc
+ * (counter = arc index, key = seed). */
+void oc_philox4x32_10(const uint32_t ctr[4], const uint32_t key[2], uint32_t out[4]) {
+  uint32_t c0 = ctr[0], c1 = ctr[1], c2 = ctr[2], c3 = ctr[3], k0 = key[0], k1 = key[1];
+  for (int r = 0; r < 10; r++) {
+    if (r > 0) {
+      k0 += 0x9E3779B9u;
+      k1 += 0xBB67AE85u;
+    }
+    const uint64_t p0 = (uint64_t)0xD2511F53u * c0;
+    const uint64_t p1 = (uint64_t)0xCD9E8D57u * c2;
+    const uint32_t n0 = (uint32_t)(p1 >> 32) ^ c1 ^ k0;
+    const uint32_t n1 = (uint32_t)p1;
+    const uint32_t n2 = (uint32_t)(p0 >> 32) ^ c3 ^ k1;
+    const uint32_t n3 = (uint32_t)p0;
+    c0 = n0; c1 = n1; c2 = n2; c3 = n3;
+  }
+  out[0] = c0; out[1] = c1; out[2] = c2; out[3] = c3;
+}
+
+/* The coin of arc j: a head when the first Philox output word is below thr. */
+static int coin_head(int64_t j, uint64_t seed, uint32_t thr) {
+  const uint32_t ctr[4] = {(uint32_t)j, (uint32_t)((uint64_t)j >> 32), 0u, 0u};
+  const uint32_t key[2] = {(uint32_t)seed, (uint32_t)(seed >> 32)};
+  uint32_t o[4];
+  oc_philox4x32_10(ctr, key, o);
+  return o[0] < thr;
+}
+
+/* Sample rate of Sec. 4.1, rate = mu / ((1 - r) D) with r = 1/10, as a 32-bit
+ * coin threshold floor(2^32 rate), capped at 2^32 - 1 (integer arithmetic). */
+static uint32_t coin_threshold(int64_t mu, int64_t D) {
+  const unsigned __int128 num = ((unsigned __int128)(10 * (uint64_t)mu)) << 32;
+  const unsigned __int128 q = num / (unsigned __int128)(9 * (uint64_t)D);
+  return q >= 0xFFFFFFFFu ? 0xFFFFFFFFu : (uint32_t)q;
+}
+
+/* Algorithm 4 (the framework with sampling) with the Peel, InitSampler,
+ * SetSampler and Error functions of Algorithm 5, sequentially, round by round
+ * (k = 0, 1, 2, ... with no round skipped) and subround by subround:
+ *   - InitSampler(v, k): sample mode when D r > k and D > threshold, where D
+ *     is v's exact induced degree at that moment (r = 1/10, so D > 10 k);
+ *     the sample count restarts at 0.
+ *   - Round k: the frontier is the live vertices outside sample mode with
+ *     induced degree k; then every vertex in sample mode is validated, and
+ *     one failing Error(v, k) is recounted by SetSampler (which may add it to
+ *     the frontier). Error(v, k) holds when D r > k and
+ *     cnt < rate (D - k) / 4, i.e. 18 D cnt < 5 mu (D - k).
+ *   - Peel(F, k): the frontier's arcs in frontier order, each arc once; a
+ *     neighbour in sample mode takes a head of its coin with probability rate
+ *     (the arc's Philox coin), and its mu-th head puts it in the counting bag;
+ *     any other neighbour has its induced degree decremented and joins the
+ *     next frontier when the decrement returned k + 1. The bag's vertices are
+ *     recounted (SetSampler) after the subround.
+ *   - SetSampler(v, k, F): the induced degree becomes the number of v's
+ *     neighbours whose arcs have not been traversed yet; at or below k, v
+ *     joins F; then InitSampler(v, k).
+ *   - Recovery (Sec. 4.1, "Recover from Errors"): a recount at round k of a
+ *     vertex that had fewer than k untraversed neighbours when round k began
+ *     means it missed an earlier round; the run stops and returns 1 (the
+ *     caller restarts without sampling).
+ * A vertex whose induced degree is 2^29 or more is never sampled (the GPU
+ * keeps the sample flag in the induced-degree word).
+ * stats (int64[8], may be NULL): [0] vertices sampled by the first
+ * InitSampler, [1] SetSampler recounts, [2] counting-bag insertions,
+ * [3] failed validations, [4] heads, [5] the round of a detected miss (-1),
+ * [6] the vertex of it (-1), [7] rounds.
+ * Returns 0 (core[] holds the coreness), 1 (a miss was detected; core[] is
+ * incomplete) or -3 (out of memory). */
+int oc_kcore_sampled(int64_t n, const int64_t* off, const int32_t* adj, int64_t mu, int64_t threshold,
+                     uint64_t seed, int32_t* core, int64_t* stats) {
+  int64_t st[8] = {0, 0, 0, 0, 0, -1, -1, 0};
+  if (n <= 0) {
+    if (stats) memcpy(stats, st, sizeof(st));
+    return 0;
+  }
+  if (mu < 1) mu = 1;
+  const int64_t kCap = (int64_t)1 << 29;
+  int64_t* dt = (int64_t*)malloc(sizeof(int64_t) * (size_t)n);    /* induced degree (D when sampled) */
+  int64_t* cnt = (int64_t*)calloc((size_t)n, sizeof(int64_t));    /* heads since InitSampler */
+  int64_t* done = (int64_t*)malloc(sizeof(int64_t) * (size_t)n);  /* round its arcs were traversed */
+  uint8_t* smode = (uint8_t*)calloc((size_t)n, 1);
+  uint8_t* inbag = (uint8_t*)calloc((size_t)n, 1);
+  int32_t* alive = (int32_t*)malloc(sizeof(int32_t) * (size_t)n);
+  int32_t* F = (int32_t*)malloc(sizeof(int32_t) * (size_t)n);
+  int32_t* Fn = (int32_t*)malloc(sizeof(int32_t) * (size_t)n);
+  int32_t* bag = (int32_t*)malloc(sizeof(int32_t) * (size_t)n);
+  if (!dt || !cnt || !done || !smode || !inbag || !alive || !F || !Fn || !bag) {
+    free(dt); free(cnt); free(done); free(smode); free(inbag); free(alive); free(F); free(Fn); free(bag);
+    return -3;
+  }
+  const int64_t kNever = INT64_MAX;
+  int64_t na = n;
+  for (int64_t v = 0; v < n; v++) {
+    dt[v] = off[v + 1] - off[v];
+    done[v] = kNever;
+    alive[v] = (int32_t)v;
+    core[v] = -1;
+  }
+  /* InitSampler(v, 0) for every v */
+  for (int64_t v = 0; v < n; v++) {
+    const int64_t D = dt[v];
+    if (D > 0 && D > threshold && D < kCap) {
+      smode[v] = 1;
+      cnt[v] = 0;
+      st[0]++;
+    }
+  }
+  int rc = 0;
+  int64_t k = 0;
+  while (na > 0 && rc == 0) {
+    st[7]++;
+    /* frontier of round k: live vertices outside sample mode with induced degree k */
+    int64_t nf = 0;
+    for (int64_t i = 0; i < na; i++) {
+      const int32_t v = alive[i];
+      if (!smode[v] && dt[v] == k) F[nf++] = v;
+    }
+    /* validate every vertex in sample mode; recount those that fail Error(v, k) */
+    for (int64_t i = 0; i < na && rc == 0; i++) {
+      const int32_t v = alive[i];
+      if (!smode[v]) continue;
+      const int64_t D = dt[v];
+      const int ok = D > 10 * k && 18 * D * cnt[v] < 5 * mu * (D - k);
+      if (ok) continue;
+      st[3]++;
+      /* SetSampler(v, k, F) */
+      st[1]++;
+      int64_t left = 0, at_start = 0;
+      for (int64_t j = off[v]; j < off[v + 1]; j++) {
+        const int64_t d = done[adj[j]];
+        if (d == kNever) left++;
+        if (d >= k) at_start++;
+      }
+      if (at_start < k) {
+        st[5] = k;
+        st[6] = v;
+        rc = 1;
+        break;
+      }
+      dt[v] = left;
+      smode[v] = 0;
+      if (left <= k) F[nf++] = v;
+      else if (left > 10 * k && left > threshold && left < kCap) {
+        smode[v] = 1;
+        cnt[v] = 0;
+      }
+    }
+    while (nf > 0 && rc == 0) {
+      for (int64_t i = 0; i < nf; i++) core[F[i]] = (int32_t)k;
+      /* Peel(F, k) with sampling */
+      int64_t nn = 0, nb = 0;
+      for (int64_t i = 0; i < nf; i++) {
+        const int32_t v = F[i];
+        done[v] = k;
+        for (int64_t j = off[v]; j < off[v + 1]; j++) {
+          const int32_t u = adj[j];
+          if (smode[u]) {
+            if (coin_head(j, seed, coin_threshold(mu, dt[u]))) {
+              st[4]++;
+              if (cnt[u]++ == mu - 1 && !inbag[u]) {
+                inbag[u] = 1;
+                bag[nb++] = u;
+                st[2]++;
+              }
+            }
+          } else {
+            const int64_t before = dt[u]--;
+            if (before == k + 1) Fn[nn++] = u;
+          }
+        }
+      }
+      /* SetSampler(v, k, F') for the counting bag */
+      for (int64_t i = 0; i < nb; i++) {
+        const int32_t v = bag[i];
+        inbag[v] = 0;
+        st[1]++;
+        int64_t left = 0, at_start = 0;
+        for (int64_t j = off[v]; j < off[v + 1]; j++) {
+          const int64_t d = done[adj[j]];
+          if (d == kNever) left++;
+          if (d >= k) at_start++;
+        }
+        if (at_start < k) {
+          st[5] = k;
+          st[6] = v;
+          rc = 1;
+          break;
+        }
+        dt[v] = left;
+        smode[v] = 0;
+        if (left <= k) Fn[nn++] = v;
+        else if (left > 10 * k && left > threshold && left < kCap) {
+          smode[v] = 1;
+          cnt[v] = 0;
+        }
+      }
+      int32_t* t = F; F = Fn; Fn = t;
+      nf = nn;
+    }
+    /* keep the live vertices above k (a vertex in sample mode is live) */
+    int64_t w = 0;
+    for (int64_t i = 0; i < na; i++) {
+      const int32_t v = alive[i];
+      if (smode[v] || dt[v] > k) alive[w++] = v;
+    }
+    na = w;
+    k++;
+  }
+  if (stats) memcpy(stats, st, sizeof(st));
+  free(dt); free(cnt); free(done); free(smode); free(inbag); free(alive); free(F); free(Fn); free(bag);
+  return rc;
 }

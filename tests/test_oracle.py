@@ -328,3 +328,95 @@ def test_kcore_mask_staircase_levels():
         inside = np.flatnonzero(mask)
         for v in inside:
             assert mask[adj[off[v]:off[v + 1]]].sum() >= kp
+
+
+# ------------------------------------------------ sampling (Sec. 4.1, Algs. 4-5)
+def test_philox_known_answers():
+    # Philox4x32-10 known-answer vectors published with the generator
+    # (Salmon et al., SC 2011; the Random123 known-answer tests)
+    assert oracle.philox4x32_10((0, 0, 0, 0), (0, 0)) == (0x6627E8D5, 0xE169C58D, 0xBC57AC4C, 0x9B00DBD8)
+    f = 0xFFFFFFFF
+    assert oracle.philox4x32_10((f, f, f, f), (f, f)) == (0x408F276D, 0x41C83B0E, 0xA20BC7C6, 0x6D5451FD)
+    assert oracle.philox4x32_10((0x243F6A88, 0x85A308D3, 0x13198A2E, 0x03707344), (0xA4093822, 0x299F31D0)) \
+        == (0xD16CFE09, 0x94FDCCEB, 0x5001E420, 0x24126EA1)
+
+
+def _sampling_graphs():
+    yield "star", gg.star(3000)
+    yield "complete", gg.complete(150)
+    yield "rmat", (4096, *gg.rmat_n(4096, 60_000, seed=3))
+    yield "cliques", gg.disjoint_union(gg.complete(120), gg.star(900), gg.staircase(60), gg.complete(40))
+    n = 20_000
+    s1, d1 = gg.knn2d(n, 10, seed=3)
+    s2, d2, _, _ = gg.planted_cliques(n, 6, 60, 300, seed=4)
+    yield "knn+cliques", (n, np.concatenate([s1, s2]), np.concatenate([d1, d2]))
+
+
+@pytest.mark.parametrize("name,g", list(_sampling_graphs()), ids=lambda x: x if isinstance(x, str) else "")
+def test_sampled_peel_is_exact_or_reports_a_true_miss(name, g):
+    # Values never fall below coreness (each is set when at most k untraversed
+    # neighbours remain), so the recovery check can only fire on a vertex that
+    # really missed an earlier round; without a report the result is exact
+    n, s, d = g
+    off, adj = oracle.build_csr(n, s, d)
+    want = oracle.bz(n, off, adj)
+    deg = np.diff(off)
+    oks = 0
+    for mu, thr in [(8, 10), (40, 30), (200, 50)]:
+        for seed in range(6):
+            ok, core, st = oracle.kcore_sampled(n, off, adj, mu, thr, seed)
+            assert st["sampled_at_start"] == int(np.count_nonzero(deg > thr))
+            if ok:
+                oks += 1
+                np.testing.assert_array_equal(core, want)
+                assert st["miss_round"] == -1
+            else:
+                v = st["miss_vertex"]
+                assert 0 <= v < n and want[v] < st["miss_round"]
+    assert oks > 0
+
+
+def test_sampled_peel_without_samples_is_algorithm_1():
+    n, s, d = gg.disjoint_union(gg.complete(30), gg.staircase(25), gg.grid2d(9, 7))
+    off, adj = oracle.build_csr(n, s, d)
+    ok, core, st = oracle.kcore_sampled(n, off, adj, 50, int(np.diff(off).max()), 1)
+    _, st1 = oracle.alg1(n, off, adj)
+    assert ok and st["sampled_at_start"] == 0 and st["heads"] == 0 and st["recounts"] == 0
+    np.testing.assert_array_equal(core, oracle.bz(n, off, adj))
+    assert st["rounds"] == st1["rounds"]
+
+
+def test_sampled_peel_complete_graph_never_misses():
+    # K_n: every vertex sampled; Error(v, k) fails once 10 k >= n - 1, the
+    # recount finds n - 1 untraversed neighbours, and the peel is exact
+    n, s, d = gg.complete(200)
+    off, adj = oracle.build_csr(n, s, d)
+    for seed in range(5):
+        ok, core, st = oracle.kcore_sampled(n, off, adj, 30, 10, seed)
+        assert ok and (core == n - 1).all()
+        assert st["sampled_at_start"] == n and st["failed_validations"] >= n
+
+
+def test_sampling_coin_rate_and_counting_bag():
+    # Star with L leaves, centre sampled: the leaves are peeled in round 1,
+    # giving the centre L coins of probability p = floor(2^32 mu / ((1 - r) L)) / 2^32
+    # (r = 1/10). The centre is recounted in round 1 only through the counting
+    # bag (mu heads); otherwise it misses round 1 and the recovery check fires.
+    scipy_stats = pytest.importorskip("scipy.stats")
+    L, mu = 4000, 60
+    n, s, d = gg.star(L)
+    off, adj = oracle.build_csr(n, s, d)
+    p = (10 * mu * 2**32 // (9 * L)) / 2**32
+    heads, misses, trials = [], 0, 300
+    for seed in range(trials):
+        ok, core, st = oracle.kcore_sampled(n, off, adj, mu, 100, seed)
+        heads.append(st["heads"])
+        if ok:
+            assert core[0] == 1 and (core == 1).all()
+        else:
+            misses += 1
+            assert st["miss_vertex"] == 0
+    mean, sd = L * p, np.sqrt(L * p * (1 - p))
+    assert abs(np.mean(heads) - mean) < 5 * sd / np.sqrt(trials)
+    q = scipy_stats.binom.cdf(mu - 1, L, p)  # P(fewer than mu heads)
+    assert abs(misses - trials * q) < 5 * np.sqrt(trials * q * (1 - q)) + 1
