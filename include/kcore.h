@@ -98,7 +98,25 @@ typedef enum {
                                          an item per warp and one per active vertex) counts its
                                          decrements per neighbour with reductions and then applies
                                          them walking the active list (Algorithm 2's batch update);
-                                         0 = every subround decrements with returning atomics */
+                                         0 = every subround decrements with returning atomics */,
+  /* Sampling (Sec. 4.1, Algorithms 4 and 5; mode 2, not with LEVEL_WINDOW or
+   * the k'-core query): a vertex whose induced degree D exceeds
+   * SAMPLE_THRESHOLD and 10 k is put in sample mode; a peeled neighbour then
+   * tosses a coin of probability mu / (0.9 D) (Philox4x32-10 of the arc index
+   * and SAMPLE_SEED) instead of decrementing it; mu heads, or a failed
+   * validation at a level's start, make the vertex recount its untraversed
+   * neighbours. A recount that finds the vertex missed an earlier level, or
+   * a failed final check (every v has at least core[v] neighbours of
+   * coreness >= core[v], SAMPLE_CHECK), makes the call recompute the result
+   * without sampling in the same stream (Las Vegas: the result is always
+   * exact; kcore_stats.sample_reruns says whether it happened). */
+  KCORE_OPT_SAMPLING = 17,            /* 0 (default) off, 1 on */
+  KCORE_OPT_SAMPLE_MU = 18,           /* heads per sampling period (1 .. 2^24); 0 = auto:
+                                         ceil(4 (c + 2) ln n) with c = 8 (Theorem 2) */
+  KCORE_OPT_SAMPLE_THRESHOLD = 19,    /* degree above which a vertex may be sampled; -1 = auto (8 mu) */
+  KCORE_OPT_SAMPLE_SEED = 20,         /* Philox key of the coins (default 1) */
+  KCORE_OPT_SAMPLE_CHECK = 21         /* 1 (default) runs the final check; 0 relies on the
+                                         recount test of Sec. 4.1 alone */
 } kcore_option;
 
 /* Counters of the last decomposition, or of the last CSR check (the three
@@ -117,6 +135,13 @@ typedef struct {
   int64_t batch_block;     /* batched calls: threads per CTA used */
   int64_t batch_smem_vertices; /* batched calls: largest graph kept in shared memory */
   int64_t slice_arcs;      /* arcs per work item the last decomposition used */
+  int64_t sample_vertices;  /* sampling: vertices put in sample mode by the first InitSampler */
+  int64_t sample_recounts;  /* sampling: SetSampler recounts */
+  int64_t sample_bag;       /* sampling: counting-bag insertions (mu heads reached) */
+  int64_t sample_failed_validations; /* sampling: Error(v, k) failures at level starts */
+  int64_t sample_heads;     /* sampling: coin heads */
+  int64_t sample_reruns;    /* sampling: 1 if the sampled result was recomputed without sampling */
+  int64_t sample_miss_round; /* sampling: level of a miss found by a recount, else -1 */
   int64_t invalid_check;   /* kcore_validate_csr: first failed check (1..6), 0 if the CSR is simple */
   int64_t invalid_vertex;  /* kcore_validate_csr: the vertex of that failure */
   int64_t invalid_arc;     /* kcore_validate_csr: the failing arc (index into adj); for codes 1

@@ -393,21 +393,20 @@ void oc_philox4x32_10(const uint32_t ctr[4], const uint32_t key[2], uint32_t out
   out[0] = c0; out[1] = c1; out[2] = c2; out[3] = c3;
 }
 
-/* The coin of arc j: a head when the first Philox output word is below thr. */
-static int coin_head(int64_t j, uint64_t seed, uint32_t thr) {
+/* The coin of arc j for a vertex in sample mode with induced degree D: x is
+ * the first Philox output word (uniform on 32 bits), and a head means
+ * x < floor(2^32 rate) with the sample rate of Sec. 4.1,
+ * rate = mu / ((1 - r) D), r = 1/10. In integers: x < floor(10 mu 2^32 / (9 D))
+ * holds exactly when 9 D (x + 1) <= 10 mu 2^32, i.e. when
+ * D (x + 1) <= floor(10 mu 2^32 / 9). */
+static int coin_head(int64_t j, uint64_t seed, int64_t mu, int64_t D) {
   const uint32_t ctr[4] = {(uint32_t)j, (uint32_t)((uint64_t)j >> 32), 0u, 0u};
   const uint32_t key[2] = {(uint32_t)seed, (uint32_t)(seed >> 32)};
   uint32_t o[4];
   oc_philox4x32_10(ctr, key, o);
-  return o[0] < thr;
-}
-
-/* Sample rate of Sec. 4.1, rate = mu / ((1 - r) D) with r = 1/10, as a 32-bit
- * coin threshold floor(2^32 rate), capped at 2^32 - 1 (integer arithmetic). */
-static uint32_t coin_threshold(int64_t mu, int64_t D) {
-  const unsigned __int128 num = ((unsigned __int128)(10 * (uint64_t)mu)) << 32;
-  const unsigned __int128 q = num / (unsigned __int128)(9 * (uint64_t)D);
-  return q >= 0xFFFFFFFFu ? 0xFFFFFFFFu : (uint32_t)q;
+  const unsigned __int128 lhs = (unsigned __int128)(9 * (uint64_t)D) * ((uint64_t)o[0] + 1);
+  const unsigned __int128 rhs = ((unsigned __int128)(10 * (uint64_t)mu)) << 32;
+  return lhs <= rhs;
 }
 
 /* Algorithm 4 (the framework with sampling) with the Peel, InitSampler,
@@ -531,7 +530,7 @@ int oc_kcore_sampled(int64_t n, const int64_t* off, const int32_t* adj, int64_t 
         for (int64_t j = off[v]; j < off[v + 1]; j++) {
           const int32_t u = adj[j];
           if (smode[u]) {
-            if (coin_head(j, seed, coin_threshold(mu, dt[u]))) {
+            if (coin_head(j, seed, mu, dt[u])) {
               st[4]++;
               if (cnt[u]++ == mu - 1 && !inbag[u]) {
                 inbag[u] = 1;

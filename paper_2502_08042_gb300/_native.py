@@ -99,7 +99,9 @@ class Stats(ctypes.Structure):
     _fields_ = [(name, c_i64) for name in ("rounds", "empty_rounds", "items", "local_items",
                                            "scanned", "kmax", "grid", "sync_mode", "passes",
                                            "barriers", "batch_block", "batch_smem_vertices", "slice_arcs",
-                                           "invalid_check", "invalid_vertex", "invalid_arc")]
+                                           "sample_vertices", "sample_recounts", "sample_bag",
+                                           "sample_failed_validations", "sample_heads", "sample_reruns",
+                                           "sample_miss_round", "invalid_check", "invalid_vertex", "invalid_arc")]
 
 
 class BatchTuning(ctypes.Structure):

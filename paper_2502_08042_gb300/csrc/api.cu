@@ -22,10 +22,12 @@ struct kcore_ctx {
   size_t ws_bytes = 0;
   bool ws_external = false;
   std::string err;
-  int64_t opt[17] = {0, 0, 0, -1, 2000, 1, 2048, 0, 0, 192, 64, 1024, -1, 0, 32, 0, 1};  // indexed by kcore_option
+  int64_t opt[22] = {0, 0, 0, -1, 2000, 1, 2048, 0, 0, 192, 64, 1024, -1, 0, 32, 0, 1,
+                     0, 0, -1, 1, 1};  // indexed by kcore_option
   cudaStream_t last_stream = nullptr;
   bool pending = false;
   kc::PeelCtl* last_ctl = nullptr;
+  kc::PeelCtl* last_ctl2 = nullptr;  // sampled calls: the control block of the rerun without sampling
   int* last_csr_status = nullptr;  // device status word of the last CSR build
   int* last_batch_status = nullptr;  // device status word of the last batched call
   int* last_validate_status = nullptr;  // device status words of the last CSR check
@@ -76,18 +78,22 @@ long long isqrt_ll(long long m) {
 
 struct PeelLayout {
   size_t deg, a0, a1, a2, q, rounds, ctl, trace, hcnt, touched, total;
-  long long qcap;
+  // sampling: the rerun's control block and round ring, and the sampler state
+  size_t ctl2, rounds2, scnt, stamp, racc, rst, rlist, rq, rqv;
+  long long qcap, rqcap;
   int max_rounds;
 };
+constexpr int kRecountSlice = 1024;  // arcs per recount slice
 
 // Workspace of the single-graph peel: d~[n], two active lists [n], the work
 // queue (every vertex pushes ceil(deg/slice) slices once: <= n + m/slice), the
 // per-round records (levels <= k_max+1 <= sqrt(m)+1, each followed by at most
 // one empty speculative level) and the control block. Everything below `deg`
 // is zeroed per call.
-PeelLayout peel_layout(long long n, long long m, int slice, bool offline = false) {
+PeelLayout peel_layout(long long n, long long m, int slice, bool offline = false, bool sample = false) {
   PeelLayout L{};
   L.qcap = n + (m + slice - 1) / slice + 1;
+  L.rqcap = n + (m + kRecountSlice - 1) / kRecountSlice + 1;
   long long mr = 2 * isqrt_ll(m) + 8;
   mr = std::min(mr, 2 * n + 8);
   L.max_rounds = (int)mr;
@@ -96,6 +102,13 @@ PeelLayout peel_layout(long long n, long long m, int slice, bool offline = false
   off = align_up(off + sizeof(kc::PeelCtl), 256);
   L.rounds = off;
   off = align_up(off + sizeof(kc::RoundRec) * (size_t)L.max_rounds, 256);
+  L.ctl2 = L.rounds2 = off;
+  if (sample) {
+    L.ctl2 = off;
+    off = align_up(off + sizeof(kc::PeelCtl), 256);
+    L.rounds2 = off;
+    off = align_up(off + sizeof(kc::RoundRec) * (size_t)kc::kPhaseRing, 256);
+  }
   L.deg = off;
   off = align_up(off + 4 * (size_t)n, 256);
   L.a0 = off;
@@ -116,6 +129,19 @@ PeelLayout peel_layout(long long n, long long m, int slice, bool offline = false
     L.touched = off;
     off = align_up(off + 4 * (size_t)n, 256);
   }
+  // sampling: head counts, stamps, recount accumulators and list, recount queue
+  L.scnt = L.stamp = L.racc = L.rst = L.rlist = L.rq = L.rqv = off;
+  if (sample) {
+    size_t* arrays[] = {&L.scnt, &L.stamp, &L.racc, &L.rst, &L.rlist};
+    for (size_t* f : arrays) {
+      *f = off;
+      off = align_up(off + 4 * (size_t)n, 256);
+    }
+    L.rq = off;
+    off = align_up(off + 8 * (size_t)L.rqcap, 256);
+    L.rqv = off;
+    off = align_up(off + 4 * (size_t)L.rqcap, 256);
+  }
   L.total = off;
   return L;
 }
@@ -124,6 +150,17 @@ PeelLayout peel_layout(long long n, long long m, int slice, bool offline = false
 int effective_mode(const kcore_ctx* h) {
   const int64_t m = h->opt[KCORE_OPT_SYNC_MODE];
   return m == 1 ? 1 : (m == 3 ? 3 : 2);
+}
+// Sampling runs in the bulk-synchronous mode, without the level window and
+// not for the k'-core query.
+bool sampling_on(const kcore_ctx* h, bool threshold) {
+  return h->opt[KCORE_OPT_SAMPLING] != 0 && !threshold && effective_mode(h) == 2 &&
+         h->opt[KCORE_OPT_LEVEL_WINDOW] == 0;
+}
+// mu of Theorem 2 with c = 8 unless set: ceil(4 (c + 2) ln n).
+int sample_mu(const kcore_ctx* h, long long n) {
+  if (h->opt[KCORE_OPT_SAMPLE_MU] > 0) return (int)h->opt[KCORE_OPT_SAMPLE_MU];
+  return (int)std::ceil(40.0 * std::log((double)std::max(n, 2ll)));
 }
 int effective_slice(const kcore_ctx* h) {
   if (h->opt[KCORE_OPT_SLICE_ARCS] > 0) return (int)h->opt[KCORE_OPT_SLICE_ARCS];
@@ -201,7 +238,7 @@ kcore_status kcore_destroy(kcore_handle h) {
 const char* kcore_last_error(kcore_handle h) { return h ? h->err.c_str() : "null handle"; }
 
 kcore_status kcore_set_option(kcore_handle h, kcore_option opt, int64_t value) {
-  if (!h || (int)opt < 0 || (int)opt > 16) return KCORE_ERR_INVALID;
+  if (!h || (int)opt < 0 || (int)opt > 21) return KCORE_ERR_INVALID;
   switch (opt) {
     case KCORE_OPT_BATCH_BLOCK:
       if (value != 256 && value != 512 && value != 1024)
@@ -221,6 +258,18 @@ kcore_status kcore_set_option(kcore_handle h, kcore_option opt, int64_t value) {
       break;
     case KCORE_OPT_BATCH_UPDATE:
       if (value < 0 || value > 1) return fail(h, KCORE_ERR_INVALID, "batch update must be 0 or 1");
+      break;
+    case KCORE_OPT_SAMPLING:
+    case KCORE_OPT_SAMPLE_CHECK:
+      if (value < 0 || value > 1) return fail(h, KCORE_ERR_INVALID, "sampling switches must be 0 or 1");
+      break;
+    case KCORE_OPT_SAMPLE_MU:
+      if (value < 0 || value > (1 << 24)) return fail(h, KCORE_ERR_INVALID, "sample mu in [0, 2^24]");
+      break;
+    case KCORE_OPT_SAMPLE_THRESHOLD:
+      if (value < -1 || value > INT32_MAX) return fail(h, KCORE_ERR_INVALID, "sample threshold in [-1, 2^31 - 1]");
+      break;
+    case KCORE_OPT_SAMPLE_SEED:
       break;
     case KCORE_OPT_IDLE_SLEEP_NS:
     case KCORE_OPT_POLL_SLEEP_NS:
@@ -262,7 +311,7 @@ kcore_status kcore_set_option(kcore_handle h, kcore_option opt, int64_t value) {
 }
 
 kcore_status kcore_get_option(kcore_handle h, kcore_option opt, int64_t* value) {
-  if (!h || !value || (int)opt < 0 || (int)opt > 16) return KCORE_ERR_INVALID;
+  if (!h || !value || (int)opt < 0 || (int)opt > 21) return KCORE_ERR_INVALID;
   *value = h->opt[opt];
   return KCORE_OK;
 }
@@ -270,7 +319,9 @@ kcore_status kcore_get_option(kcore_handle h, kcore_option opt, int64_t* value) 
 kcore_status kcore_workspace_size(kcore_handle h, int64_t n, int64_t m, size_t* bytes) {
   if (!h || !bytes || n < 0 || m < 0 || n > INT32_MAX - 1) return KCORE_ERR_INVALID;
   *bytes = peel_layout(n, m, effective_slice(h),
-                       effective_mode(h) == 3 || (effective_mode(h) == 2 && h->opt[KCORE_OPT_BATCH_UPDATE])).total;
+                       effective_mode(h) == 3 || (effective_mode(h) == 2 && h->opt[KCORE_OPT_BATCH_UPDATE]),
+                       sampling_on(h, false))
+               .total;
   return KCORE_OK;
 }
 
@@ -318,7 +369,8 @@ kcore_status peel_call(kcore_ctx* h, int64_t n, int64_t m, const int64_t* offset
   const int slice = h->opt[KCORE_OPT_SLICE_ARCS] > 0 ? (int)h->opt[KCORE_OPT_SLICE_ARCS] : (mode == 1 ? 512 : 64);
   const bool hybrid = mode == 2 && !threshold && h->opt[KCORE_OPT_BATCH_UPDATE] != 0 &&
                       h->opt[KCORE_OPT_LEVEL_WINDOW] == 0;
-  PeelLayout L = peel_layout(n, m, slice, mode == 3 || hybrid);
+  const bool sample = sampling_on(h, threshold);
+  PeelLayout L = peel_layout(n, m, slice, mode == 3 || hybrid, sample);
   kcore_status st = ensure_ws(h, L.total);
   if (st != KCORE_OK) return st;
   char* ws = (char*)h->ws;
@@ -380,9 +432,44 @@ kcore_status peel_call(kcore_ctx* h, int64_t n, int64_t m, const int64_t* offset
     return cuda_fail(h, e, "memset trace");
   if ((mode == 3 || hybrid) && (e = cudaMemsetAsync(a.hcnt, 0, 4 * (size_t)n, stream)) != cudaSuccess)
     return cuda_fail(h, e, "memset counts");
-  e = mode != 1 ? kc::bsp_launch(a, (int)grid, stream) : kc::peel_launch(a, (int)grid, stream);
-  if (e != cudaSuccess) return cuda_fail(h, e, "peel launch");
-  h->last_ctl = a.ctl;
+  h->last_ctl2 = nullptr;
+  if (sample) {
+    // the sampled run, its final check, and the rerun without sampling that
+    // runs only when the sampled result is not exact
+    kc::PeelArgs sa = a;
+    sa.sample = 1;
+    sa.hybrid = 0;
+    sa.window = 0;
+    sa.trace = nullptr;
+    sa.mu = sample_mu(h, n);
+    sa.sthreshold = h->opt[KCORE_OPT_SAMPLE_THRESHOLD] >= 0 ? h->opt[KCORE_OPT_SAMPLE_THRESHOLD] : 8ll * sa.mu;
+    sa.seed = (unsigned long long)h->opt[KCORE_OPT_SAMPLE_SEED];
+    sa.coin_lim = ((unsigned long long)(10ull * (unsigned long long)sa.mu) << 32) / 9ull;
+    sa.scnt = (int*)(ws + L.scnt);
+    sa.stamp = (int*)(ws + L.stamp);
+    sa.racc = (int*)(ws + L.racc);
+    sa.rst = (int*)(ws + L.rst);
+    sa.rlist = (int*)(ws + L.rlist);
+    sa.RQ = (unsigned long long*)(ws + L.rq);
+    sa.RQv = (int*)(ws + L.rqv);
+    sa.rqcap = L.rqcap;
+    sa.rslice = kRecountSlice;
+    if ((e = kc::bsp_launch(sa, (int)grid, stream)) != cudaSuccess) return cuda_fail(h, e, "sampled peel launch");
+    if (h->opt[KCORE_OPT_SAMPLE_CHECK] &&
+        (e = kc::sample_check_launch(n, m, (const long long*)offsets, adj, out, sa.racc, sa.ctl, h->sms,
+                                     stream)) != cudaSuccess)
+      return cuda_fail(h, e, "sampled result check launch");
+    a.ctl = (kc::PeelCtl*)(ws + L.ctl2);
+    a.rounds = (kc::RoundRec*)(ws + L.rounds2);
+    a.run_if = &sa.ctl->s_redo;
+    if ((e = kc::bsp_launch(a, (int)grid, stream)) != cudaSuccess) return cuda_fail(h, e, "rerun launch");
+    h->last_ctl = sa.ctl;
+    h->last_ctl2 = a.ctl;
+  } else {
+    e = mode != 1 ? kc::bsp_launch(a, (int)grid, stream) : kc::peel_launch(a, (int)grid, stream);
+    if (e != cudaSuccess) return cuda_fail(h, e, "peel launch");
+    h->last_ctl = a.ctl;
+  }
   h->last_trace = a.trace;
   h->last_max_rounds = L.max_rounds;
   h->last_grid = (int)grid;
@@ -697,6 +784,21 @@ kcore_status kcore_sync_status(kcore_handle h) {
   kc::PeelCtl c;
   e = cudaMemcpy(&c, h->last_ctl, sizeof(c), cudaMemcpyDeviceToHost);
   if (e != cudaSuccess) return cuda_fail(h, e, "read status");
+  if (h->last_ctl2) {
+    // sampled call: sampling counters from its run; the peel counters from the
+    // rerun when it ran
+    h->stats.sample_vertices = c.s_sampled;
+    h->stats.sample_recounts = c.s_recounts;
+    h->stats.sample_bag = c.s_bag;
+    h->stats.sample_failed_validations = c.s_failed;
+    h->stats.sample_heads = c.s_heads;
+    h->stats.sample_reruns = c.s_redo ? 1 : 0;
+    h->stats.sample_miss_round = c.s_miss ? c.s_miss_round : -1;
+    if (c.s_redo && c.status == 0) {
+      e = cudaMemcpy(&c, h->last_ctl2, sizeof(c), cudaMemcpyDeviceToHost);
+      if (e != cudaSuccess) return cuda_fail(h, e, "read status");
+    }
+  }
   h->stats.rounds = c.rounds;
   h->stats.empty_rounds = c.empty_rounds;
   h->stats.items = (int64_t)c.items;

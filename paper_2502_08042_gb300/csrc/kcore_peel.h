@@ -24,7 +24,9 @@ struct RoundRec {
   unsigned long long alen;   // length of the next active list
   int minkey;                // max over survivors of INT_MAX - d~ (0: no survivor)
   int pad3;
-  char pad4[104];
+  unsigned long long rcount;  // sampling: vertices appended to the recount list
+  unsigned long long rqtail;  // sampling: recount slices appended
+  char pad4[88];
 };
 
 // Round-completion broadcast: the thread whose counter update finishes round r
@@ -60,6 +62,14 @@ struct PeelCtl {
   unsigned long long tr_arcs, tr_decs;  // bulk-synchronous mode, with tracing: running sums
   unsigned long long crossed;           // k'-core query: vertices removed by a decrement
   char pad7[88];
+  // sampling (Sec. 4.1): vertices sampled by the first InitSampler, recounts,
+  // counting-bag insertions, failed validations, heads; a detected miss (the
+  // flag, its round and vertex) and a failed final check
+  long long s_sampled, s_recounts, s_bag, s_failed, s_heads;
+  int s_miss, s_miss_round;
+  long long s_miss_vertex;
+  int s_redo;  // 1: the sampled run's result is not exact (miss or failed check); rerun without sampling
+  int pad8[23];
 };
 
 // The bulk-synchronous mode uses round records 0..2 as a ring: phase p uses
@@ -108,6 +118,29 @@ struct PeelArgs {
   // heavy subrounds over a short active list use Algorithm 2's batch update
   // (counts in hcnt, zero at launch and left zero)
   int hybrid;
+  // sampling (Sec. 4.1, Algorithms 4-5; bulk-synchronous mode): a vertex in
+  // sample mode keeps -1 - D in deg[] (D: its induced degree at InitSampler).
+  // scnt: heads since InitSampler; stamp: the pass that traverses a vertex's
+  // arcs (INT_MAX before it is assigned); racc / rst: recount accumulators
+  // (zero between recounts); rlist: vertices to recount; RQ / RQv: their
+  // adjacency slices and owners (rqcap entries of rslice arcs at most).
+  int sample;
+  int mu;                  // heads that fill the counting bag
+  long long sthreshold;    // sample mode needs D > sthreshold (and D r > k)
+  unsigned long long seed; // Philox key of the coins
+  unsigned long long coin_lim;  // floor(10 mu 2^32 / 9): a coin x is a head when D (x + 1) <= coin_lim
+  int* scnt;
+  int* stamp;
+  int* racc;
+  int* rst;
+  int* rlist;
+  unsigned long long* RQ;
+  int* RQv;
+  long long rqcap;
+  int rslice;
+  // when set, the kernel runs only if *run_if != 0 (the rerun after a sampled
+  // run that was not exact)
+  const int* run_if;
 };
 
 // Per-round trace record (KCORE_OPT_TRACE): globaltimer at round start (CTA 0),
@@ -128,6 +161,13 @@ cudaError_t peel_launch(const PeelArgs& args, int grid, cudaStream_t stream);
 int bsp_max_ctas_per_sm();
 int bsp_block_size();
 cudaError_t bsp_launch(const PeelArgs& args, int grid, cudaStream_t stream);
+
+// Final check of a sampled run (sample.cu): every v must have at least
+// core[v] neighbours u with core[u] >= core[v]; a failure sets ctl->s_redo.
+// Skipped when ctl->s_redo is already set. acc: device int[n], zero on entry
+// and left zero.
+cudaError_t sample_check_launch(long long n, long long m, const long long* off, const int* adj, const int* core,
+                                int* acc, PeelCtl* ctl, int sms, cudaStream_t stream);
 
 // Simple-CSR check (validate.cu). st: device int[8] (code, pad, vertex, arc as
 // int64); zeroed by the launch, code 0 when the CSR is simple.

@@ -32,6 +32,7 @@
 // next pass instead of being walked by the warp that started it. Every wait is
 // bounded by the handle's time limit (KCORE_ERR_TIMEOUT).
 #include <climits>
+#include <type_traits>
 
 #include "kcore_device.cuh"
 #include "kcore_peel.h"
@@ -69,6 +70,16 @@ struct Shared {
   int flag;
 };
 
+// Sampling keeps the vertex of each local-queue entry beside it (a spilled
+// entry's vertex is traversed a pass later, which its stamp must say) and the
+// warps' head counts.
+struct SharedS : Shared {
+  int lqv[kWarps][kLocalQueueMax];
+  unsigned long long heads[kWarps];
+};
+template <bool kSample>
+using ShT = std::conditional_t<kSample, SharedS, Shared>;
+
 // Records the first error and makes every CTA leave at its next barrier.
 __device__ __forceinline__ void raise_status(const PeelArgs& a, int code) {
   atomicCAS(&a.ctl->status, 0, code);
@@ -77,6 +88,88 @@ __device__ __forceinline__ void raise_status(const PeelArgs& a, int code) {
 
 __device__ __forceinline__ unsigned long long make_item(long long a0, long long len) {
   return (unsigned long long)a0 | ((unsigned long long)len << kLenShift);
+}
+
+// ---- sampling (Sec. 4.1) ------------------------------------------------
+// First output word of Philox4x32-10 (Salmon et al., SC 2011) for counter
+// (j, 0) and key `seed`: the coin of arc j.
+__device__ __forceinline__ unsigned philox_coin(unsigned long long j, unsigned long long seed) {
+  unsigned c0 = (unsigned)j, c1 = (unsigned)(j >> 32), c2 = 0u, c3 = 0u;
+  unsigned k0 = (unsigned)seed, k1 = (unsigned)(seed >> 32);
+#pragma unroll
+  for (int r = 0; r < 10; r++) {
+    if (r > 0) {
+      k0 += 0x9E3779B9u;
+      k1 += 0xBB67AE85u;
+    }
+    const unsigned hi0 = __umulhi(0xD2511F53u, c0), lo0 = 0xD2511F53u * c0;
+    const unsigned hi1 = __umulhi(0xCD9E8D57u, c2), lo1 = 0xCD9E8D57u * c2;
+    const unsigned n0 = hi1 ^ c1 ^ k0, n2 = hi0 ^ c3 ^ k1;
+    c0 = n0;
+    c1 = lo1;
+    c2 = n2;
+    c3 = lo0;
+  }
+  return c0;
+}
+
+// Sample rate mu / ((1 - r) D), r = 1/10: a head is a coin x (uniform on
+// 32 bits) below floor(2^32 rate), i.e. D (x + 1) <= floor(10 mu 2^32 / 9)
+// = a.coin_lim (exact in integers).
+__device__ __forceinline__ bool coin_head(unsigned x, int D, unsigned long long lim) {
+  return (unsigned long long)D * ((unsigned long long)x + 1ull) <= lim;
+}
+
+// Error(v, k) of Algorithm 5 holds (v may stay in sample mode through level
+// k): D r > k and cnt < rate (D - k) / 4, i.e. 18 D cnt < 5 mu (D - k).
+__device__ __forceinline__ bool sample_safe(int D, int cnt, int k, int mu) {
+  return (long long)D > 10ll * k && 18ll * D * cnt < 5ll * mu * ((long long)D - k);
+}
+
+// The first level above which sample_safe fails for this (D, cnt): an empty
+// level skipped by the scan's minimum must not pass it.
+__device__ __forceinline__ int sample_key(int D, int cnt, int mu) {
+  const long long k1 = ((long long)D + 9) / 10;
+  long long k2 = (long long)D - (18ll * D * cnt) / (5ll * mu);
+  if (k2 < 0) k2 = 0;
+  return (int)(k1 < k2 ? k1 : k2);
+}
+
+// Appends the flagged lanes' vertices to the recount list and their adjacency
+// lists, cut in slices of a.rslice arcs, to the recount queue (counts in
+// R->rcount and R->rqtail). Warp-collective.
+__device__ void append_recount(const PeelArgs& a, RoundRec* R, bool flag, int v, int lane) {
+  const unsigned fm = __ballot_sync(kFull, flag);
+  if (!fm) return;
+  long long e0 = 0, e1 = 0;
+  int nsl = 0;
+  if (flag) {
+    e0 = a.off[v];
+    e1 = a.off[v + 1];
+    nsl = (int)((e1 - e0 + a.rslice - 1) / a.rslice);
+  }
+  unsigned long long vb = 0;
+  if (lane == 0) vb = atomicAdd(&R->rcount, (unsigned long long)__popc(fm));
+  vb = __shfl_sync(kFull, vb, 0);
+  const unsigned long long pv = vb + __popc(fm & lanemask_lt());
+  if (flag) {
+    if (pv < (unsigned long long)a.n) a.rlist[pv] = v;
+    else raise_status(a, ST_CAPACITY);
+  }
+  const int incl = warp_incl_scan(nsl, lane);
+  const int tot = __shfl_sync(kFull, incl, 31);
+  unsigned long long qb = 0;
+  if (lane == 31 && tot) qb = atomicAdd(&R->rqtail, (unsigned long long)tot);
+  qb = __shfl_sync(kFull, qb, 31);
+  if (qb + (unsigned long long)tot > (unsigned long long)a.rqcap) {
+    if (lane == 0 && tot) raise_status(a, ST_CAPACITY);
+    return;
+  }
+  unsigned long long p = qb + (unsigned long long)(incl - nsl);
+  for (long long s0 = e0; s0 < e1; s0 += a.rslice, p++) {
+    a.RQ[p] = make_item(s0, min((long long)a.rslice, e1 - s0));
+    a.RQv[p] = v;
+  }
 }
 
 // Grid barrier on one word: the arrivals (release adds) and the abort bit.
@@ -154,10 +247,17 @@ __device__ __forceinline__ int block_excl_scan(Shared& sh, int x, int* total) {
 // then their d~: kTile independent loads per thread each), its frontier
 // vertices are staged in shared memory and expanded into slices in a second
 // step, so the offsets of only those vertices are read.
+//
+// With sampling (kSample): the first scan runs InitSampler(v, 0) on every
+// vertex (and clears its sampling state); a later scan validates every vertex
+// in sample mode at level take_at: it is kept, and either contributes the
+// first level its validation could fail at to the minimum, or, failing
+// Error(v, k), goes to the recount list. Taken vertices get stamp stamp_val.
+template <bool kSample = false>
 __device__ ScanOut scan_range(const PeelArgs& a, Shared& sh, RoundRec* R, unsigned long long qbase,
                               const int* Ain, int* Aout, long long lo, long long hi, int keep_above,
                               int take_at, bool take_le = false, int take_val = -1, int keep_val = -1,
-                              int* Aover = nullptr, int over_from = INT_MAX) {
+                              int* Aover = nullptr, int over_from = INT_MAX, int stamp_val = 0) {
   // Aover: kept entries with d~ >= over_from go there instead of Aout (the
   // overflow list of a window rebuild; count in R->head)
   // take_le: take every entry with d~ <= take_at (k'-core query); take_val /
@@ -167,10 +267,11 @@ __device__ ScanOut scan_range(const PeelArgs& a, Shared& sh, RoundRec* R, unsign
   const int tid = threadIdx.x;
   unsigned long long found = 0;  // staged frontier vertices (block-uniform)
   int direct = 0;                // frontier vertices without arcs (this thread)
+  int nsampled = 0;              // first scan with sampling: vertices put in sample mode
   int dmin = INT_MAX;
   for (long long tile = lo; tile < hi; tile += (long long)kBlock * kTile) {
     int v[kTile];
-    unsigned keep = 0, take = 0, over = 0;
+    unsigned keep = 0, take = 0, over = 0, rec = 0;
 #pragma unroll
     for (int q = 0; q < kTile; q++) {
       const long long i = tile + (long long)q * kBlock + tid;
@@ -201,8 +302,30 @@ __device__ ScanOut scan_range(const PeelArgs& a, Shared& sh, RoundRec* R, unsign
           v[q] = -1;
           continue;
         }
+        if constexpr (kSample) {
+          a.stamp[x] = INT_MAX;
+          a.scnt[x] = 0;
+          a.racc[x] = 0;
+          a.rst[x] = 0;
+          if (d > 0 && (long long)d > a.sthreshold) {  // InitSampler(v, 0)
+            a.deg[x] = -1 - d;
+            nsampled++;
+            keep |= 1u << q;
+            dmin = min(dmin, sample_key(d, 0, a.mu));
+            continue;
+          }
+        }
       } else {
         d = __ldcg(a.deg + x);
+        if constexpr (kSample) {
+          if (d < 0) {  // in sample mode: validate at level take_at
+            const int D = -1 - d, cnt = __ldcg(a.scnt + x);
+            keep |= 1u << q;
+            if (sample_safe(D, cnt, take_at, a.mu)) dmin = min(dmin, sample_key(D, cnt, a.mu));
+            else rec |= 1u << q;
+            continue;
+          }
+        }
       }
       if (d > keep_above) {
         if (d >= over_from) over |= 1u << q;
@@ -258,6 +381,7 @@ __device__ ScanOut scan_range(const PeelArgs& a, Shared& sh, RoundRec* R, unsign
           e0[k] = a.off[x];
           e1[k] = a.off[x + 1];
           a.core[x] = take_val;
+          if constexpr (kSample) a.stamp[x] = stamp_val;
         }
       }
 #pragma unroll
@@ -282,8 +406,18 @@ __device__ ScanOut scan_range(const PeelArgs& a, Shared& sh, RoundRec* R, unsign
       }
       __syncthreads();
     }
+    if constexpr (kSample) {
+      // vertices that failed validation: recount before the level's passes
+      const int ln = tid & 31;
+#pragma unroll
+      for (int q = 0; q < kTile; q++) append_recount(a, R, (rec >> q) & 1u, v[q], ln);
+    }
   }
   const int lane = tid & 31, warp = tid >> 5;
+  if constexpr (kSample) {
+    const int sw = warp_sum(nsampled);
+    if (lane == 0 && sw) atomicAdd((unsigned long long*)&a.ctl->s_sampled, (unsigned long long)sw);
+  }
   const int mw = warp_min(dmin);
   const int dw = warp_sum(direct);
   if (lane == 0) {
@@ -310,6 +444,7 @@ struct PassCtx {
   int win_hi;               // level window's end (a decrement returning it appends the vertex), or -1
   int* near;                // the active list, appended from near_base on (count in R->found)
   unsigned long long near_base;
+  int pass;                 // sampling: index of the running pass (stamps)
 };
 
 // Appends `cnt` items per lane (lane-owned arc ranges [e0, e1) cut in
@@ -333,8 +468,9 @@ __device__ __forceinline__ void append_ranges(const PeelArgs& a, const PassCtx& 
 // The vertices u of the lanes with `flag` crossed to the current level (their
 // coreness is set): one-slice lists go to the warp's local queue while it has
 // room, the rest go to the queue as slices for the next pass.
-__device__ __forceinline__ void push_crossed(const PeelArgs& a, Shared& sh, const PassCtx& pc, bool flag, int u,
-                                             int warp, int lane) {
+template <bool kSample = false>
+__device__ __forceinline__ void push_crossed(const PeelArgs& a, ShT<kSample>& sh, const PassCtx& pc, bool flag,
+                                             int u, int warp, int lane) {
   long long e0 = 0, e1 = 0;
   int nsl = 0;
   if (flag) {
@@ -351,6 +487,11 @@ __device__ __forceinline__ void push_crossed(const PeelArgs& a, Shared& sh, cons
   const int rank = __popc(om & lanemask_lt());
   const bool local = one && rank < room;
   if (local) sh.lq[warp][lqn + rank] = make_item(e0, e1 - e0);
+  if constexpr (kSample) {
+    // a local entry is traversed in this pass, a queued one in the next
+    if (local) sh.lqv[warp][lqn + rank] = u;
+    if (flag) a.stamp[u] = local ? pc.pass : pc.pass + 1;
+  }
   __syncwarp();
   if (lane == 0) sh.lqn[warp] = lqn + min(__popc(om), room);
   __syncwarp();
@@ -358,9 +499,12 @@ __device__ __forceinline__ void push_crossed(const PeelArgs& a, Shared& sh, cons
 }
 
 // Arcs of the items held by lanes < c, spread evenly over the warp.
-template <bool kWin>
-__device__ void process_items(const PeelArgs& a, Shared& sh, const PassCtx& pc, unsigned long long item, int c,
-                              int warp, int lane) {
+// With sampling (kSample), d~ is always read first: a neighbour in sample
+// mode (d~ < 0) is not decremented but tosses the arc's coin, and its mu-th
+// head puts it in the counting bag (the recount list of the next recount).
+template <bool kWin, bool kSample = false>
+__device__ void process_items(const PeelArgs& a, ShT<kSample>& sh, const PassCtx& pc, unsigned long long item,
+                              int c, int warp, int lane) {
   const int t = pc.t;
   const long long a0 = lane < c ? (long long)(item & kArcMask) : 0;
   const int len = lane < c ? (int)(item >> kLenShift) : 0;
@@ -371,6 +515,7 @@ __device__ void process_items(const PeelArgs& a, Shared& sh, const PassCtx& pc, 
   __syncwarp();
   const int* excl = sh.excl[warp];
   int ndec = 0;
+  unsigned nheads = 0;
   for (int base = 0; base < total; base += kWarp * kIlp) {
     int u[kIlp];
     int j = base + lane;
@@ -381,6 +526,7 @@ __device__ void process_items(const PeelArgs& a, Shared& sh, const PassCtx& pc, 
       else hi = mid;
     }
     int idx = lo > 0 ? lo - 1 : 0;
+    const int idx0 = idx;
 #pragma unroll
     for (int q = 0; q < kIlp; q++, j += kWarp) {
       u[q] = -1;
@@ -400,14 +546,30 @@ __device__ void process_items(const PeelArgs& a, Shared& sh, const PassCtx& pc, 
     // is safe, as a neighbour at or below k never returns k + 1 and its d~ is
     // not read again.
     int dq[kIlp];
-    if (pc.precheck && total > kWarp * kIlp) {
+    if (kSample || (pc.precheck && total > kWarp * kIlp)) {
 #pragma unroll
       for (int q = 0; q < kIlp; q++) dq[q] = u[q] >= 0 ? __ldcg(a.deg + u[q]) : INT_MIN;
     } else {
 #pragma unroll
       for (int q = 0; q < kIlp; q++) dq[q] = u[q] >= 0 ? INT_MAX : INT_MIN;
     }
-    unsigned cross = 0, enter = 0;
+    unsigned cross = 0, enter = 0, bag = 0;
+    if constexpr (kSample) {
+      int ix = idx0;
+#pragma unroll
+      for (int q = 0; q < kIlp; q++)
+        if (u[q] >= 0 && dq[q] < 0) {
+          // sample mode: one coin of probability mu / ((1 - r) D) per arc,
+          // drawn from the arc's index
+          const int jq = base + lane + q * kWarp;
+          while (ix + 1 < c && excl[ix + 1] <= jq) ix++;
+          const long long arc = sh.a0[warp][ix] + (jq - excl[ix]);
+          if (coin_head(philox_coin((unsigned long long)arc, a.seed), -1 - dq[q], a.coin_lim)) {
+            nheads++;
+            if (atomicAdd(a.scnt + u[q], 1) == a.mu - 1) bag |= 1u << q;
+          }
+        }
+    }
 #pragma unroll
     for (int q = 0; q < kIlp; q++)
       if (dq[q] > t) {
@@ -434,12 +596,18 @@ __device__ void process_items(const PeelArgs& a, Shared& sh, const PassCtx& pc, 
         }
       }
     }
+    if constexpr (kSample) {
+      if (__any_sync(kFull, bag != 0)) {
+#pragma unroll
+        for (int q = 0; q < kIlp; q++) append_recount(a, pc.R, (bag >> q) & 1u, u[q], lane);
+      }
+    }
     if (__any_sync(kFull, cross != 0)) {
 #pragma unroll
       for (int q = 0; q < kIlp; q++) {
         const bool f = (cross >> q) & 1u;
         if (f) a.core[u[q]] = pc.val;
-        if (__any_sync(kFull, f)) push_crossed(a, sh, pc, f, u[q], warp, lane);
+        if (__any_sync(kFull, f)) push_crossed<kSample>(a, sh, pc, f, u[q], warp, lane);
       }
       if (a.threshold) {
         const int nc = warp_sum(__popc(cross));
@@ -454,13 +622,19 @@ __device__ void process_items(const PeelArgs& a, Shared& sh, const PassCtx& pc, 
       sh.tr_decs[warp] += ndec;
     }
   }
+  if constexpr (kSample) {
+    if (__any_sync(kFull, nheads != 0)) {
+      nheads = warp_sum(nheads);
+      if (lane == 0) sh.heads[warp] += nheads;
+    }
+  }
   __syncwarp();
 }
 
 // Runs up to `budget` batches from the warp's local queue (vertices that
 // crossed during this pass), then moves what is left to the queue.
-template <bool kWin>
-__device__ void drain_local(const PeelArgs& a, Shared& sh, const PassCtx& pc, int warp, int lane,
+template <bool kWin, bool kSample = false>
+__device__ void drain_local(const PeelArgs& a, ShT<kSample>& sh, const PassCtx& pc, int warp, int lane,
                             long long& local_items, unsigned& local_batches) {
   for (int b = 0;; b++) {
     const int lqn = sh.lqn[warp];
@@ -477,6 +651,9 @@ __device__ void drain_local(const PeelArgs& a, Shared& sh, const PassCtx& pc, in
       } else {
         for (int i = lane; i < lqn; i += kWarp) a.Q[base + i] = sh.lq[warp][i];
       }
+      if constexpr (kSample) {
+        for (int i = lane; i < lqn; i += kWarp) a.stamp[sh.lqv[warp][i]] = pc.pass + 1;
+      }
       __syncwarp();
       return;
     }
@@ -485,7 +662,7 @@ __device__ void drain_local(const PeelArgs& a, Shared& sh, const PassCtx& pc, in
     __syncwarp();
     if (lane == 0) sh.lqn[warp] = lqn - c;
     __syncwarp();
-    process_items<kWin>(a, sh, pc, item, c, warp, lane);
+    process_items<kWin, kSample>(a, sh, pc, item, c, warp, lane);
     local_items += c;
     if (lane == 0 && ((++local_batches) & 63) == 0) atomicAdd(&a.ctl->progress, 1ull);
   }
@@ -495,8 +672,8 @@ __device__ void drain_local(const PeelArgs& a, Shared& sh, const PassCtx& pc, in
 // its own contiguous share (len / warps items, one more for the first
 // len % warps warps) in chunks of up to 32 items, so a pass has no claim
 // traffic and ends for a warp as soon as its share and local queue are done.
-template <bool kWin>
-__device__ void run_pass(const PeelArgs& a, Shared& sh, const PassCtx& pc, unsigned long long qb,
+template <bool kWin, bool kSample = false>
+__device__ void run_pass(const PeelArgs& a, ShT<kSample>& sh, const PassCtx& pc, unsigned long long qb,
                          unsigned long long qe, long long& items, long long& local_items,
                          unsigned& local_batches) {
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
@@ -508,9 +685,9 @@ __device__ void run_pass(const PeelArgs& a, Shared& sh, const PassCtx& pc, unsig
   for (unsigned long long pos = b; pos < e; pos += kTake) {
     const int c = (int)min((unsigned long long)kTake, e - pos);
     const unsigned long long item = lane < c ? __ldcg(a.Q + pos + lane) : 0;
-    process_items<kWin>(a, sh, pc, item, c, warp, lane);
+    process_items<kWin, kSample>(a, sh, pc, item, c, warp, lane);
     items += c;
-    drain_local<kWin>(a, sh, pc, warp, lane, local_items, local_batches);
+    drain_local<kWin, kSample>(a, sh, pc, warp, lane, local_items, local_batches);
   }
 }
 
@@ -639,17 +816,120 @@ __device__ void run_apply(const PeelArgs& a, const PassCtx& pc, const int* list,
   }
 }
 
-// Instantiations: kOffline (Algorithm 2's subrounds) and kWindow (the level
-// window), each compiled apart so the default kernel carries neither.
-template <bool kOffline, bool kWindow, bool kHybrid>
+// ---- sampling recounts (SetSampler of Algorithm 5, two phases) ------------
+// Counting phase: the recount queue's slices are split into per-warp shares;
+// a warp counts the arcs of its slice whose target is not yet traversed
+// (stamp >= done_passes: no completed pass traversed it) and those not
+// traversed before the level began (stamp >= level_pass), and adds both to
+// the slice owner's accumulators.
+__device__ void run_recount_count(const PeelArgs& a, unsigned long long nq, long long done_passes,
+                                  long long level_pass) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const unsigned long long gw = (unsigned long long)blockIdx.x * kWarps + warp;
+  const unsigned long long nw = (unsigned long long)gridDim.x * kWarps;
+  for (unsigned long long i = gw; i < nq; i += nw) {
+    const unsigned long long item = __ldcg(a.RQ + i);
+    const int v = __ldcg(a.RQv + i);
+    const long long a0 = (long long)(item & kArcMask);
+    const int len = (int)(item >> kLenShift);
+    int left = 0, at = 0;
+    for (int j0 = 0; j0 < len; j0 += kWarp * 4) {
+      int st[4];
+#pragma unroll
+      for (int q = 0; q < 4; q++) {
+        const int j = j0 + q * kWarp + lane;
+        st[q] = INT_MIN;
+        if (j < len) {
+          const long long arc = a0 + j;
+          const int u = arc < a.m ? ld_stream_s32(a.adj + arc) : -1;
+          if ((unsigned)u < (unsigned)a.n) st[q] = __ldcg(a.stamp + u);
+          else raise_status(a, ST_NOT_SIMPLE);
+        }
+      }
+#pragma unroll
+      for (int q = 0; q < 4; q++) {
+        left += st[q] >= done_passes ? 1 : 0;
+        at += st[q] >= level_pass ? 1 : 0;
+      }
+    }
+    left = warp_sum(left);
+    at = warp_sum(at);
+    if (lane == 0) {
+      if (left) atomicAdd(a.racc + v, left);
+      if (at) atomicAdd(a.rst + v, at);
+    }
+  }
+}
+
+// Apply phase: each recounted vertex v (one thread) takes its untraversed
+// count as d~. A vertex with fewer than k neighbours untraversed when level k
+// began missed an earlier level: the run is marked for a rerun without
+// sampling (Sec. 4.1, "Recover from Errors"). Otherwise, at or below k, v
+// gets coreness k and joins the next pass (stamp next_pass, slices appended
+// after pc.qbase, count in pc.R->found); above it, InitSampler(v, k) puts v
+// back in sample mode or leaves its exact d~. Accumulators are cleared. The
+// least next key of the vertices kept goes to pc.R->minkey.
+__device__ void run_recount_apply(const PeelArgs& a, const PassCtx& pc, unsigned long long nr, int k,
+                                  int next_pass) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const unsigned long long gw = (unsigned long long)blockIdx.x * kWarps + warp;
+  const unsigned long long nw = (unsigned long long)gridDim.x * kWarps;
+  int kmin = INT_MAX;
+  for (unsigned long long base = gw * kWarp; base < nr; base += nw * kWarp) {
+    const unsigned long long i = base + lane;
+    bool join = false;
+    long long e0 = 0, e1 = 0;
+    if (i < nr) {
+      const int v = __ldcg(a.rlist + i);
+      const int left = __ldcg(a.racc + v), at = __ldcg(a.rst + v);
+      a.racc[v] = 0;
+      a.rst[v] = 0;
+      if (at < k) {
+        if (atomicCAS(&a.ctl->s_miss, 0, 1) == 0) {
+          a.ctl->s_miss_round = k;
+          a.ctl->s_miss_vertex = v;
+        }
+        a.ctl->s_redo = 1;
+      } else if (left <= k) {
+        a.core[v] = pc.val;
+        a.deg[v] = left;
+        a.stamp[v] = next_pass;
+        join = true;
+        e0 = a.off[v];
+        e1 = a.off[v + 1];
+      } else if ((long long)left > 10ll * k && (long long)left > a.sthreshold) {
+        a.deg[v] = -1 - left;  // InitSampler(v, k): sample mode again
+        a.scnt[v] = 0;
+        kmin = min(kmin, sample_key(left, 0, a.mu));
+      } else {
+        a.deg[v] = left;
+        kmin = min(kmin, left);
+      }
+    }
+    const unsigned jm = __ballot_sync(kFull, join);
+    if (jm && lane == 0) atomicAdd(&pc.R->found, (unsigned long long)__popc(jm));
+    const int nsl = join ? (int)((e1 - e0 + a.slice - 1) / a.slice) : 0;
+    append_ranges(a, pc, nsl, e0, e1, lane);
+  }
+  kmin = warp_min(kmin);
+  if (lane == 0 && kmin != INT_MAX) atomicMax(&pc.R->minkey, INT_MAX - kmin);
+}
+
+// Instantiations: kOffline (Algorithm 2's subrounds), kWindow (the level
+// window), kHybrid (batch update of heavy subrounds) and kSample (sampling),
+// each compiled apart so the default kernel carries none of the others.
+template <bool kOffline, bool kWindow, bool kHybrid, bool kSample>
 __global__ void __launch_bounds__(kBlock, 2) peel_bsp(PeelArgs a) {
-  __shared__ Shared sh;
+  __shared__ ShT<kSample> sh;
+  // a rerun that is not needed ends at once (every CTA reads the same flag)
+  if (a.run_if && ld_relaxed_s32(a.run_if) == 0) return;
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   const bool lead = blockIdx.x == 0 && tid == 0;
   if (lane == 0) {
     sh.lqn[warp] = 0;
     sh.tr_arcs[warp] = sh.tr_decs[warp] = 0;
     sh.ncross[warp] = 0;
+    if constexpr (kSample) sh.heads[warp] = 0;
   }
   unsigned long long gen = 0;
   long long phase = 0;  // RoundRec (phase % 3) belongs to phase `phase`
@@ -664,6 +944,10 @@ __global__ void __launch_bounds__(kBlock, 2) peel_bsp(PeelArgs a) {
         R->minkey = 0;
         R->tail = 0;
         R->head = 0;
+        if constexpr (kSample) {
+          R->rcount = 0;
+          R->rqtail = 0;
+        }
       }
     }
   };
@@ -692,6 +976,7 @@ __global__ void __launch_bounds__(kBlock, 2) peel_bsp(PeelArgs a) {
   unsigned local_batches = 0;
   unsigned long long qend = 0;  // items appended by all completed phases
   bool was_rebuild = false;
+  if constexpr (!kSample) {
   for (;;) {
     // ---- scan: keep d~ > tp+1, take d~ == tp+1 (a k'-core query: one level,
     // kprime - 1, taking every d~ below kprime and marking the rest 1)
@@ -881,6 +1166,102 @@ __global__ void __launch_bounds__(kBlock, 2) peel_bsp(PeelArgs a) {
     }
     if (!ok || (la == 0 && lover == 0 && near_extra == 0)) break;
   }
+  } else {
+    // ---- Algorithm 4 with the sampling Peel of Algorithm 5. A level is a
+    // scan at k = previous level + 1 that also validates the vertices in
+    // sample mode (those failing Error(v, k) are recounted before the first
+    // pass), then passes as above in which a neighbour in sample mode tosses
+    // a coin instead of being decremented; after a pass that filled counting
+    // bags, those vertices are recounted. A recount is two phases (count,
+    // apply), each closed by the grid barrier. A level that finds no vertex
+    // moves to the least next key of the kept vertices: their least d~, or
+    // for a vertex in sample mode the first level its validation could fail
+    // at. A recount that finds a missed level ends the run (the result is
+    // then recomputed without sampling).
+    for (;;) {
+      const int tk = tp + 1;
+      reset_next();
+      RoundRec* R = a.rounds + (phase % kPhaseRing);
+      int* Aout = free_list(Acur, nullptr);
+      const long long lin = la;
+      const long long nscan = nscan_of(lin);
+      if (blockIdx.x < nscan) {
+        const long long lo = lin * blockIdx.x / nscan, hi = lin * (blockIdx.x + 1) / nscan;
+        const ScanOut o = scan_range<true>(a, sh, R, qend, Acur, Aout, lo, hi, tk, tk, false, -1, -1, nullptr,
+                                           INT_MAX, (int)passes);
+        if (tid == 0) {
+          if (o.found) atomicAdd(&R->found, o.found);
+          if (o.dmin != INT_MAX) atomicMax(&R->minkey, INT_MAX - o.dmin);
+        }
+      }
+      if (!grid_barrier(a, sh, gen)) break;
+      phase++;
+      scanned += lin;
+      unsigned long long nfound = ld_relaxed_u64(&R->found);
+      la = (long long)ld_relaxed_u64(&R->alen);
+      const int mk = ld_relaxed_s32(&R->minkey);
+      int kmin = mk ? INT_MAX - mk : INT_MAX;
+      unsigned long long qb = qend;
+      qend += ld_relaxed_u64(&R->tail);
+      const unsigned long long nr = ld_relaxed_u64(&R->rcount), nrq = ld_relaxed_u64(&R->rqtail);
+      Acur = Aout;
+      if (lead && nr) a.ctl->s_failed += (long long)nr;
+      const long long level_pass = passes;
+      bool ok = true, miss = false;
+      auto recount = [&](unsigned long long nrv, unsigned long long nrqv) {
+        // an append past either bound raised a status, which ended the phase's
+        // barrier, so the counts are within them here
+        nrv = min(nrv, (unsigned long long)a.n);
+        nrqv = min(nrqv, (unsigned long long)a.rqcap);
+        reset_next();
+        run_recount_count(a, nrqv, passes, level_pass);
+        if (!(ok = grid_barrier(a, sh, gen))) return;
+        phase++;
+        reset_next();
+        RoundRec* P = a.rounds + (phase % kPhaseRing);
+        const PassCtx pc{P, qend, tk, tk, false, -1, nullptr, 0, (int)passes};
+        run_recount_apply(a, pc, nrv, tk, (int)passes);
+        if (!(ok = grid_barrier(a, sh, gen))) return;
+        phase++;
+        nfound += ld_relaxed_u64(&P->found);
+        qend += ld_relaxed_u64(&P->tail);
+        const int mk2 = ld_relaxed_s32(&P->minkey);
+        if (mk2) kmin = min(kmin, INT_MAX - mk2);
+        if (lead) a.ctl->s_recounts += (long long)nrv;
+        miss = ld_relaxed_s32(&a.ctl->s_miss) != 0;
+      };
+      if (nr) recount(nr, nrq);
+      if (!ok || miss) break;
+      if (nfound == 0) {
+        if (la == 0) break;  // nothing left
+        empty++;
+        tp = kmin == INT_MAX ? tk : kmin - 1;
+        continue;
+      }
+      kmax = tk;
+      tp = tk;
+      levels++;
+      while (qend > qb) {
+        reset_next();
+        RoundRec* P = a.rounds + (phase % kPhaseRing);
+        const PassCtx pc{P, qend, tk, tk, true, -1, nullptr, 0, (int)passes};
+        run_pass<false, true>(a, sh, pc, qb, qend, items, local_items, local_batches);
+        if (!(ok = grid_barrier(a, sh, gen))) break;
+        phase++;
+        passes++;
+        qb = qend;
+        qend += ld_relaxed_u64(&P->tail);
+        const unsigned long long br = ld_relaxed_u64(&P->rcount), bq = ld_relaxed_u64(&P->rqtail);
+        if (br) {
+          if (lead) a.ctl->s_bag += (long long)br;
+          recount(br, bq);
+          if (!ok || miss) break;
+        }
+      }
+      if (!ok || miss || la == 0) break;
+    }
+    if (lane == 0 && sh.heads[warp]) atomicAdd((unsigned long long*)&a.ctl->s_heads, sh.heads[warp]);
+  }
   if (lane == 0) {
     if (items) atomicAdd(&a.ctl->items, (unsigned long long)items);
     if (local_items) atomicAdd(&a.ctl->local_items, (unsigned long long)local_items);
@@ -899,8 +1280,11 @@ __global__ void __launch_bounds__(kBlock, 2) peel_bsp(PeelArgs a) {
 }  // namespace
 
 int bsp_max_ctas_per_sm() {
-  const void* fns[] = {(const void*)peel_bsp<false, false, false>, (const void*)peel_bsp<true, false, false>,
-                       (const void*)peel_bsp<false, true, false>, (const void*)peel_bsp<false, false, true>};
+  const void* fns[] = {(const void*)peel_bsp<false, false, false, false>,
+                       (const void*)peel_bsp<true, false, false, false>,
+                       (const void*)peel_bsp<false, true, false, false>,
+                       (const void*)peel_bsp<false, false, true, false>,
+                       (const void*)peel_bsp<false, false, false, true>};
   int best = 1 << 30;
   for (const void* f : fns) {
     int nb = 0;
@@ -915,10 +1299,11 @@ int bsp_block_size() { return kBlock; }
 cudaError_t bsp_launch(const PeelArgs& args, int grid, cudaStream_t stream) {
   PeelArgs a = args;
   void* params[] = {&a};
-  const void* fn = a.offline      ? (const void*)peel_bsp<true, false, false>
-                   : a.window > 0 ? (const void*)peel_bsp<false, true, false>
-                   : a.hybrid     ? (const void*)peel_bsp<false, false, true>
-                                  : (const void*)peel_bsp<false, false, false>;
+  const void* fn = a.sample       ? (const void*)peel_bsp<false, false, false, true>
+                   : a.offline    ? (const void*)peel_bsp<true, false, false, false>
+                   : a.window > 0 ? (const void*)peel_bsp<false, true, false, false>
+                   : a.hybrid     ? (const void*)peel_bsp<false, false, true, false>
+                                  : (const void*)peel_bsp<false, false, false, false>;
   return cudaLaunchCooperativeKernel(fn, dim3(grid), dim3(kBlock), params, 0, stream);
 }
 
