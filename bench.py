@@ -362,7 +362,13 @@ def run_gpu(args):
     w = WORKLOADS[args.workload]
     n, s, d = make_edges(w)
     E = len(s)
-    k = KCore(local, sync_mode=args.sync_mode)
+    variant = {}
+    if args.sampling:
+        variant.update(sampling=1, sample_mu=args.sample_mu, sample_threshold=args.sample_threshold,
+                       sample_check=0 if args.no_sample_check else 1)
+    if args.warp_combine:
+        variant.update(warp_combine=1)
+    k = KCore(local, sync_mode=args.sync_mode, **variant)
     S = torch.from_numpy(s).to(dev)
     D = torch.from_numpy(d).to(dev)
     del s, d
@@ -442,7 +448,7 @@ def run_gpu(args):
     traffic = None
     # recorded traffic belongs to the default schedule of its kernel
     tp = os.path.join(ROOT, "profiles", f"{kname}_{args.workload}_traffic.json")
-    if st["sync_mode"] == 3:
+    if st["sync_mode"] == 3 or variant:
         tp = ""
     if os.path.exists(tp):
         with open(tp) as f:
@@ -462,6 +468,12 @@ def run_gpu(args):
             "rounds": st["rounds"], "empty_rounds": st["empty_rounds"], "grid": st["grid"],
             "sync_mode": st["sync_mode"], "slice_arcs": st["slice_arcs"], "passes": st["passes"],
             "barriers": st["barriers"],
+            **({"sampling": {key: st[key] for key in ("sample_vertices", "sample_recounts", "sample_bag",
+                                                       "sample_failed_validations", "sample_heads",
+                                                       "sample_reruns")},
+                "sample_mu": args.sample_mu, "sample_threshold": args.sample_threshold,
+                "sample_check": not args.no_sample_check} if args.sampling else {}),
+            **({"warp_combine": True} if args.warp_combine else {}),
             "l2": "inputs larger than L2 and a 258 MB buffer written between timed steps",
             "csr_build_ms": min(csr_ms), "parallelism": "replicas" if ws > 1 else "single GPU",
             "wall_s": wall,
@@ -470,7 +482,10 @@ def run_gpu(args):
                      "frac": achieved / peak, "traffic": traffic, "peak_kind": peak_kind,
                      "algorithmic_bytes": bmin, "kernel": kname},
         "e2e": e2e,
-        "gpu_launches": args.steps,
+        # a sampled step is the sampled peel, the two check kernels and the
+        # rerun kernel (which returns at once when not needed)
+        "gpu_launches": args.steps * (4 if args.sampling and not args.no_sample_check
+                                      else 2 if args.sampling else 1),
         "cpu_baseline": cpu,
     }
     clocks = clk.summary()
@@ -783,6 +798,13 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
     ap.add_argument("--workload", default="rmat24", choices=sorted(WORKLOADS))
+    ap.add_argument("--sampling", action="store_true",
+                    help="single-graph workloads: the sampled peel of Algorithms 4-5 (mode 2)")
+    ap.add_argument("--sample-mu", type=int, default=0, help="heads per sampling period (0 = auto)")
+    ap.add_argument("--sample-threshold", type=int, default=-1, help="sampling degree threshold (-1 = auto)")
+    ap.add_argument("--no-sample-check", action="store_true", help="skip the final check of a sampled run")
+    ap.add_argument("--warp-combine", action="store_true",
+                    help="single-graph workloads: warp-aggregated decrements (mode 2)")
     ap.add_argument("--sync-mode", type=int, default=0, choices=[0, 1, 2, 3],
                     help="single-graph schedule (0: the library's default)")
     ap.add_argument("--graphs", type=int, default=0,

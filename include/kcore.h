@@ -115,8 +115,12 @@ typedef enum {
                                          ceil(4 (c + 2) ln n) with c = 8 (Theorem 2) */
   KCORE_OPT_SAMPLE_THRESHOLD = 19,    /* degree above which a vertex may be sampled; -1 = auto (8 mu) */
   KCORE_OPT_SAMPLE_SEED = 20,         /* Philox key of the coins (default 1) */
-  KCORE_OPT_SAMPLE_CHECK = 21         /* 1 (default) runs the final check; 0 relies on the
+  KCORE_OPT_SAMPLE_CHECK = 21,        /* 1 (default) runs the final check; 0 relies on the
                                          recount test of Sec. 4.1 alone */
+  KCORE_OPT_WARP_COMBINE = 22         /* mode 2: 1 = the lanes of a warp that decrement the same
+                                         vertex in one step send one atomic of their count (warp
+                                         aggregation, the GPU alternative to sampling for hub
+                                         contention); 0 (default) = one atomic per arc */
 } kcore_option;
 
 /* Counters of the last decomposition, or of the last CSR check (the three

@@ -22,8 +22,8 @@ struct kcore_ctx {
   size_t ws_bytes = 0;
   bool ws_external = false;
   std::string err;
-  int64_t opt[22] = {0, 0, 0, -1, 2000, 1, 2048, 0, 0, 192, 64, 1024, -1, 0, 32, 0, 1,
-                     0, 0, -1, 1, 1};  // indexed by kcore_option
+  int64_t opt[23] = {0, 0, 0, -1, 2000, 1, 2048, 0, 0, 192, 64, 1024, -1, 0, 32, 0, 1,
+                     0, 0, -1, 1, 1, 0};  // indexed by kcore_option
   cudaStream_t last_stream = nullptr;
   bool pending = false;
   kc::PeelCtl* last_ctl = nullptr;
@@ -238,7 +238,7 @@ kcore_status kcore_destroy(kcore_handle h) {
 const char* kcore_last_error(kcore_handle h) { return h ? h->err.c_str() : "null handle"; }
 
 kcore_status kcore_set_option(kcore_handle h, kcore_option opt, int64_t value) {
-  if (!h || (int)opt < 0 || (int)opt > 21) return KCORE_ERR_INVALID;
+  if (!h || (int)opt < 0 || (int)opt > 22) return KCORE_ERR_INVALID;
   switch (opt) {
     case KCORE_OPT_BATCH_BLOCK:
       if (value != 256 && value != 512 && value != 1024)
@@ -261,6 +261,7 @@ kcore_status kcore_set_option(kcore_handle h, kcore_option opt, int64_t value) {
       break;
     case KCORE_OPT_SAMPLING:
     case KCORE_OPT_SAMPLE_CHECK:
+    case KCORE_OPT_WARP_COMBINE:
       if (value < 0 || value > 1) return fail(h, KCORE_ERR_INVALID, "sampling switches must be 0 or 1");
       break;
     case KCORE_OPT_SAMPLE_MU:
@@ -311,7 +312,7 @@ kcore_status kcore_set_option(kcore_handle h, kcore_option opt, int64_t value) {
 }
 
 kcore_status kcore_get_option(kcore_handle h, kcore_option opt, int64_t* value) {
-  if (!h || !value || (int)opt < 0 || (int)opt > 21) return KCORE_ERR_INVALID;
+  if (!h || !value || (int)opt < 0 || (int)opt > 22) return KCORE_ERR_INVALID;
   *value = h->opt[opt];
   return KCORE_OK;
 }
@@ -408,6 +409,7 @@ kcore_status peel_call(kcore_ctx* h, int64_t n, int64_t m, const int64_t* offset
   a.touched = (int*)(ws + L.touched);
   a.kprime = threshold ? std::max<int32_t>(kprime, 0) : 0;
   a.size_out = (long long*)size_out;
+  a.combine = mode == 2 && h->opt[KCORE_OPT_WARP_COMBINE] != 0 ? 1 : 0;
 
   if (mode != 1 && m >= ((int64_t)1 << 40))
     return fail(h, KCORE_ERR_INVALID, "the bulk-synchronous modes take at most 2^40 arcs");

@@ -141,6 +141,9 @@ struct PeelArgs {
   // when set, the kernel runs only if *run_if != 0 (the rerun after a sampled
   // run that was not exact)
   const int* run_if;
+  // bulk-synchronous mode: the lanes of a warp that decrement the same vertex
+  // in the same step send one atomic of their count (warp aggregation)
+  int combine;
 };
 
 // Per-round trace record (KCORE_OPT_TRACE): globaltimer at round start (CTA 0),

@@ -502,7 +502,7 @@ __device__ __forceinline__ void push_crossed(const PeelArgs& a, ShT<kSample>& sh
 // With sampling (kSample), d~ is always read first: a neighbour in sample
 // mode (d~ < 0) is not decremented but tosses the arc's coin, and its mu-th
 // head puts it in the counting bag (the recount list of the next recount).
-template <bool kWin, bool kSample = false>
+template <bool kWin, bool kSample = false, bool kCombine = false>
 __device__ void process_items(const PeelArgs& a, ShT<kSample>& sh, const PassCtx& pc, unsigned long long item,
                               int c, int warp, int lane) {
   const int t = pc.t;
@@ -573,10 +573,24 @@ __device__ void process_items(const PeelArgs& a, ShT<kSample>& sh, const PassCtx
 #pragma unroll
     for (int q = 0; q < kIlp; q++)
       if (dq[q] > t) {
-        ndec++;
-        const int old = atomicSub(a.deg + u[q], 1);
-        if (old == t + 1) cross |= 1u << q;
-        if (kWin && old == pc.win_hi) enter |= 1u << q;  // d~ drops into the level window
+        if constexpr (kCombine) {
+          // warp aggregation: the lanes of this slot that decrement the same
+          // vertex send one atomic of their count; the lane whose interval
+          // (old - cnt, old] holds k reports the crossing, so it is still
+          // decided once per vertex
+          const unsigned grp = __match_any_sync(__activemask(), u[q]);
+          if (lane == __ffs(grp) - 1) {
+            const int cnt = __popc(grp);
+            ndec++;
+            const int old = atomicSub(a.deg + u[q], cnt);
+            if (old > t && old - cnt <= t) cross |= 1u << q;
+          }
+        } else {
+          ndec++;
+          const int old = atomicSub(a.deg + u[q], 1);
+          if (old == t + 1) cross |= 1u << q;
+          if (kWin && old == pc.win_hi) enter |= 1u << q;  // d~ drops into the level window
+        }
       }
     if (kWin && __any_sync(kFull, enter != 0)) {
       // append the vertices entering the window to the active list
@@ -633,7 +647,7 @@ __device__ void process_items(const PeelArgs& a, ShT<kSample>& sh, const PassCtx
 
 // Runs up to `budget` batches from the warp's local queue (vertices that
 // crossed during this pass), then moves what is left to the queue.
-template <bool kWin, bool kSample = false>
+template <bool kWin, bool kSample = false, bool kCombine = false>
 __device__ void drain_local(const PeelArgs& a, ShT<kSample>& sh, const PassCtx& pc, int warp, int lane,
                             long long& local_items, unsigned& local_batches) {
   for (int b = 0;; b++) {
@@ -662,7 +676,7 @@ __device__ void drain_local(const PeelArgs& a, ShT<kSample>& sh, const PassCtx& 
     __syncwarp();
     if (lane == 0) sh.lqn[warp] = lqn - c;
     __syncwarp();
-    process_items<kWin, kSample>(a, sh, pc, item, c, warp, lane);
+    process_items<kWin, kSample, kCombine>(a, sh, pc, item, c, warp, lane);
     local_items += c;
     if (lane == 0 && ((++local_batches) & 63) == 0) atomicAdd(&a.ctl->progress, 1ull);
   }
@@ -672,7 +686,7 @@ __device__ void drain_local(const PeelArgs& a, ShT<kSample>& sh, const PassCtx& 
 // its own contiguous share (len / warps items, one more for the first
 // len % warps warps) in chunks of up to 32 items, so a pass has no claim
 // traffic and ends for a warp as soon as its share and local queue are done.
-template <bool kWin, bool kSample = false>
+template <bool kWin, bool kSample = false, bool kCombine = false>
 __device__ void run_pass(const PeelArgs& a, ShT<kSample>& sh, const PassCtx& pc, unsigned long long qb,
                          unsigned long long qe, long long& items, long long& local_items,
                          unsigned& local_batches) {
@@ -685,9 +699,9 @@ __device__ void run_pass(const PeelArgs& a, ShT<kSample>& sh, const PassCtx& pc,
   for (unsigned long long pos = b; pos < e; pos += kTake) {
     const int c = (int)min((unsigned long long)kTake, e - pos);
     const unsigned long long item = lane < c ? __ldcg(a.Q + pos + lane) : 0;
-    process_items<kWin, kSample>(a, sh, pc, item, c, warp, lane);
+    process_items<kWin, kSample, kCombine>(a, sh, pc, item, c, warp, lane);
     items += c;
-    drain_local<kWin, kSample>(a, sh, pc, warp, lane, local_items, local_batches);
+    drain_local<kWin, kSample, kCombine>(a, sh, pc, warp, lane, local_items, local_batches);
   }
 }
 
@@ -916,9 +930,10 @@ __device__ void run_recount_apply(const PeelArgs& a, const PassCtx& pc, unsigned
 }
 
 // Instantiations: kOffline (Algorithm 2's subrounds), kWindow (the level
-// window), kHybrid (batch update of heavy subrounds) and kSample (sampling),
-// each compiled apart so the default kernel carries none of the others.
-template <bool kOffline, bool kWindow, bool kHybrid, bool kSample>
+// window), kHybrid (batch update of heavy subrounds), kSample (sampling) and
+// kCombine (warp-aggregated decrements), each compiled apart so the default
+// kernel carries none of the others.
+template <bool kOffline, bool kWindow, bool kHybrid, bool kSample, bool kCombine = false>
 __global__ void __launch_bounds__(kBlock, 2) peel_bsp(PeelArgs a) {
   __shared__ ShT<kSample> sh;
   // a rerun that is not needed ends at once (every CTA reads the same flag)
@@ -1123,7 +1138,7 @@ __global__ void __launch_bounds__(kBlock, 2) peel_bsp(PeelArgs a) {
         const bool pre = (qend - qb) >= (unsigned long long)kPrecheckShare * gridDim.x * kWarps;
         const PassCtx pc{P, qend, t, a.threshold ? 0 : t, pre, W ? hi_w : -1, const_cast<int*>(Acur),
                          (unsigned long long)(la + near_extra)};
-        run_pass<kWindow>(a, sh, pc, qb, qend, items, local_items, local_batches);
+        run_pass<kWindow, false, kCombine>(a, sh, pc, qb, qend, items, local_items, local_batches);
         if (a.threshold && lane == 0 && sh.ncross[warp]) {
           atomicAdd(&a.ctl->crossed, (unsigned long long)sh.ncross[warp]);
           sh.ncross[warp] = 0;
@@ -1284,7 +1299,9 @@ int bsp_max_ctas_per_sm() {
                        (const void*)peel_bsp<true, false, false, false>,
                        (const void*)peel_bsp<false, true, false, false>,
                        (const void*)peel_bsp<false, false, true, false>,
-                       (const void*)peel_bsp<false, false, false, true>};
+                       (const void*)peel_bsp<false, false, false, true>,
+                       (const void*)peel_bsp<false, false, true, false, true>,
+                       (const void*)peel_bsp<false, false, false, false, true>};
   int best = 1 << 30;
   for (const void* f : fns) {
     int nb = 0;
@@ -1301,6 +1318,9 @@ cudaError_t bsp_launch(const PeelArgs& args, int grid, cudaStream_t stream) {
   void* params[] = {&a};
   const void* fn = a.sample       ? (const void*)peel_bsp<false, false, false, true>
                    : a.offline    ? (const void*)peel_bsp<true, false, false, false>
+                   : a.combine && a.window == 0
+                       ? (a.hybrid ? (const void*)peel_bsp<false, false, true, false, true>
+                                   : (const void*)peel_bsp<false, false, false, false, true>)
                    : a.window > 0 ? (const void*)peel_bsp<false, true, false, false>
                    : a.hybrid     ? (const void*)peel_bsp<false, false, true, false>
                                   : (const void*)peel_bsp<false, false, false, false>;

@@ -1,4 +1,5 @@
-"""The sampled peel (Sec. 4.1, Algorithms 4-5) on the GPU, through the C ABI:
+"""The sampled peel (Sec. 4.1, Algorithms 4-5) and warp-aggregated decrements
+(its alternative for hub contention) on the GPU, through the C ABI:
 bit-exact coreness against Batagelj-Zaversnik on graphs with hubs, cliques
 and long paths, over mu, thresholds and seeds; the coins are the oracle's
 (Philox4x32-10 of the arc index), so on a star the GPU's heads and its
@@ -146,3 +147,16 @@ def test_sampled_rmat20_exact(kc):
     core, km, st = _run(kc, off, adj, sampling=1)
     np.testing.assert_array_equal(core, want)
     assert st["sample_vertices"] > 0
+
+
+@pytest.mark.parametrize("name", list(GRAPHS))
+@pytest.mark.parametrize("batch_update", [0, 1])
+def test_warp_combined_decrements_are_exact(kc, name, batch_update):
+    # warp aggregation of decrements to one vertex: one atomic per group, the
+    # crossing reported by the group whose interval holds the level
+    n, s, d = GRAPHS[name]()
+    off, adj = oracle.build_csr(n, s, d)
+    core, km, st = _run(kc, off, adj, warp_combine=1, batch_update=batch_update)
+    want = oracle.bz(n, off, adj)
+    np.testing.assert_array_equal(core, want)
+    assert km == int(want.max()) and st["sync_mode"] == 2
