@@ -76,7 +76,8 @@ typedef enum {
                                     completion token (mode 1) or its arrival at the first grid
                                     barrier (mode 2), so every device wait must run out its
                                     time limit and the call ends with KCORE_ERR_TIMEOUT */
-  KCORE_OPT_TRACE = 8,           /* 1 records a per-round timeline (kcore_get_trace) */
+  KCORE_OPT_TRACE = 8,           /* 1 records a per-round timeline (kcore_get_trace); 2 (modes 2
+                                    and 3) one record per phase instead */
   KCORE_OPT_IDLE_SLEEP_NS = 9,   /* nanosleep of a warp waiting for work (0 .. 100000) */
   KCORE_OPT_POLL_SLEEP_NS = 10,  /* nanosleep of a CTA's round-end poller (0 .. 100000) */
   KCORE_OPT_BATCH_BLOCK = 11,    /* batched peel: threads per CTA (256, 512 or 1024; default 1024) */
@@ -417,6 +418,12 @@ kcore_status kcore_get_stats(kcore_handle h, kcore_stats* out);
  * [12] summed time warps spent in work batches (ns), [13] work batches.
  * In mode 2 there is one entry per non-empty level: [1] is when its scan
  * phases ended, [10..12] are 0 and [13] counts its subround passes.
+ * With KCORE_OPT_TRACE = 2 (modes 2 and 3) there is one entry per phase
+ * (grid barrier) instead: [0] device time (ns) the phase ended, [1] its kind
+ * (0 scan, 1 subround pass, 2 counting phase, 3 apply phase, 4 second scan
+ * of an empty level), [2] the level, [3] the range it worked on (list
+ * entries of a scan, queue items of a pass), [4] items it appended, [5]
+ * frontier vertices a scan found, [6] arcs a pass read; [7..13] are 0.
  * Tracing adds atomics and slows the run. At most max_rounds rounds are
  * copied; *rounds_out receives the number copied. */
 kcore_status kcore_get_trace(kcore_handle h, uint64_t* out, int64_t max_rounds, int64_t* rounds_out);

@@ -33,6 +33,7 @@ struct kcore_ctx {
   int* last_validate_status = nullptr;  // device status words of the last CSR check
   int last_batch_block = 0, last_batch_grid = 0, last_batch_smem_vertices = 0;
   unsigned long long* last_trace = nullptr;
+  bool last_trace_phases = false;  // the trace holds one record per phase
   int last_max_rounds = 0;
   kcore_stats stats{};
   int last_grid = 0;
@@ -277,7 +278,7 @@ kcore_status kcore_set_option(kcore_handle h, kcore_option opt, int64_t value) {
       if (value < 0 || value > 100000) return fail(h, KCORE_ERR_INVALID, "sleep must be in [0, 100000] ns");
       break;
     case KCORE_OPT_TRACE:
-      if (value < 0 || value > 1) return fail(h, KCORE_ERR_INVALID, "trace must be 0 or 1");
+      if (value < 0 || value > 2) return fail(h, KCORE_ERR_INVALID, "trace must be 0, 1 or 2");
       break;
     case KCORE_OPT_TEST_STALL:
       if (value < 0 || value > 1) return fail(h, KCORE_ERR_INVALID, "test stall must be 0 or 1");
@@ -399,6 +400,7 @@ kcore_status peel_call(kcore_ctx* h, int64_t n, int64_t m, const int64_t* offset
   a.poll_sleep_ns = (int)h->opt[KCORE_OPT_POLL_SLEEP_NS];
   a.inject_stall = (int)h->opt[KCORE_OPT_TEST_STALL];
   a.trace = h->opt[KCORE_OPT_TRACE] ? (unsigned long long*)(ws + L.trace) : nullptr;
+  a.trace_phases = h->opt[KCORE_OPT_TRACE] == 2 && mode != 1 ? 1 : 0;
   a.local_batches = h->opt[KCORE_OPT_LOCAL_BATCHES] > 0 ? (int)h->opt[KCORE_OPT_LOCAL_BATCHES] : INT32_MAX;
   a.threshold = threshold ? 1 : 0;
   a.offline = mode == 3 ? 1 : 0;
@@ -473,6 +475,7 @@ kcore_status peel_call(kcore_ctx* h, int64_t n, int64_t m, const int64_t* offset
     h->last_ctl = a.ctl;
   }
   h->last_trace = a.trace;
+  h->last_trace_phases = a.trace_phases != 0;
   h->last_max_rounds = L.max_rounds;
   h->last_grid = (int)grid;
   h->last_mode = mode;
@@ -831,8 +834,11 @@ kcore_status kcore_get_trace(kcore_handle h, uint64_t* out, int64_t max_rounds, 
   *rounds_out = 0;
   if (!h->last_trace) return fail(h, KCORE_ERR_INVALID, "the last decomposition ran without tracing");
   DeviceGuard g(h->device);
-  // the bulk-synchronous modes record one entry per non-empty level
-  const int64_t have = h->last_mode != 1 ? h->stats.rounds - h->stats.empty_rounds : h->stats.rounds;
+  // the bulk-synchronous modes record one entry per non-empty level, or per
+  // phase (barrier) with trace mode 2
+  const int64_t have = h->last_trace_phases ? h->stats.barriers
+                       : h->last_mode != 1  ? h->stats.rounds - h->stats.empty_rounds
+                                            : h->stats.rounds;
   int64_t r = std::min<int64_t>(std::min<int64_t>(max_rounds, have), h->last_max_rounds);
   if (r > 0) {
     cudaError_t e = cudaMemcpy(out, h->last_trace, sizeof(uint64_t) * kc::kTraceFields * (size_t)r,

@@ -100,6 +100,7 @@ struct PeelArgs {
   int poll_sleep_ns;  // sleep of the CTA's round poller between polls
   int inject_stall;
   unsigned long long* trace;  // optional: kTraceFields words per round (nullptr = off)
+  int trace_phases;           // bulk-synchronous mode: one trace record per phase instead of per level
   int local_batches;          // bulk-synchronous mode: local batches per chunk taken
   // k'-core query (bulk-synchronous mode only): one peel at level kprime - 1
   // taking every vertex below kprime; core[] receives 1 (in the k'-core) or 0

@@ -966,6 +966,27 @@ __global__ void __launch_bounds__(kBlock, 2) peel_bsp(PeelArgs a) {
       }
     }
   };
+  // per-phase timeline (trace mode 2): after each barrier CTA 0 records the
+  // time, the phase kind (0 scan, 1 pass, 2 count, 3 apply, 4 second scan),
+  // the level, the range it worked on, its appends, the frontier found and
+  // the arcs read (passes)
+  long long nrec = 0;
+  unsigned long long arcs_seen = 0;
+  auto prec = [&](int kind, int level, unsigned long long range, unsigned long long appended,
+                  unsigned long long found) {
+    if (!(lead && a.trace_phases && nrec < a.max_rounds)) return;
+    unsigned long long* tr = a.trace + (size_t)nrec * kTraceFields;
+    const unsigned long long arcs = ld_relaxed_u64(&a.ctl->tr_arcs);
+    tr[0] = globaltimer_ns();
+    tr[1] = (unsigned long long)kind;
+    tr[2] = (unsigned long long)level;
+    tr[3] = range;
+    tr[4] = appended;
+    tr[5] = found;
+    tr[6] = arcs - arcs_seen;
+    arcs_seen = arcs;
+    nrec++;
+  };
   auto nscan_of = [&](long long len) {
     long long ns = (len + a.scan_min - 1) / a.scan_min;
     return ns < 1 ? 1ll : (ns > (long long)gridDim.x ? (long long)gridDim.x : ns);
@@ -1022,6 +1043,7 @@ __global__ void __launch_bounds__(kBlock, 2) peel_bsp(PeelArgs a) {
     phase++;
     scanned += lin;
     const unsigned long long found = ld_relaxed_u64(&R->found);
+    prec(0, tk, (unsigned long long)lin, ld_relaxed_u64(&R->tail), found);
     const long long alen = (long long)ld_relaxed_u64(&R->alen);
     const int minkey = ld_relaxed_s32(&R->minkey);
     unsigned long long qb = qend;
@@ -1061,6 +1083,7 @@ __global__ void __launch_bounds__(kBlock, 2) peel_bsp(PeelArgs a) {
       phase++;
       scanned += la;
       nfound = ld_relaxed_u64(&R->found);
+      prec(4, t, (unsigned long long)la, ld_relaxed_u64(&R->tail), nfound);
       qend += ld_relaxed_u64(&R->tail);
     }
     kmax = t;
@@ -1118,12 +1141,14 @@ __global__ void __launch_bounds__(kBlock, 2) peel_bsp(PeelArgs a) {
           run_hist<false>(a, sh, hc, qb, qend, items);
           if (!(ok = grid_barrier(a, sh, gen))) break;
           phase++;
+          prec(2, t, qend - qb, 0, 0);
           reset_next();
           RoundRec* P2 = a.rounds + (phase % kPhaseRing);
           const PassCtx pc{P2, qend, t, t, false, -1, nullptr, 0};
           run_apply(a, pc, Acur, (unsigned long long)la);
           if (!(ok = grid_barrier(a, sh, gen))) break;
           phase++;
+          prec(3, t, (unsigned long long)la, ld_relaxed_u64(&P2->tail), 0);
           passes++;
           level_passes++;
           qb = qend;
@@ -1152,6 +1177,7 @@ __global__ void __launch_bounds__(kBlock, 2) peel_bsp(PeelArgs a) {
         phase++;
         passes++;
         level_passes++;
+        prec(1, t, qend - qb, ld_relaxed_u64(&P->tail), 0);
         qb = qend;
         qend += ld_relaxed_u64(&P->tail);
         if (W) near_extra += (long long)ld_relaxed_u64(&P->found);
@@ -1159,7 +1185,7 @@ __global__ void __launch_bounds__(kBlock, 2) peel_bsp(PeelArgs a) {
     } else {
       qb = qend;
     }
-    if (lead && a.trace && levels - 1 < a.max_rounds) {
+    if (lead && a.trace && !a.trace_phases && levels - 1 < a.max_rounds) {
       unsigned long long* tr = a.trace + (size_t)(levels - 1) * kTraceFields;
       tr[0] = t_start;
       tr[1] = t_scan;

@@ -121,9 +121,11 @@ class KCore:
         return {f: int(getattr(s, f)) for f, _ in _native.Stats._fields_}
 
     def trace(self) -> np.ndarray:
-        """Per-round timeline of the last decomposition (needs trace=1):
-        structured array with the fields of TRACE_FIELDS."""
-        max_r = max(self.stats()["rounds"], 0)
+        """Timeline of the last decomposition: one row of TRACE_FIELDS per
+        round with trace=1, one row per phase with trace=2 (fields as
+        kcore_get_trace documents)."""
+        st = self.stats()
+        max_r = max(st["barriers"] if self.get_option("trace") == 2 else st["rounds"], 0)
         buf = np.zeros((max(max_r, 1), len(TRACE_FIELDS)), np.uint64)
         got = ctypes.c_int64()
         self._check(self._L.kcore_get_trace(self._h, buf.ctypes.data, max_r, ctypes.byref(got)))

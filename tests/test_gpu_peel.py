@@ -242,6 +242,32 @@ def test_bsp_counters_and_trace():
     assert (tr[:, 2] >= tr[:, 1]).all() and (tr[:, 1] >= tr[:, 0]).all()
 
 
+@pytest.mark.parametrize("batch_update", [0, 1])
+def test_bsp_phase_trace(batch_update):
+    """Trace mode 2: one record per grid barrier, in time order, levels
+    non-decreasing; without the batch update the passes read every arc once
+    (each vertex's list is traversed exactly once), and the scans' found
+    counts sum to the vertices they took."""
+    n = 60000
+    s, d = gg.rmat_n(n, 500000, seed=22)
+    off, adj = _csr(n, s, d)
+    want = oracle.bz(n, off, adj)
+    with KCore(0, sync_mode=2, trace=2, batch_update=batch_update) as k:
+        assert_parity(k, n, off, adj, want)
+        st = k.stats()
+        tr = k.trace().astype(np.int64)
+    assert len(tr) == st["barriers"]
+    assert (np.diff(tr[:, 0]) >= 0).all()
+    kinds = tr[:, 1]
+    assert set(np.unique(kinds)) <= {0, 1, 2, 3, 4}
+    assert (np.diff(tr[:, 2]) >= 0).all()
+    assert int(np.count_nonzero(kinds == 1)) + int(np.count_nonzero(kinds == 3)) == st["passes"]
+    assert int(np.count_nonzero((kinds == 0) | (kinds == 4))) == st["rounds"] + 1
+    if batch_update == 0:
+        assert int(tr[kinds == 1, 6].sum()) == len(adj)
+    assert set(np.unique(tr[kinds == 1, 2])) <= set(np.unique(want).tolist())
+
+
 @pytest.mark.parametrize("mode", MODES)
 def test_isolated_only_and_single_level(mode):
     """Graphs whose vertices all share one coreness: isolated vertices only,
