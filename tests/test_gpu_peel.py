@@ -262,7 +262,10 @@ def test_bsp_phase_trace(batch_update):
     assert set(np.unique(kinds)) <= {0, 1, 2, 3, 4}
     assert (np.diff(tr[:, 2]) >= 0).all()
     assert int(np.count_nonzero(kinds == 1)) + int(np.count_nonzero(kinds == 3)) == st["passes"]
-    assert int(np.count_nonzero((kinds == 0) | (kinds == 4))) == st["rounds"] + 1
+    # a scan per visited level (two for an empty one), and perhaps a last
+    # scan that finds nothing left
+    assert int(np.count_nonzero((kinds == 0) | (kinds == 4))) - st["rounds"] in (0, 1)
+    assert int(np.count_nonzero(kinds == 4)) == st["empty_rounds"]
     if batch_update == 0:
         assert int(tr[kinds == 1, 6].sum()) == len(adj)
     assert set(np.unique(tr[kinds == 1, 2])) <= set(np.unique(want).tolist())
