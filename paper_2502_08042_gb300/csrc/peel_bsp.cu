@@ -68,6 +68,14 @@ struct Shared {
   unsigned long long tr_arcs[kWarps], tr_decs[kWarps];  // trace only
   unsigned ncross[kWarps];                               // k'-core query: crossings
   int flag;
+  long long trec;            // per-phase trace: records written (CTA 0)
+  unsigned long long tarcs;  // per-phase trace: arcs counted at the last record
+  // the finished phase's counters, read once per CTA by grid_barrier (every
+  // thread loading them would queue thousands of loads on one L2 line)
+  struct {
+    unsigned long long tail, head, found, alen, rcount, rqtail;
+    int minkey, miss;
+  } po;
 };
 
 // Sampling keeps the vertex of each local-queue entry beside it (a spilled
@@ -88,6 +96,30 @@ __device__ __forceinline__ void raise_status(const PeelArgs& a, int code) {
 
 __device__ __forceinline__ unsigned long long make_item(long long a0, long long len) {
   return (unsigned long long)a0 | ((unsigned long long)len << kLenShift);
+}
+
+// Writes each lane's arc range [e0, e1), cut in `cnt` slices, to the queue
+// from slot p on. A lane with a few slices writes its own; the slices of a
+// long range (a hub) are written by the whole warp, so one lane never stores
+// thousands of items alone. Warp-collective.
+__device__ __forceinline__ void write_slices(const PeelArgs& a, long long e0, long long e1, int cnt,
+                                             unsigned long long p, int lane) {
+  constexpr int kOwn = 4;
+  if (cnt <= kOwn)
+    for (int i = 0; i < cnt; i++) {
+      const long long s0 = e0 + (long long)i * a.slice;
+      a.Q[p + i] = make_item(s0, min((long long)a.slice, e1 - s0));
+    }
+  for (unsigned big = __ballot_sync(kFull, cnt > kOwn); big; big &= big - 1) {
+    const int L = __ffs(big) - 1;
+    const long long b0 = __shfl_sync(kFull, e0, L), b1 = __shfl_sync(kFull, e1, L);
+    const unsigned long long bp = __shfl_sync(kFull, p, L);
+    const int bc = __shfl_sync(kFull, cnt, L);
+    for (int i = lane; i < bc; i += kWarp) {
+      const long long s0 = b0 + (long long)i * a.slice;
+      a.Q[bp + i] = make_item(s0, min((long long)a.slice, b1 - s0));
+    }
+  }
 }
 
 // ---- sampling (Sec. 4.1) ------------------------------------------------
@@ -178,7 +210,10 @@ __device__ void append_recount(const PeelArgs& a, RoundRec* R, bool flag, int v,
 // Waiters give up after timeout_ns without progress (a warp running a long
 // local chain ticks ctl->progress). Returns false when a status was raised
 // before the barrier completed, or when the wait gave up.
-__device__ bool grid_barrier(const PeelArgs& a, Shared& sh, unsigned long long& gen) {
+// With R, thread 0 then reads R's counters (and the sampling miss flag) into
+// sh.po for the whole CTA.
+__device__ bool grid_barrier(const PeelArgs& a, Shared& sh, unsigned long long& gen,
+                             const RoundRec* R = nullptr) {
   __syncthreads();
   if (threadIdx.x == 0) {
     int ok = 1;
@@ -211,6 +246,16 @@ __device__ bool grid_barrier(const PeelArgs& a, Shared& sh, unsigned long long& 
     }
     gen++;
     sh.flag = ok;
+    if (ok && R) {
+      sh.po.tail = ld_relaxed_u64(&R->tail);
+      sh.po.head = ld_relaxed_u64(&R->head);
+      sh.po.found = ld_relaxed_u64(&R->found);
+      sh.po.alen = ld_relaxed_u64(&R->alen);
+      sh.po.rcount = ld_relaxed_u64(&R->rcount);
+      sh.po.rqtail = ld_relaxed_u64(&R->rqtail);
+      sh.po.minkey = ld_relaxed_s32(&R->minkey);
+      sh.po.miss = ld_relaxed_s32(&a.ctl->s_miss);
+    }
   }
   __syncthreads();
   return sh.flag != 0;
@@ -449,6 +494,7 @@ struct PassCtx {
 
 // Appends `cnt` items per lane (lane-owned arc ranges [e0, e1) cut in
 // slices) to the queue.
+template <bool kCoop = false>
 __device__ __forceinline__ void append_ranges(const PeelArgs& a, const PassCtx& pc, int cnt, long long e0,
                                               long long e1, int lane) {
   const int incl = warp_incl_scan(cnt, lane);
@@ -462,7 +508,11 @@ __device__ __forceinline__ void append_ranges(const PeelArgs& a, const PassCtx& 
     return;
   }
   unsigned long long p = base + (unsigned long long)(incl - cnt);
-  for (long long s0 = e0; s0 < e1 && cnt > 0; s0 += a.slice) a.Q[p++] = make_item(s0, min((long long)a.slice, e1 - s0));
+  if constexpr (kCoop) {
+    write_slices(a, e0, e1, cnt, p, lane);
+  } else {
+    for (long long s0 = e0; s0 < e1 && cnt > 0; s0 += a.slice) a.Q[p++] = make_item(s0, min((long long)a.slice, e1 - s0));
+  }
 }
 
 // The vertices u of the lanes with `flag` crossed to the current level (their
@@ -826,7 +876,7 @@ __device__ void run_apply(const PeelArgs& a, const PassCtx& pc, const int* list,
         raise_status(a, ST_CAPACITY);
       }
     }
-    append_ranges(a, pc, cross ? nsl : 0, e0, e1, lane);
+    append_ranges<true>(a, pc, cross ? nsl : 0, e0, e1, lane);
   }
 }
 
@@ -923,7 +973,7 @@ __device__ void run_recount_apply(const PeelArgs& a, const PassCtx& pc, unsigned
     const unsigned jm = __ballot_sync(kFull, join);
     if (jm && lane == 0) atomicAdd(&pc.R->found, (unsigned long long)__popc(jm));
     const int nsl = join ? (int)((e1 - e0 + a.slice - 1) / a.slice) : 0;
-    append_ranges(a, pc, nsl, e0, e1, lane);
+    append_ranges<true>(a, pc, nsl, e0, e1, lane);
   }
   kmin = warp_min(kmin);
   if (lane == 0 && kmin != INT_MAX) atomicMax(&pc.R->minkey, INT_MAX - kmin);
@@ -970,12 +1020,19 @@ __global__ void __launch_bounds__(kBlock, 2) peel_bsp(PeelArgs a) {
   // time, the phase kind (0 scan, 1 pass, 2 count, 3 apply, 4 second scan),
   // the level, the range it worked on, its appends, the frontier found and
   // the arcs read (passes)
-  long long nrec = 0;
-  unsigned long long arcs_seen = 0;
-  auto prec = [&](int kind, int level, unsigned long long range, unsigned long long appended,
+  // (the record count lives in shared memory: a register held across the
+  // whole level loop made the hot loop spill)
+  if (lead) {
+    sh.trec = 0;
+    sh.tarcs = 0;
+  }
+  // (the appends are read here, from the phase's record, only when tracing:
+  // an argument load at every call site cost a dependent L2 read per phase)
+  auto prec = [&](int kind, int level, unsigned long long range, const RoundRec* rec,
                   unsigned long long found) {
-    if (!(lead && a.trace_phases && nrec < a.max_rounds)) return;
-    unsigned long long* tr = a.trace + (size_t)nrec * kTraceFields;
+    if (!(lead && a.trace_phases && sh.trec < a.max_rounds)) return;
+    const unsigned long long appended = rec ? ld_relaxed_u64(&rec->tail) : 0;
+    unsigned long long* tr = a.trace + (size_t)sh.trec * kTraceFields;
     const unsigned long long arcs = ld_relaxed_u64(&a.ctl->tr_arcs);
     tr[0] = globaltimer_ns();
     tr[1] = (unsigned long long)kind;
@@ -983,9 +1040,9 @@ __global__ void __launch_bounds__(kBlock, 2) peel_bsp(PeelArgs a) {
     tr[3] = range;
     tr[4] = appended;
     tr[5] = found;
-    tr[6] = arcs - arcs_seen;
-    arcs_seen = arcs;
-    nrec++;
+    tr[6] = arcs - sh.tarcs;
+    sh.tarcs = arcs;
+    sh.trec++;
   };
   auto nscan_of = [&](long long len) {
     long long ns = (len + a.scan_min - 1) / a.scan_min;
@@ -1039,19 +1096,19 @@ __global__ void __launch_bounds__(kBlock, 2) peel_bsp(PeelArgs a) {
         if (o.dmin != INT_MAX) atomicMax(&R->minkey, INT_MAX - o.dmin);
       }
     }
-    if (!grid_barrier(a, sh, gen)) break;
+    if (!grid_barrier(a, sh, gen, R)) break;
     phase++;
     scanned += lin;
-    const unsigned long long found = ld_relaxed_u64(&R->found);
-    prec(0, tk, (unsigned long long)lin, ld_relaxed_u64(&R->tail), found);
-    const long long alen = (long long)ld_relaxed_u64(&R->alen);
-    const int minkey = ld_relaxed_s32(&R->minkey);
+    const unsigned long long found = sh.po.found;
+    prec(0, tk, (unsigned long long)lin, R, found);
+    const long long alen = (long long)sh.po.alen;
+    const int minkey = sh.po.minkey;
     unsigned long long qb = qend;
-    qend += ld_relaxed_u64(&R->tail);
+    qend += sh.po.tail;
     Acur = Aout;
     if (rebuild) {
       Aover = Aov;
-      lover = (long long)ld_relaxed_u64(&R->head);
+      lover = (long long)sh.po.head;
       hi_w = tk + W;
       rebuilds++;
     }
@@ -1079,12 +1136,12 @@ __global__ void __launch_bounds__(kBlock, 2) peel_bsp(PeelArgs a) {
         const ScanOut o = scan_range(a, sh, R, qend, Acur, nullptr, lo, hi, INT_MAX, t);
         if (tid == 0 && o.found) atomicAdd(&R->found, o.found);
       }
-      if (!grid_barrier(a, sh, gen)) break;
+      if (!grid_barrier(a, sh, gen, R)) break;
       phase++;
       scanned += la;
-      nfound = ld_relaxed_u64(&R->found);
-      prec(4, t, (unsigned long long)la, ld_relaxed_u64(&R->tail), nfound);
-      qend += ld_relaxed_u64(&R->tail);
+      nfound = sh.po.found;
+      prec(4, t, (unsigned long long)la, R, nfound);
+      qend += sh.po.tail;
     }
     kmax = t;
     tp = t;
@@ -1105,20 +1162,20 @@ __global__ void __launch_bounds__(kBlock, 2) peel_bsp(PeelArgs a) {
         RoundRec* P = a.rounds + (phase % kPhaseRing);
         const PassCtx hc{P, qend, t, t, false, -1, nullptr, 0};
         run_hist<true>(a, sh, hc, qb, qend, items);
-        if (!(ok = grid_barrier(a, sh, gen))) break;
+        if (!(ok = grid_barrier(a, sh, gen, P))) break;
         phase++;
-        const unsigned long long nt = ld_relaxed_u64(&P->head);
+        const unsigned long long nt = sh.po.head;
         // apply phase: crossings append the next frontier (count in P2->tail)
         reset_next();
         RoundRec* P2 = a.rounds + (phase % kPhaseRing);
         const PassCtx pc{P2, qend, t, t, false, -1, nullptr, 0};
         run_apply(a, pc, a.touched, nt);
-        if (!(ok = grid_barrier(a, sh, gen))) break;
+        if (!(ok = grid_barrier(a, sh, gen, P2))) break;
         phase++;
         passes++;
         level_passes++;
         qb = qend;
-        qend += ld_relaxed_u64(&P2->tail);
+        qend += sh.po.tail;
       }
       if (ok && level_passes == 0 && nfound > 0) {
         passes++;
@@ -1141,18 +1198,18 @@ __global__ void __launch_bounds__(kBlock, 2) peel_bsp(PeelArgs a) {
           run_hist<false>(a, sh, hc, qb, qend, items);
           if (!(ok = grid_barrier(a, sh, gen))) break;
           phase++;
-          prec(2, t, qend - qb, 0, 0);
+          prec(2, t, qend - qb, nullptr, 0);
           reset_next();
           RoundRec* P2 = a.rounds + (phase % kPhaseRing);
           const PassCtx pc{P2, qend, t, t, false, -1, nullptr, 0};
           run_apply(a, pc, Acur, (unsigned long long)la);
-          if (!(ok = grid_barrier(a, sh, gen))) break;
+          if (!(ok = grid_barrier(a, sh, gen, P2))) break;
           phase++;
-          prec(3, t, (unsigned long long)la, ld_relaxed_u64(&P2->tail), 0);
+          prec(3, t, (unsigned long long)la, P2, 0);
           passes++;
           level_passes++;
           qb = qend;
-          qend += ld_relaxed_u64(&P2->tail);
+          qend += sh.po.tail;
           continue;
         }
         reset_next();
@@ -1168,19 +1225,29 @@ __global__ void __launch_bounds__(kBlock, 2) peel_bsp(PeelArgs a) {
           atomicAdd(&a.ctl->crossed, (unsigned long long)sh.ncross[warp]);
           sh.ncross[warp] = 0;
         }
-        if (a.trace && lane == 0) {
-          atomicAdd(&a.ctl->tr_arcs, sh.tr_arcs[warp]);
-          atomicAdd(&a.ctl->tr_decs, sh.tr_decs[warp]);
-          sh.tr_arcs[warp] = sh.tr_decs[warp] = 0;
+        if (a.trace) {
+          // one pair of atomics per CTA (per warp, 9,728 same-address atomics
+          // would add several microseconds to every traced pass)
+          __syncthreads();
+          if (tid == 0) {
+            unsigned long long ta = 0, td = 0;
+            for (int w = 0; w < kWarps; w++) {
+              ta += sh.tr_arcs[w];
+              td += sh.tr_decs[w];
+              sh.tr_arcs[w] = sh.tr_decs[w] = 0;
+            }
+            if (ta) atomicAdd(&a.ctl->tr_arcs, ta);
+            if (td) atomicAdd(&a.ctl->tr_decs, td);
+          }
         }
-        if (!(ok = grid_barrier(a, sh, gen))) break;
+        if (!(ok = grid_barrier(a, sh, gen, P))) break;
         phase++;
         passes++;
         level_passes++;
-        prec(1, t, qend - qb, ld_relaxed_u64(&P->tail), 0);
+        prec(1, t, qend - qb, P, 0);
         qb = qend;
-        qend += ld_relaxed_u64(&P->tail);
-        if (W) near_extra += (long long)ld_relaxed_u64(&P->found);
+        qend += sh.po.tail;
+        if (W) near_extra += (long long)sh.po.found;
       }
     } else {
       qb = qend;
@@ -1235,16 +1302,16 @@ __global__ void __launch_bounds__(kBlock, 2) peel_bsp(PeelArgs a) {
           if (o.dmin != INT_MAX) atomicMax(&R->minkey, INT_MAX - o.dmin);
         }
       }
-      if (!grid_barrier(a, sh, gen)) break;
+      if (!grid_barrier(a, sh, gen, R)) break;
       phase++;
       scanned += lin;
-      unsigned long long nfound = ld_relaxed_u64(&R->found);
-      la = (long long)ld_relaxed_u64(&R->alen);
-      const int mk = ld_relaxed_s32(&R->minkey);
+      unsigned long long nfound = sh.po.found;
+      la = (long long)sh.po.alen;
+      const int mk = sh.po.minkey;
       int kmin = mk ? INT_MAX - mk : INT_MAX;
       unsigned long long qb = qend;
-      qend += ld_relaxed_u64(&R->tail);
-      const unsigned long long nr = ld_relaxed_u64(&R->rcount), nrq = ld_relaxed_u64(&R->rqtail);
+      qend += sh.po.tail;
+      const unsigned long long nr = sh.po.rcount, nrq = sh.po.rqtail;
       Acur = Aout;
       if (lead && nr) a.ctl->s_failed += (long long)nr;
       const long long level_pass = passes;
@@ -1262,14 +1329,14 @@ __global__ void __launch_bounds__(kBlock, 2) peel_bsp(PeelArgs a) {
         RoundRec* P = a.rounds + (phase % kPhaseRing);
         const PassCtx pc{P, qend, tk, tk, false, -1, nullptr, 0, (int)passes};
         run_recount_apply(a, pc, nrv, tk, (int)passes);
-        if (!(ok = grid_barrier(a, sh, gen))) return;
+        if (!(ok = grid_barrier(a, sh, gen, P))) return;
         phase++;
-        nfound += ld_relaxed_u64(&P->found);
-        qend += ld_relaxed_u64(&P->tail);
-        const int mk2 = ld_relaxed_s32(&P->minkey);
+        nfound += sh.po.found;
+        qend += sh.po.tail;
+        const int mk2 = sh.po.minkey;
         if (mk2) kmin = min(kmin, INT_MAX - mk2);
         if (lead) a.ctl->s_recounts += (long long)nrv;
-        miss = ld_relaxed_s32(&a.ctl->s_miss) != 0;
+        miss = sh.po.miss != 0;
       };
       if (nr) recount(nr, nrq);
       if (!ok || miss) break;
@@ -1287,12 +1354,12 @@ __global__ void __launch_bounds__(kBlock, 2) peel_bsp(PeelArgs a) {
         RoundRec* P = a.rounds + (phase % kPhaseRing);
         const PassCtx pc{P, qend, tk, tk, true, -1, nullptr, 0, (int)passes};
         run_pass<false, true>(a, sh, pc, qb, qend, items, local_items, local_batches);
-        if (!(ok = grid_barrier(a, sh, gen))) break;
+        if (!(ok = grid_barrier(a, sh, gen, P))) break;
         phase++;
         passes++;
         qb = qend;
-        qend += ld_relaxed_u64(&P->tail);
-        const unsigned long long br = ld_relaxed_u64(&P->rcount), bq = ld_relaxed_u64(&P->rqtail);
+        qend += sh.po.tail;
+        const unsigned long long br = sh.po.rcount, bq = sh.po.rqtail;
         if (br) {
           if (lead) a.ctl->s_bag += (long long)br;
           recount(br, bq);
