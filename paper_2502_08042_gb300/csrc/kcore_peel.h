@@ -50,12 +50,13 @@ struct PeelCtl {
   unsigned long long items, local_items;
   long long rounds, empty_rounds, scanned, kmax;
   char pad3[80];
-  // bulk-synchronous mode: grid barrier (arrivals, generation), queue tail,
-  // subround passes and barriers taken
-  unsigned long long bar_count;
-  char pad4[120];
-  unsigned long long bar_gen;
-  char pad5[120];
+  // bulk-synchronous mode: the grid barrier's words (barrier g uses word
+  // g % 3: arrivals, the phase's queue appends, the abort bit; reset two
+  // phases ahead), queue tail, subround passes and barriers taken
+  struct {
+    unsigned long long v;
+    char pad[120];
+  } bar_ring[3];
   unsigned long long qtail;
   char pad6[120];
   long long passes, barriers;

@@ -50,7 +50,16 @@ constexpr int kTake = 32;  // queue items per chunk of a warp's share
 constexpr int kPrecheckShare = 64;  // per-warp share from which a pass reads d~ before decrementing
 constexpr int kLenShift = 40;  // item = first arc | length << 40
 constexpr unsigned long long kArcMask = (1ull << kLenShift) - 1;
-constexpr unsigned long long kAbort = 1ull << 62;  // barrier word: a status was raised
+// barrier word: arrivals in bits 0..30, the phase's queue appends in bits
+// 31..62 (every append is counted there too, so a pass's range is known from
+// the word that ends the wait), bit 63: a status was raised
+constexpr int kAppShift = 31;
+constexpr unsigned long long kArrMask = (1ull << kAppShift) - 1;
+constexpr unsigned long long kAppMask = (1ull << 32) - 1;
+constexpr unsigned long long kAbort = 1ull << 63;
+
+// queue items the CTA appended in the current phase (added to its arrival)
+__shared__ unsigned long long s_app;
 
 struct Shared {
   int excl[kWarps][kWarp];
@@ -91,7 +100,7 @@ using ShT = std::conditional_t<kSample, SharedS, Shared>;
 // Records the first error and makes every CTA leave at its next barrier.
 __device__ __forceinline__ void raise_status(const PeelArgs& a, int code) {
   atomicCAS(&a.ctl->status, 0, code);
-  atomicOr(&a.ctl->bar_count, kAbort);
+  for (int i = 0; i < 3; i++) atomicOr(&a.ctl->bar_ring[i].v, kAbort);
 }
 
 __device__ __forceinline__ unsigned long long make_item(long long a0, long long len) {
@@ -204,32 +213,39 @@ __device__ void append_recount(const PeelArgs& a, RoundRec* R, bool flag, int v,
   }
 }
 
-// Grid barrier on one word: the arrivals (release adds) and the abort bit.
-// Phase g is complete when (g + 1) * gridDim.x arrivals are counted; the
-// acquire load that sees them makes every CTA's writes of the phase visible.
-// Waiters give up after timeout_ns without progress (a warp running a long
-// local chain ticks ctl->progress). Returns false when a status was raised
-// before the barrier completed, or when the wait gave up.
-// With R, thread 0 then reads R's counters (and the sampling miss flag) into
-// sh.po for the whole CTA.
+// Grid barrier g on word g % 3 (zeroed by CTA 0 during phase g - 1, which
+// every CTA finishes polling before CTA 0 can reach phase g + 2): each CTA adds
+// one arrival plus its phase's queue appends with a release add; the phase is
+// complete when gridDim.x arrivals are counted, and the acquire load that sees
+// them makes every CTA's writes of the phase visible and gives the phase's
+// appends (sh.po.tail) without another read. Waiters give up after timeout_ns
+// without progress (a warp running a long local chain ticks ctl->progress).
+// Returns false when a status was raised before the barrier completed, or
+// when the wait gave up. With R, thread 0 then also reads R's other counters
+// (and the sampling miss flag) into sh.po for the whole CTA.
 __device__ bool grid_barrier(const PeelArgs& a, Shared& sh, unsigned long long& gen,
                              const RoundRec* R = nullptr) {
   __syncthreads();
   if (threadIdx.x == 0) {
     int ok = 1;
-    const unsigned long long target = (gen + 1) * gridDim.x;
+    unsigned long long* w = &a.ctl->bar_ring[gen % 3].v;
+    const unsigned long long add = 1ull + (s_app << kAppShift);
+    s_app = 0;
     // the CTA barrier above orders the CTA's writes before this release
     if (!(a.inject_stall && blockIdx.x == 0 && gen == 0))
-      asm volatile("red.release.gpu.global.add.u64 [%0], 1;" ::"l"(&a.ctl->bar_count) : "memory");
+      asm volatile("red.release.gpu.global.add.u64 [%0], %1;" ::"l"(w), "l"(add) : "memory");
     uint64_t t0 = 0;
     unsigned long long pg = 0;
     for (unsigned spins = 0;; spins++) {
-      const unsigned long long v = ld_acquire_u64(&a.ctl->bar_count);
+      const unsigned long long v = ld_acquire_u64(w);
       if (v & kAbort) {
         ok = 0;
         break;
       }
-      if (v >= target) break;
+      if ((v & kArrMask) >= gridDim.x) {
+        sh.po.tail = (v >> kAppShift) & kAppMask;
+        break;
+      }
       if ((spins & 31) == 0) {
         const uint64_t now = globaltimer_ns();
         const unsigned long long p2 = ld_relaxed_u64(&a.ctl->progress);
@@ -247,7 +263,6 @@ __device__ bool grid_barrier(const PeelArgs& a, Shared& sh, unsigned long long& 
     gen++;
     sh.flag = ok;
     if (ok && R) {
-      sh.po.tail = ld_relaxed_u64(&R->tail);
       sh.po.head = ld_relaxed_u64(&R->head);
       sh.po.found = ld_relaxed_u64(&R->found);
       sh.po.alen = ld_relaxed_u64(&R->alen);
@@ -435,6 +450,7 @@ __device__ ScanOut scan_range(const PeelArgs& a, Shared& sh, RoundRec* R, unsign
       const int exs = block_excl_scan(sh, nsl, &ntot);
       if (tid == 0) {
         unsigned long long bq = qbase + (ntot ? atomicAdd(&R->tail, (unsigned long long)ntot) : 0);
+        s_app += (unsigned long long)ntot;
         if (bq + (unsigned long long)ntot > (unsigned long long)a.qcap) {
           raise_status(a, ST_CAPACITY);
           bq = ~0ull;
@@ -501,7 +517,10 @@ __device__ __forceinline__ void append_ranges(const PeelArgs& a, const PassCtx& 
   const int tot = __shfl_sync(kFull, incl, 31);
   if (tot == 0) return;
   unsigned long long base = 0;
-  if (lane == 31) base = pc.qbase + atomicAdd(&pc.R->tail, (unsigned long long)tot);
+  if (lane == 31) {
+    base = pc.qbase + atomicAdd(&pc.R->tail, (unsigned long long)tot);
+    atomicAdd(&s_app, (unsigned long long)tot);
+  }
   base = __shfl_sync(kFull, base, 31);
   if (base + (unsigned long long)tot > (unsigned long long)a.qcap) {
     if (lane == 0) raise_status(a, ST_CAPACITY);
@@ -708,7 +727,10 @@ __device__ void drain_local(const PeelArgs& a, ShT<kSample>& sh, const PassCtx& 
       __syncwarp();
       if (lane == 0) sh.lqn[warp] = 0;
       unsigned long long base = 0;
-      if (lane == 0) base = pc.qbase + atomicAdd(&pc.R->tail, (unsigned long long)lqn);
+      if (lane == 0) {
+        base = pc.qbase + atomicAdd(&pc.R->tail, (unsigned long long)lqn);
+        atomicAdd(&s_app, (unsigned long long)lqn);
+      }
       base = __shfl_sync(kFull, base, 0);
       if (base + (unsigned long long)lqn > (unsigned long long)a.qcap) {
         if (lane == 0) raise_status(a, ST_CAPACITY);
@@ -990,6 +1012,7 @@ __global__ void __launch_bounds__(kBlock, 2) peel_bsp(PeelArgs a) {
   if (a.run_if && ld_relaxed_s32(a.run_if) == 0) return;
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   const bool lead = blockIdx.x == 0 && tid == 0;
+  if (tid == 0) s_app = 0;
   if (lane == 0) {
     sh.lqn[warp] = 0;
     sh.tr_arcs[warp] = sh.tr_decs[warp] = 0;
@@ -1009,6 +1032,7 @@ __global__ void __launch_bounds__(kBlock, 2) peel_bsp(PeelArgs a) {
         R->minkey = 0;
         R->tail = 0;
         R->head = 0;
+        a.ctl->bar_ring[r].v = 0;
         if constexpr (kSample) {
           R->rcount = 0;
           R->rqtail = 0;
@@ -1170,7 +1194,7 @@ __global__ void __launch_bounds__(kBlock, 2) peel_bsp(PeelArgs a) {
         RoundRec* P2 = a.rounds + (phase % kPhaseRing);
         const PassCtx pc{P2, qend, t, t, false, -1, nullptr, 0};
         run_apply(a, pc, a.touched, nt);
-        if (!(ok = grid_barrier(a, sh, gen, P2))) break;
+        if (!(ok = grid_barrier(a, sh, gen))) break;
         phase++;
         passes++;
         level_passes++;
@@ -1203,7 +1227,7 @@ __global__ void __launch_bounds__(kBlock, 2) peel_bsp(PeelArgs a) {
           RoundRec* P2 = a.rounds + (phase % kPhaseRing);
           const PassCtx pc{P2, qend, t, t, false, -1, nullptr, 0};
           run_apply(a, pc, Acur, (unsigned long long)la);
-          if (!(ok = grid_barrier(a, sh, gen, P2))) break;
+          if (!(ok = grid_barrier(a, sh, gen))) break;
           phase++;
           prec(3, t, (unsigned long long)la, P2, 0);
           passes++;
@@ -1240,7 +1264,7 @@ __global__ void __launch_bounds__(kBlock, 2) peel_bsp(PeelArgs a) {
             if (td) atomicAdd(&a.ctl->tr_decs, td);
           }
         }
-        if (!(ok = grid_barrier(a, sh, gen, P))) break;
+        if (!(ok = grid_barrier(a, sh, gen, W ? P : nullptr))) break;
         phase++;
         passes++;
         level_passes++;
