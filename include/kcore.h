@@ -118,10 +118,15 @@ typedef enum {
   KCORE_OPT_SAMPLE_SEED = 20,         /* Philox key of the coins (default 1) */
   KCORE_OPT_SAMPLE_CHECK = 21,        /* 1 (default) runs the final check; 0 relies on the
                                          recount test of Sec. 4.1 alone */
-  KCORE_OPT_WARP_COMBINE = 22         /* mode 2: 1 = the lanes of a warp that decrement the same
+  KCORE_OPT_WARP_COMBINE = 22,        /* mode 2: 1 = the lanes of a warp that decrement the same
                                          vertex in one step send one atomic of their count (warp
                                          aggregation, the GPU alternative to sampling for hub
                                          contention); 0 (default) = one atomic per arc */
+  KCORE_OPT_PRECHECK_ITEMS = 23       /* mode 2: a subround whose queue range gives every warp at
+                                         least this many items reads d~ before decrementing (sparing
+                                         atomics on neighbours already peeled); shorter subrounds
+                                         decrement unconditionally (sparing a dependent read).
+                                         Default 64; 0 = always read first */
 } kcore_option;
 
 /* Counters of the last decomposition, or of the last CSR check (the three

@@ -22,8 +22,8 @@ struct kcore_ctx {
   size_t ws_bytes = 0;
   bool ws_external = false;
   std::string err;
-  int64_t opt[23] = {0, 0, 0, -1, 2000, 1, 2048, 0, 0, 192, 64, 1024, -1, 0, 32, 0, 1,
-                     0, 0, -1, 1, 1, 0};  // indexed by kcore_option
+  int64_t opt[24] = {0, 0, 0, -1, 2000, 1, 2048, 0, 0, 192, 64, 1024, -1, 0, 32, 0, 1,
+                     0, 0, -1, 1, 1, 0, 64};  // indexed by kcore_option
   cudaStream_t last_stream = nullptr;
   bool pending = false;
   kc::PeelCtl* last_ctl = nullptr;
@@ -239,7 +239,7 @@ kcore_status kcore_destroy(kcore_handle h) {
 const char* kcore_last_error(kcore_handle h) { return h ? h->err.c_str() : "null handle"; }
 
 kcore_status kcore_set_option(kcore_handle h, kcore_option opt, int64_t value) {
-  if (!h || (int)opt < 0 || (int)opt > 22) return KCORE_ERR_INVALID;
+  if (!h || (int)opt < 0 || (int)opt > 23) return KCORE_ERR_INVALID;
   switch (opt) {
     case KCORE_OPT_BATCH_BLOCK:
       if (value != 256 && value != 512 && value != 1024)
@@ -272,6 +272,9 @@ kcore_status kcore_set_option(kcore_handle h, kcore_option opt, int64_t value) {
       if (value < -1 || value > INT32_MAX) return fail(h, KCORE_ERR_INVALID, "sample threshold in [-1, 2^31 - 1]");
       break;
     case KCORE_OPT_SAMPLE_SEED:
+      break;
+    case KCORE_OPT_PRECHECK_ITEMS:
+      if (value < 0 || value > (1 << 20)) return fail(h, KCORE_ERR_INVALID, "precheck items in [0, 2^20]");
       break;
     case KCORE_OPT_IDLE_SLEEP_NS:
     case KCORE_OPT_POLL_SLEEP_NS:
@@ -313,7 +316,7 @@ kcore_status kcore_set_option(kcore_handle h, kcore_option opt, int64_t value) {
 }
 
 kcore_status kcore_get_option(kcore_handle h, kcore_option opt, int64_t* value) {
-  if (!h || !value || (int)opt < 0 || (int)opt > 22) return KCORE_ERR_INVALID;
+  if (!h || !value || (int)opt < 0 || (int)opt > 23) return KCORE_ERR_INVALID;
   *value = h->opt[opt];
   return KCORE_OK;
 }
@@ -412,6 +415,7 @@ kcore_status peel_call(kcore_ctx* h, int64_t n, int64_t m, const int64_t* offset
   a.kprime = threshold ? std::max<int32_t>(kprime, 0) : 0;
   a.size_out = (long long*)size_out;
   a.combine = mode == 2 && h->opt[KCORE_OPT_WARP_COMBINE] != 0 ? 1 : 0;
+  a.precheck_items = (int)h->opt[KCORE_OPT_PRECHECK_ITEMS];
 
   if (mode != 1 && m >= ((int64_t)1 << 40))
     return fail(h, KCORE_ERR_INVALID, "the bulk-synchronous modes take at most 2^40 arcs");

@@ -103,6 +103,7 @@ struct PeelArgs {
   unsigned long long* trace;  // optional: kTraceFields words per round (nullptr = off)
   int trace_phases;           // bulk-synchronous mode: one trace record per phase instead of per level
   int local_batches;          // bulk-synchronous mode: local batches per chunk taken
+  int precheck_items;         // bulk-synchronous mode: per-warp share of a pass from which d~ is read first
   // k'-core query (bulk-synchronous mode only): one peel at level kprime - 1
   // taking every vertex below kprime; core[] receives 1 (in the k'-core) or 0
   int threshold;
@@ -120,6 +121,7 @@ struct PeelArgs {
   // heavy subrounds over a short active list use Algorithm 2's batch update
   // (counts in hcnt, zero at launch and left zero)
   int hybrid;
+
   // sampling (Sec. 4.1, Algorithms 4-5; bulk-synchronous mode): a vertex in
   // sample mode keeps -1 - D in deg[] (D: its induced degree at InitSampler).
   // scnt: heads since InitSampler; stamp: the pass that traverses a vertex's

@@ -131,6 +131,7 @@ extern "C" kcore_status kcore_decompose_static(int64_t n, int64_t m, const int64
     int grid = (int)std::max<long long>(1, std::min(want, gmax));
     a.take_div = grid * (kc::bsp_block_size() / 32);
     a.local_batches = 8;
+    a.precheck_items = 64;
     // the array keeps the previous call's contents: clear what must start at
     // zero (control block, this call's round records); the bulk-synchronous
     // peel reads only queue slots written earlier in the same call

@@ -47,7 +47,6 @@ constexpr int kTile = 8;   // active-list entries per thread per scan tile
 constexpr int kExpand = 4; // staged frontier vertices per thread per expansion round
 constexpr int kIlp = 8;    // arcs per lane in flight
 constexpr int kTake = 32;  // queue items per chunk of a warp's share
-constexpr int kPrecheckShare = 64;  // per-warp share from which a pass reads d~ before decrementing
 constexpr int kLenShift = 40;  // item = first arc | length << 40
 constexpr unsigned long long kArcMask = (1ull << kLenShift) - 1;
 // barrier word: arrivals in bits 0..30, the phase's queue appends in bits
@@ -1238,10 +1237,10 @@ __global__ void __launch_bounds__(kBlock, 2) peel_bsp(PeelArgs a) {
         }
         reset_next();
         RoundRec* P = a.rounds + (phase % kPhaseRing);
-        // a pass whose per-warp share is at least kPrecheckShare items is
+        // a pass whose per-warp share is at least a.precheck_items items is
         // throughput-bound (measured: kNN's largest level 1,700 items per
         // warp; R-MAT passes a few)
-        const bool pre = (qend - qb) >= (unsigned long long)kPrecheckShare * gridDim.x * kWarps;
+        const bool pre = (qend - qb) >= (unsigned long long)a.precheck_items * gridDim.x * kWarps;
         const PassCtx pc{P, qend, t, a.threshold ? 0 : t, pre, W ? hi_w : -1, const_cast<int*>(Acur),
                          (unsigned long long)(la + near_extra)};
         run_pass<kWindow, false, kCombine>(a, sh, pc, qb, qend, items, local_items, local_batches);

@@ -421,6 +421,7 @@ kcore_status kcore_server_poll(kcore_server s, int64_t* tickets_out, int32_t* km
     int grid = (int)std::max<long long>(1, std::min(want, gmax));
     a.take_div = grid * (kc::bsp_block_size() / 32);
     a.local_batches = 8;
+    a.precheck_items = 64;
     e = cudaMemsetAsync(ws, 0, L.deg, s->large);
     if (e == cudaSuccess) e = kc::bsp_launch(a, grid, s->large);
     if (e == cudaSuccess) e = cudaEventRecord(r.ev, s->large);

@@ -332,17 +332,19 @@ def test_level_window(W):
         assert rebuilds >= len(levels) // 2  # a rebuild (almost) every level
 
 
-def test_batch_update_of_heavy_subrounds():
+@pytest.mark.parametrize("opts", [dict(), dict(precheck_items=0), dict(precheck_items=1 << 20)])
+def test_batch_update_of_heavy_subrounds(opts):
     """KCORE_OPT_BATCH_UPDATE: heavy subrounds count decrements with
     reductions and apply them walking the active list; the coreness is the
-    oracle's on graphs with dense cores, hubs, long paths and many levels."""
+    oracle's on graphs with dense cores, hubs, long paths and many levels,
+    whether the other subrounds read d~ first or not."""
     n0 = 40000
     s, d = gg.rmat_n(n0, 600000, seed=8)
     n, s2, d2 = gg.disjoint_union((n0, s, d), gg.complete(200), gg.staircase(150), gg.star(5000),
                                   gg.path(3000), (9, np.zeros(0, np.int32), np.zeros(0, np.int32)))
     off, adj = _csr(n, s2, d2)
     want = oracle.bz(n, off, adj)
-    with KCore(0, batch_update=1) as k:
+    with KCore(0, batch_update=1, **opts) as k:
         assert_parity(k, n, off, adj, want)
         for i in range(len(CLOSED)):
             nn, ss, dd = CLOSED[i]
