@@ -279,7 +279,11 @@ static int bits_for(long long n) {
 CsrLayout csr_layout(long long n, long long E, int sms, long long max_graph_n) {
   CsrLayout L{};
   long long N = 2 * E;
-  long long G = (long long)sms * 2;
+  // four CTAs per SM: the downsweep's 64 registers x 256 threads allow four
+  // resident (45 KB of shared memory each); with two the scatter was latency
+  // bound (R-MAT 24: 56.8 -> 37.7 ms per build; five, forced by launch bounds,
+  // spill and give 40.0 ms)
+  long long G = (long long)sms * 4;
   long long tiles = (N + kTile - 1) / kTile;
   if (tiles < G) G = tiles < 1 ? 1 : tiles;
   L.grid = (int)G;
