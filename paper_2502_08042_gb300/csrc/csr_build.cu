@@ -9,7 +9,7 @@
 //   2. stable LSD radix sort of the keys over their 2B significant bits, 8-bit
 //      digits. Each CTA owns a contiguous chunk; a pass is an upsweep (digit
 //      histogram per CTA), a scan of the 256 x CTAs histogram, and a downsweep
-//      that ranks each 4096-key tile in shared memory (warp match for the
+//      that ranks each 2,048-key tile in shared memory (warp match for the
 //      within-iteration rank) and writes runs of equal digits contiguously.
 //   3. unique + emit: keys equal to their predecessor are dropped; the rest
 //      are written in order as adj[] (low B bits), and the first arc of each
@@ -25,8 +25,8 @@
 namespace kc {
 
 constexpr int kCsrBlock = 256;
-constexpr int kKeysPerThread = 16;
-constexpr int kTile = kCsrBlock * kKeysPerThread;  // 4096
+constexpr int kKeysPerThread = 8;
+constexpr int kTile = kCsrBlock * kKeysPerThread;  // 2048
 constexpr unsigned long long kSentinel = ~0ull;
 
 // Keys (source << Bd) | target. Single graph: ids in [0, n), source = id.
@@ -113,7 +113,7 @@ __global__ void __launch_bounds__(1024) scan_u32_to_u64(const unsigned* in, unsi
 
 // Stable scatter of one radix pass. Each CTA walks its chunk tile by tile, in
 // order; offs[d * G + g] is where its first key of digit d goes.
-__global__ void __launch_bounds__(kCsrBlock) rs_downsweep(const unsigned long long* in,
+__global__ void __launch_bounds__(kCsrBlock, 6) rs_downsweep(const unsigned long long* in,
                                                           unsigned long long* out, long long N,
                                                           long long chunk, int shift,
                                                           const unsigned long long* offs) {
@@ -279,11 +279,11 @@ static int bits_for(long long n) {
 CsrLayout csr_layout(long long n, long long E, int sms, long long max_graph_n) {
   CsrLayout L{};
   long long N = 2 * E;
-  // four CTAs per SM: the downsweep's 64 registers x 256 threads allow four
-  // resident (45 KB of shared memory each); with two the scatter was latency
-  // bound (R-MAT 24: 56.8 -> 37.7 ms per build; five, forced by launch bounds,
-  // spill and give 40.0 ms)
-  long long G = (long long)sms * 4;
+  // six CTAs per SM, each sorting 2,048-key tiles (28 KB of shared memory,
+  // at most 40 registers): the scatter is latency bound, so resident warps
+  // count. Measured on R-MAT 24 (ms per build): 2 CTAs x 4,096-key tiles 56.8,
+  // 4 x 4,096 37.7, 6 x 2,048 35.6, 7 x 2,048 38.2, 8 x 1,536 37.3
+  long long G = (long long)sms * 6;
   long long tiles = (N + kTile - 1) / kTile;
   if (tiles < G) G = tiles < 1 ? 1 : tiles;
   L.grid = (int)G;
