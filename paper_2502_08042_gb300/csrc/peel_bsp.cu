@@ -12,9 +12,8 @@
 //            collects its vertices.
 //   pass   - one subround over the queue range appended before it: each warp
 //            takes its own share of the items, 32 at a time, and processes
-//            their arcs edge-balanced. A
-//            decrement of a neighbour above k that returns k+1 is the crossing
-//            of Algorithm 3: the neighbour gets coreness k and is processed by
+//            their arcs edge-balanced. A decrement of a neighbour above k that
+//            returns k+1 is the crossing of Algorithm 3: the neighbour gets coreness k and is processed by
 //            the same warp in the same pass if its list fits one slice and the
 //            warp's local queue has room (the local FIFO of vertical
 //            granularity control, Sec. 4.2); otherwise its slices go to the
@@ -25,12 +24,16 @@
 // pass ends at the barrier. A queue item is an arc range (first arc,
 // length), so processing it needs no offset lookup. Each phase counts its own
 // appends, which land after everything appended before the phase, so the next
-// range is known to every CTA after the barrier. Every vertex is appended at
+// range is known to every CTA from the barrier word that ends the phase (it
+// carries the appends with the arrivals). Every vertex is appended at
 // most once over the whole run, so the queue never wraps. A warp runs at most
 // `local_batches` batches from its local queue per chunk it takes and then
 // moves the rest to the queue: a large cascade is shared by all warps in the
-// next pass instead of being walked by the warp that started it. Every wait is
-// bounded by the handle's time limit (KCORE_ERR_TIMEOUT).
+// next pass instead of being walked by the warp that started it. Heavy
+// subrounds may instead count their decrements and apply them in a second
+// phase (Algorithm 2's batch update); the offline peel, the level window,
+// sampling and warp aggregation are variants compiled apart (see the kernel).
+// Every wait is bounded by the handle's time limit (KCORE_ERR_TIMEOUT).
 #include <climits>
 #include <type_traits>
 
@@ -713,8 +716,8 @@ __device__ void process_items(const PeelArgs& a, ShT<kSample>& sh, const PassCtx
   __syncwarp();
 }
 
-// Runs up to `budget` batches from the warp's local queue (vertices that
-// crossed during this pass), then moves what is left to the queue.
+// Runs up to a.local_batches batches from the warp's local queue (vertices
+// that crossed during this pass), then moves what is left to the queue.
 template <bool kWin, bool kSample = false, bool kCombine = false>
 __device__ void drain_local(const PeelArgs& a, ShT<kSample>& sh, const PassCtx& pc, int warp, int lane,
                             long long& local_items, unsigned& local_batches) {
