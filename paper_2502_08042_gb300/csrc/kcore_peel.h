@@ -52,13 +52,11 @@ struct PeelCtl {
   char pad3[80];
   // bulk-synchronous mode: the grid barrier's words (barrier g uses word
   // g % 3: arrivals, the phase's queue appends, the abort bit; reset two
-  // phases ahead), queue tail, subround passes and barriers taken
+  // phases ahead), subround passes and barriers taken
   struct {
     unsigned long long v;
     char pad[120];
   } bar_ring[3];
-  unsigned long long qtail;
-  char pad6[120];
   long long passes, barriers;
   unsigned long long tr_arcs, tr_decs;  // bulk-synchronous mode, with tracing: running sums
   unsigned long long crossed;           // k'-core query: vertices removed by a decrement
