@@ -60,3 +60,52 @@ def test_smoke_graph_is_well_formed():
     off, adj = oracle.build_csr(n, s, d)
     assert len(off) == n + 1 and oracle.check_simple(n, off, adj) == 0
     assert int(oracle.bz(n, off, adj).max()) >= 40
+
+
+def _header_text():
+    text = open(os.path.join(ROOT, "include", "kcore.h")).read()
+    return re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+
+
+def test_binding_option_names_match_the_header():
+    """Every KCORE_OPT_* of the header has the binding's name and value, and
+    the binding names no option the header lacks."""
+    from paper_2502_08042_gb300 import kcore
+    enum = re.search(r"typedef enum\s*\{(.*?)\}\s*kcore_option\s*;", _header_text(), flags=re.S).group(1)
+    opts = {m.group(1).lower(): int(m.group(2)) for m in re.finditer(r"KCORE_OPT_(\w+)\s*=\s*(\d+)", enum)}
+    assert opts == kcore.OPTIONS
+    assert sorted(opts.values()) == list(range(len(opts)))  # dense, no gaps
+
+
+def test_stats_struct_matches_the_header():
+    """The binding's kcore_stats mirror has the header's fields in order, all
+    int64, so ctypes reads the same bytes the library writes."""
+    body = re.search(r"typedef struct\s*\{(.*?)\}\s*kcore_stats\s*;", _header_text(), flags=re.S).group(1)
+    fields = re.findall(r"int64_t\s+(\w+)\s*;", body)
+    assert [name for name, _ in _native.Stats._fields_] == fields
+    assert ctypes.sizeof(_native.Stats) == 8 * len(fields)
+
+
+def test_status_codes_match_the_header():
+    from paper_2502_08042_gb300 import kcore
+    enum = re.search(r"typedef enum\s*\{(.*?)\}\s*kcore_status\s*;", _header_text(), flags=re.S).group(1)
+    codes = {int(m.group(2)): m.group(1) for m in re.finditer(r"KCORE_(?:ERR_)?(\w+)\s*=\s*(\d+)", enum)}
+    for value, name in codes.items():
+        assert kcore.STATUS[value].upper() == name, (value, name)
+
+
+_CTYPES = {"int64_t": ctypes.c_int64, "int32_t": ctypes.c_int32, "int": ctypes.c_int, "size_t": ctypes.c_size_t,
+           "double": ctypes.c_double}
+
+
+def _struct_fields(name):
+    body = re.search(r"typedef struct\s*\{(.*?)\}\s*" + name + r"\s*;", _header_text(), flags=re.S).group(1)
+    return [(m.group(2), m.group(1)) for m in re.finditer(r"(int64_t|int32_t|int|size_t|double)\s+(\w+)\s*;", body)]
+
+
+def test_other_mirrored_structs_match_the_header():
+    for cname, mirror in (("kcore_batch_tuning", _native.BatchTuning), ("kcore_server_config", _native.ServerConfig)):
+        fields = _struct_fields(cname)
+        assert [n for n, _ in mirror._fields_] == [n for n, _ in fields], cname
+        for (n, ct), (_, cty) in zip(mirror._fields_, fields):
+            assert ctypes.sizeof(ct) == ctypes.sizeof(_CTYPES[cty]), (cname, n)
