@@ -80,7 +80,7 @@ def test_binding_option_names_match_the_header():
 def test_stats_struct_matches_the_header():
     """The binding's kcore_stats mirror has the header's fields in order, all
     int64, so ctypes reads the same bytes the library writes."""
-    body = re.search(r"typedef struct\s*\{(.*?)\}\s*kcore_stats\s*;", _header_text(), flags=re.S).group(1)
+    body = re.search(r"typedef struct\s*\{([^{}]*)\}\s*kcore_stats\s*;", _header_text()).group(1)
     fields = re.findall(r"int64_t\s+(\w+)\s*;", body)
     assert [name for name, _ in _native.Stats._fields_] == fields
     assert ctypes.sizeof(_native.Stats) == 8 * len(fields)
@@ -99,7 +99,7 @@ _CTYPES = {"int64_t": ctypes.c_int64, "int32_t": ctypes.c_int32, "int": ctypes.c
 
 
 def _struct_fields(name):
-    body = re.search(r"typedef struct\s*\{(.*?)\}\s*" + name + r"\s*;", _header_text(), flags=re.S).group(1)
+    body = re.search(r"typedef struct\s*\{([^{}]*)\}\s*" + name + r"\s*;", _header_text()).group(1)
     return [(m.group(2), m.group(1)) for m in re.finditer(r"(int64_t|int32_t|int|size_t|double)\s+(\w+)\s*;", body)]
 
 
