@@ -113,7 +113,8 @@ typedef enum {
    * exact; kcore_stats.sample_reruns says whether it happened). */
   KCORE_OPT_SAMPLING = 17,            /* 0 (default) off, 1 on */
   KCORE_OPT_SAMPLE_MU = 18,           /* heads per sampling period (1 .. 2^24); 0 = auto:
-                                         ceil(4 (c + 2) ln n) with c = 8 (Theorem 2) */
+                                         ceil(4 (c + 2) ln n) with c = 8 (the sampling
+                                         theorem of Sec. 4.1) */
   KCORE_OPT_SAMPLE_THRESHOLD = 19,    /* degree above which a vertex may be sampled; -1 = auto (8 mu) */
   KCORE_OPT_SAMPLE_SEED = 20,         /* Philox key of the coins (default 1) */
   KCORE_OPT_SAMPLE_CHECK = 21,        /* 1 (default) runs the final check; 0 relies on the

@@ -158,7 +158,7 @@ bool sampling_on(const kcore_ctx* h, bool threshold) {
   return h->opt[KCORE_OPT_SAMPLING] != 0 && !threshold && effective_mode(h) == 2 &&
          h->opt[KCORE_OPT_LEVEL_WINDOW] == 0;
 }
-// mu of Theorem 2 with c = 8 unless set: ceil(4 (c + 2) ln n).
+// mu of the sampling theorem (Sec. 4.1) with c = 8 unless set: ceil(4 (c + 2) ln n).
 int sample_mu(const kcore_ctx* h, long long n) {
   if (h->opt[KCORE_OPT_SAMPLE_MU] > 0) return (int)h->opt[KCORE_OPT_SAMPLE_MU];
   return (int)std::ceil(40.0 * std::log((double)std::max(n, 2ll)));
