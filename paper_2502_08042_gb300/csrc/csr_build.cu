@@ -10,7 +10,8 @@
 //      digits. Each CTA owns a contiguous chunk; a pass is an upsweep (digit
 //      histogram per CTA), a scan of the 256 x CTAs histogram, and a downsweep
 //      that ranks each 2,048-key tile in shared memory (warp match for the
-//      within-iteration rank) and writes runs of equal digits contiguously.
+//      within-iteration rank) and writes runs of equal digits contiguously,
+//      while the next tile arrives by asynchronous copy (cp.async).
 //   3. unique + emit: keys equal to their predecessor are dropped; the rest
 //      are written in order as adj[] (low B bits), and the first arc of each
 //      source vertex fixes offsets[] (vertices without arcs take the next
@@ -118,6 +119,7 @@ __global__ void __launch_bounds__(kCsrBlock, 6) rs_downsweep(const unsigned long
                                                           long long chunk, int shift,
                                                           const unsigned long long* offs) {
   __shared__ unsigned long long buf[kTile];
+  __shared__ __align__(16) unsigned long long stage[kTile];  // the next tile, copied asynchronously
   __shared__ unsigned wbase[kCsrBlock / 32][256];
   __shared__ unsigned local_off[256];
   __shared__ unsigned tile_cnt[256];
@@ -127,19 +129,37 @@ __global__ void __launch_bounds__(kCsrBlock, 6) rs_downsweep(const unsigned long
   const int G = gridDim.x;
   run[tid] = offs[(long long)tid * G + blockIdx.x];
   long long lo = (long long)blockIdx.x * chunk, hi = min(N, lo + chunk);
+  // 16-byte asynchronous copies of a tile's keys into `stage` (pairs of keys;
+  // a last odd key is copied with its neighbour, which lies inside the
+  // 256-byte-aligned key buffer and is not used)
+  auto prefetch = [&](long long t0) {
+    const long long tn = min((long long)kTile, hi - t0);
+    const unsigned sbase = (unsigned)__cvta_generic_to_shared(stage);
+    for (int c = tid; 2 * c < tn; c += kCsrBlock)
+      asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(sbase + 16u * c), "l"(in + t0 + 2 * c)
+                   : "memory");
+    asm volatile("cp.async.commit_group;" ::: "memory");
+  };
+  if (lo < hi) prefetch(lo);
   for (long long ts = lo; ts < hi; ts += kTile) {
     const long long tn = min((long long)kTile, hi - ts);
     for (int i = tid; i < (kCsrBlock / 32) * 256; i += kCsrBlock) (&wbase[0][0])[i] = 0;
+    asm volatile("cp.async.wait_all;" ::: "memory");
     __syncthreads();
     unsigned long long k[kKeysPerThread];
     int dg[kKeysPerThread];
 #pragma unroll
     for (int it = 0; it < kKeysPerThread; it++) {
       long long j = (long long)warp * (kKeysPerThread * 32) + it * 32 + lane;
+      k[it] = j < tn ? stage[j] : 0;
+    }
+    __syncthreads();  // the stage is read: copy the next tile into it
+    if (ts + kTile < hi) prefetch(ts + kTile);
+#pragma unroll
+    for (int it = 0; it < kKeysPerThread; it++) {
+      long long j = (long long)warp * (kKeysPerThread * 32) + it * 32 + lane;
       dg[it] = 256;  // invalid lane
-      k[it] = 0;
       if (j < tn) {
-        k[it] = in[ts + j];
         dg[it] = digit_of(k[it], shift);
         atomicAdd(&wbase[warp][dg[it]], 1u);
       }
@@ -279,11 +299,14 @@ static int bits_for(long long n) {
 CsrLayout csr_layout(long long n, long long E, int sms, long long max_graph_n) {
   CsrLayout L{};
   long long N = 2 * E;
-  // six CTAs per SM, each sorting 2,048-key tiles (28 KB of shared memory,
-  // at most 40 registers): the scatter is latency bound, so resident warps
-  // count. Measured on R-MAT 24 (ms per build): 2 CTAs x 4,096-key tiles 56.8,
-  // 4 x 4,096 37.7, 6 x 2,048 35.6, 7 x 2,048 38.2, 8 x 1,536 37.3
-  long long G = (long long)sms * 6;
+  // five CTAs per SM, each sorting 2,048-key tiles with the next tile copied
+  // into shared memory while the current one is ranked (44 KB of shared
+  // memory, which admits five; 40 registers, held to six CTAs' worth by the
+  // kernel's launch bounds): the scatter is latency bound, so resident warps and
+  // loads in flight count. Measured on R-MAT 24 (ms per build): 2 CTAs x
+  // 4,096-key tiles 56.8, 4 x 4,096 37.7, 6 x 2,048 35.6, 7 x 2,048 38.2,
+  // 8 x 1,536 37.3; with the asynchronous copy 5 x 2,048 31.0, 4 x 2,048 31.8
+  long long G = (long long)sms * 5;
   long long tiles = (N + kTile - 1) / kTile;
   if (tiles < G) G = tiles < 1 ? 1 : tiles;
   L.grid = (int)G;
