@@ -77,7 +77,8 @@ typedef enum {
                                     barrier (mode 2), so every device wait must run out its
                                     time limit and the call ends with KCORE_ERR_TIMEOUT */
   KCORE_OPT_TRACE = 8,           /* 1 records a per-round timeline (kcore_get_trace); 2 (modes 2
-                                    and 3) one record per phase instead */
+                                    and 3) one record per phase instead; calls with
+                                    KCORE_OPT_SAMPLING record none */
   KCORE_OPT_IDLE_SLEEP_NS = 9,   /* nanosleep of a warp waiting for work (0 .. 100000) */
   KCORE_OPT_POLL_SLEEP_NS = 10,  /* nanosleep of a CTA's round-end poller (0 .. 100000) */
   KCORE_OPT_BATCH_BLOCK = 11,    /* batched peel: threads per CTA (256, 512 or 1024; default 1024) */

@@ -478,7 +478,7 @@ kcore_status peel_call(kcore_ctx* h, int64_t n, int64_t m, const int64_t* offset
     if (e != cudaSuccess) return cuda_fail(h, e, "peel launch");
     h->last_ctl = a.ctl;
   }
-  h->last_trace = a.trace;
+  h->last_trace = sample ? nullptr : a.trace;  // the sampled peel records no timeline
   h->last_trace_phases = a.trace_phases != 0;
   h->last_max_rounds = L.max_rounds;
   h->last_grid = (int)grid;
