@@ -225,23 +225,25 @@ def job_throughput(units_per_rank: float, ws: int, max_ms: float) -> float:
     return ws * units_per_rank / (max_ms / 1e3)
 
 
-def cpu_oracle_baseline(scale: int = 22, reps: int = 1):
-    """The oracle (sequential Batagelj-Zaversnik in C, one host core) on an
-    R-MAT graph of the same generator and parameters at a smaller scale."""
-    import graphgen as gg
+def cpu_oracle_baseline(n: int, off, adj, what: str, warmup: int = 1, runs: int = 5):
+    """The oracle (sequential Batagelj-Zaversnik in C, one host core) on the
+    very CSR the GPU decomposes, with the paper's protocol (Sec. 6: one
+    warm-up, then the mean of five runs; the minimum is reported beside it)."""
     import oracle
-    s, d = gg.rmat(scale, 16, seed=1, perm_seed=2)
-    n = 1 << scale
-    off, adj = oracle.build_csr(n, s, d)
+    for _ in range(warmup):
+        oracle.bz(n, off, adj)
     ts = []
-    for _ in range(reps):
+    for _ in range(runs):
         t0 = time.perf_counter()
         oracle.bz(n, off, adj)
         ts.append(time.perf_counter() - t0)
-    t = min(ts)
-    return {"value": (len(adj) // 2) / t, "unit": UNIT, "cores": 1, "kind": "oracle",
-            "sample": f"Batagelj-Zaversnik on R-MAT scale {scale} (same generator, edge factor 16; "
-                      f"{len(adj) // 2} undirected edges), best of {reps}, {t:.2f} s"}
+    mean, best = sum(ts) / len(ts), min(ts)
+    mu = len(adj) // 2
+    return {"value": mu / mean, "unit": UNIT, "cores": 1, "kind": "oracle",
+            "value_min_time": mu / best, "s_mean": mean, "s_min": best,
+            "sample": f"Batagelj-Zaversnik on the bench's own graph ({what}, {mu} undirected edges), "
+                      f"{warmup} warm-up + mean of {runs} runs ({mean:.2f} s mean, {best:.2f} s min), "
+                      f"one host core"}
 
 
 def run_kquery(args):
@@ -334,15 +336,21 @@ def run_kquery(args):
 
 
 def run_reference(args):
+    """The oracle on the GPU arm's own workload: each step is one
+    Batagelj-Zaversnik decomposition (one host core) of the same graph, from
+    the same generator, built by the oracle's CSR builder (not timed)."""
     ws, rank, local = dist_env()
     if rank != 0:
         return
-    import graphgen as gg
     import oracle
-    scale = 20
-    s, d = gg.rmat(scale, 16, seed=1, perm_seed=2)
-    n = 1 << scale
+    w = WORKLOADS[args.workload]
+    if w["kind"] not in ("rmat", "knn", "er"):
+        emit({"impl": "reference", "unavailable": f"no CPU reference arm for the {args.workload} workload"})
+        return
+    n, s, d = make_edges(w)
+    E = len(s)
     off, adj = oracle.build_csr(n, s, d)
+    del s, d
     mu = len(adj) // 2
     for _ in range(args.warmup):
         oracle.bz(n, off, adj)
@@ -351,14 +359,15 @@ def run_reference(args):
         oracle.bz(n, off, adj)
     dt = time.perf_counter() - t0
     value = mu * args.steps / dt
-    sample = (f"each step: Batagelj-Zaversnik on R-MAT scale {scale} (same generator as "
-              f"{args.workload}, {mu} undirected edges), 1 host core")
+    sample = (f"each step: Batagelj-Zaversnik on the whole {workload_name(args.workload, w)} graph "
+              f"({mu} undirected edges), 1 host core")
     emit({
         "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": dt * 1e3 / args.steps,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "int32",
         "data": "synthetic",
-        "config": {"workload": f"{args.workload} (CPU sample: rmat{scale})", "parallelism": "none"},
+        "config": {"workload": workload_name(args.workload, w), "n": n, "edges_drawn": E,
+                   "undirected_edges": mu, "arcs": len(adj), "parallelism": "none"},
         "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample},
         "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     })
@@ -471,9 +480,14 @@ def run_gpu(args):
             tj = json.load(f)
         if tj.get("workload") == args.workload and tj.get("kernel_rev") == kernel_revision(ksrc):
             traffic = tj.get("dram_bytes_per_launch")
+    # the synchronisation floor: grid barriers taken x the measured latency of
+    # one barrier on the same grid (tail phases end at a CTA barrier instead)
+    bar_ns = k.barrier_latency_ns(grid=st["grid"], iters=2000)
+    sync_floor = {"barriers": st["barriers"], "barrier_us": bar_ns / 1e3,
+                  "ms": st["barriers"] * bar_ns / 1e6, "tail_phases": st["tail_phases"]}
     cpu = None
     if not args.no_cpu_baseline:
-        cpu = cpu_oracle_baseline()
+        cpu = cpu_oracle_baseline(n, off.cpu().numpy(), adj.cpu().numpy(), workload_name(args.workload, w))
     out = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True,
@@ -483,7 +497,8 @@ def run_gpu(args):
             "n": n, "edges_drawn": E, "undirected_edges": mu, "arcs": m, "kmax": int(kmax.item()),
             "rounds": st["rounds"], "empty_rounds": st["empty_rounds"], "grid": st["grid"],
             "sync_mode": st["sync_mode"], "slice_arcs": st["slice_arcs"], "passes": st["passes"],
-            "barriers": st["barriers"],
+            "barriers": st["barriers"], "tail_phases": st["tail_phases"],
+            "tail_episodes": st["tail_episodes"],
             **({"sampling": {key: st[key] for key in ("sample_vertices", "sample_recounts", "sample_bag",
                                                        "sample_failed_validations", "sample_heads",
                                                        "sample_reruns")},
@@ -504,6 +519,8 @@ def run_gpu(args):
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                      "frac": achieved / peak, "traffic": traffic, "peak_kind": peak_kind,
                      "algorithmic_bytes": bmin, "kernel": kname},
+        "sync_floor_ms": sync_floor["ms"],
+        "sync_floor": sync_floor,
         "e2e": e2e,
         # a sampled step is the sampled peel, the two check kernels and the
         # rerun kernel (which returns at once when not needed)

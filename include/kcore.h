@@ -124,11 +124,23 @@ typedef enum {
                                          vertex in one step send one atomic of their count (warp
                                          aggregation, the GPU alternative to sampling for hub
                                          contention); 0 (default) = one atomic per arc */
-  KCORE_OPT_PRECHECK_ITEMS = 23       /* mode 2: a subround whose queue range gives every warp at
+  KCORE_OPT_PRECHECK_ITEMS = 23,      /* mode 2: a subround whose queue range gives every warp at
                                          least this many items reads d~ before decrementing (sparing
                                          atomics on neighbours already peeled); shorter subrounds
                                          decrement unconditionally (sparing a dependent read).
                                          Default 64; 0 = always read first */
+  /* Tail mode (mode 2, not with LEVEL_WINDOW, not the k'-core query): the
+   * many short phases of a long peel (Algorithm 1's subrounds of a few
+   * vertices, scans of a short active list; Sec. 3.2 counts each as a
+   * synchronisation of the burdened span) run on one CTA, closed by a CTA
+   * barrier instead of the grid barrier. The other CTAs park on a bounded
+   * wait (KCORE_OPT_TIMEOUT_MS, KCORE_ERR_TIMEOUT) until CTA 0 meets a
+   * larger phase and hands them the loop state. */
+  KCORE_OPT_TAIL_ITEMS = 24,          /* a subround pass of at most this many work items runs on one
+                                         CTA (0 .. 2^30; 0 = never) */
+  KCORE_OPT_TAIL_ENTRIES = 25,        /* a scan of at most this many active-list entries runs on one
+                                         CTA (0 .. 2^31 - 2; 0 = never) */
+  KCORE_OPT_PARK_SLEEP_NS = 26        /* nanosleep of a parked CTA between polls (0 .. 100000) */
 } kcore_option;
 
 /* Counters of the last decomposition, or of the last CSR check (the three
@@ -158,6 +170,8 @@ typedef struct {
   int64_t invalid_vertex;  /* kcore_validate_csr: the vertex of that failure */
   int64_t invalid_arc;     /* kcore_validate_csr: the failing arc (index into adj); for codes 1
                               and 2 the offending offset value instead */
+  int64_t tail_phases;     /* mode 2: phases run by one CTA in tail mode (not counted in barriers) */
+  int64_t tail_episodes;   /* mode 2: times the grid parked while one CTA ran tail phases */
 } kcore_stats;
 
 /* Creates a handle on `device` (CUDA ordinal). The handle owns a workspace
@@ -324,6 +338,38 @@ kcore_status kcore_autotune_batched(kcore_handle h, int64_t num_graphs, int64_t 
                                     int32_t* kmax_out, int32_t repeats, kcore_batch_tuning* best_out,
                                     kcore_stream_t stream);
 
+/* Result of kcore_autotune: the option values chosen (see kcore_option). */
+typedef struct {
+  int32_t sync_mode;      /* KCORE_OPT_SYNC_MODE */
+  int32_t batch_update;   /* KCORE_OPT_BATCH_UPDATE */
+  int32_t warp_combine;   /* KCORE_OPT_WARP_COMBINE */
+  int32_t ctas_per_sm;    /* KCORE_OPT_CTAS_PER_SM (0 = occupancy maximum) */
+  int64_t tail_items;     /* KCORE_OPT_TAIL_ITEMS */
+  int64_t tail_entries;   /* KCORE_OPT_TAIL_ENTRIES */
+  int64_t precheck_items; /* KCORE_OPT_PRECHECK_ITEMS */
+  int64_t local_batches;  /* KCORE_OPT_LOCAL_BATCHES */
+  int32_t candidates;     /* schedules timed */
+  double ms;              /* best time of one decomposition with the chosen schedule */
+} kcore_tuning;
+
+/* Autotuner of the single-graph peel's schedule (Algorithm 1's subround and
+ * round scheduling, Sec. 3.2: how the many synchronisations of a long peel
+ * are paid). Times each candidate schedule -- the bulk-synchronous default;
+ * tail mode at a few thresholds, including the whole peel on one CTA; no
+ * batch update; d~ read first in shorter subrounds; shorter local chains;
+ * warp aggregation; one CTA per SM; the asynchronous schedule -- on the
+ * caller's own graph (the arguments of kcore_decompose), best of `repeats`
+ * (1..100) calls after one warm-up each, with CUDA events on `stream`. It then
+ * sets the handle's options to the fastest schedule, decomposes once more
+ * with it and fills *best_out. Tracing is off while it times. Synchronous; the
+ * outputs hold that last, exact result. Errors: KCORE_ERR_INVALID (bad
+ * arguments, n < 1; options unchanged), the first input or memory error a call
+ * reports (KCORE_ERR_NOT_SIMPLE, _OOM; options restored), KCORE_ERR_CUDA if no
+ * schedule could run. */
+kcore_status kcore_autotune(kcore_handle h, int64_t n, int64_t m, const int64_t* offsets, const int32_t* adj,
+                            int32_t* coreness_out, int32_t* kmax_out, int32_t repeats, kcore_tuning* best_out,
+                            kcore_stream_t stream);
+
 /* ------------------------------------------------------------------------
  * Served peel (the paper peels one graph at a time; this is the request-loop
  * form of the same peel). A server owns a device memory pool reserved at
@@ -380,15 +426,22 @@ kcore_status kcore_server_destroy(kcore_server s);
  * cannot accept the device-wide synchronisation an allocation can cause. This
  * call allocates nothing (no cudaMalloc, no cudaFree, no allocating library
  * routine) and needs no handle: its scratch memory is one fixed array in the
- * library's device memory (about 26 MB), present on every GPU that loads the
- * library until the process exits. The caller still passes the graph and the
- * output arrays, exactly as for kcore_decompose (same layout and meaning):
+ * library's device memory (under 32 MB). It runs the peel with the settings of
+ * a handle's defaults. The caller still passes the graph and the output arrays,
+ * exactly as for kcore_decompose (same layout and meaning):
  *   n <= KCORE_STATIC_MAX_VERTICES, m <= KCORE_STATIC_MAX_ARCS; larger graphs
  *   are rejected with KCORE_ERR_CAPACITY before any work is queued.
- * It runs on the calling thread's current device and waits for `stream` before
- * returning the device status (KCORE_OK, KCORE_ERR_TIMEOUT, ...).
- * The first call on a device looks up the array's device address (a one-time
- * set-up per device); make that first call before any stream capture.
+ * It runs on the calling thread's current device and is synchronous: it waits
+ * for `stream` before returning the device status (KCORE_OK,
+ * KCORE_ERR_TIMEOUT, ...).
+ * The first call on a device does a one-time set-up: it looks up the array's
+ * device address, and under CUDA's default lazy module loading that lookup is
+ * what creates the array on the device (one allocation by the CUDA runtime,
+ * kept until the process exits). So make the first call on each device at
+ * start-up, before another allocator reserves the device memory, or run with
+ * CUDA_MODULE_LOADING=EAGER (the array then exists from the moment the
+ * library's code is loaded); make that first call before any stream capture.
+ * Later calls change nothing in the device's memory use.
  * Every call uses the same array and leaves its contents behind (each call
  * clears what must start from zero); calls that overlap on the GPU, from two
  * threads or two streams, race on it and must not be made. */
@@ -412,6 +465,16 @@ kcore_status kcore_core_mask(kcore_handle h, int64_t n, int64_t m, const int64_t
  * device recorded (KCORE_OK, KCORE_ERR_TIMEOUT, ...). */
 kcore_status kcore_sync_status(kcore_handle h);
 
+/* Latency of the bulk-synchronous schedule's grid barrier (the synchronisation
+ * each phase of Algorithm 1's rounds and subrounds ends with; the burdened
+ * span of Sec. 3.2 charges one per subround): `iters` (1 .. 10^6) barriers of
+ * `grid` co-resident CTAs (0 = the grid kcore_decompose uses for a large
+ * graph) run back to back with no work between them; *ns_out receives the
+ * mean time of one, in nanoseconds. Waits for the handle's last call and for
+ * the device; uses the handle's workspace. Errors: INVALID (bad arguments, a
+ * grid above the co-resident maximum), OOM, CUDA, TIMEOUT. */
+kcore_status kcore_barrier_latency(kcore_handle h, int64_t grid, int32_t iters, double* ns_out);
+
 /* Counters of the last decomposition; call after kcore_sync_status. */
 kcore_status kcore_get_stats(kcore_handle h, kcore_stats* out);
 
@@ -426,11 +489,12 @@ kcore_status kcore_get_stats(kcore_handle h, kcore_stats* out);
  * In mode 2 there is one entry per non-empty level: [1] is when its scan
  * phases ended, [10..12] are 0 and [13] counts its subround passes.
  * With KCORE_OPT_TRACE = 2 (modes 2 and 3) there is one entry per phase
- * (grid barrier) instead: [0] device time (ns) the phase ended, [1] its kind
- * (0 scan, 1 subround pass, 2 counting phase, 3 apply phase, 4 second scan
- * of an empty level), [2] the level, [3] the range it worked on (list
- * entries of a scan, queue items of a pass), [4] items it appended, [5]
- * frontier vertices a scan found, [6] arcs a pass read; [7..13] are 0.
+ * (grid barrier or tail phase) instead: [0] device time (ns) the phase
+ * ended, [1] its kind (0 scan, 1 subround pass, 2 counting phase, 3 apply
+ * phase, 4 second scan of an empty level), [2] the level, [3] the range it
+ * worked on (list entries of a scan, queue items of a pass), [4] items it
+ * appended, [5] frontier vertices a scan found, [6] arcs a pass read, [7] 1
+ * if one CTA ran it (tail mode); [8..13] are 0.
  * Tracing adds atomics and slows the run. At most max_rounds rounds are
  * copied; *rounds_out receives the number copied. */
 kcore_status kcore_get_trace(kcore_handle h, uint64_t* out, int64_t max_rounds, int64_t* rounds_out);

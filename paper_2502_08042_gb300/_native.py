@@ -101,7 +101,15 @@ class Stats(ctypes.Structure):
                                            "barriers", "batch_block", "batch_smem_vertices", "slice_arcs",
                                            "sample_vertices", "sample_recounts", "sample_bag",
                                            "sample_failed_validations", "sample_heads", "sample_reruns",
-                                           "sample_miss_round", "invalid_check", "invalid_vertex", "invalid_arc")]
+                                           "sample_miss_round", "invalid_check", "invalid_vertex", "invalid_arc",
+                                           "tail_phases", "tail_episodes")]
+
+
+class Tuning(ctypes.Structure):
+    _fields_ = [("sync_mode", ctypes.c_int32), ("batch_update", ctypes.c_int32),
+                ("warp_combine", ctypes.c_int32), ("ctas_per_sm", ctypes.c_int32),
+                ("tail_items", c_i64), ("tail_entries", c_i64), ("precheck_items", c_i64),
+                ("local_batches", c_i64), ("candidates", ctypes.c_int32), ("ms", ctypes.c_double)]
 
 
 class BatchTuning(ctypes.Structure):
@@ -125,6 +133,7 @@ SIGNATURES = {
     "kcore_validate_csr": ([c_p, c_i64, c_i64, c_p, c_p, c_p], ctypes.c_int),
     "kcore_sync_status": ([c_p], ctypes.c_int),
     "kcore_get_stats": ([c_p, ctypes.POINTER(Stats)], ctypes.c_int),
+    "kcore_barrier_latency": ([c_p, c_i64, ctypes.c_int32, ctypes.POINTER(ctypes.c_double)], ctypes.c_int),
     "kcore_get_trace": ([c_p, c_p, c_i64, ctypes.POINTER(c_i64)], ctypes.c_int),
     "kcore_build_csr": ([c_p, c_i64, c_i64, c_p, c_p, c_p, c_p, c_p, c_p], ctypes.c_int),
     "kcore_build_csr_workspace_size": ([c_p, c_i64, c_i64, ctypes.POINTER(c_sz)], ctypes.c_int),
@@ -134,6 +143,8 @@ SIGNATURES = {
     "kcore_batched_workspace_size": ([c_p, c_i64, c_i64, ctypes.POINTER(c_sz)], ctypes.c_int),
     "kcore_autotune_batched": ([c_p, c_i64, c_i64, c_i64, c_p, c_p, c_p, c_p, c_p, ctypes.c_int32,
                                 ctypes.POINTER(BatchTuning), c_p], ctypes.c_int),
+    "kcore_autotune": ([c_p, c_i64, c_i64, c_p, c_p, c_p, c_p, ctypes.c_int32, ctypes.POINTER(Tuning), c_p],
+                       ctypes.c_int),
     "kcore_build_csr_batched": ([c_p, c_i64, c_i64, c_i64, c_i64, c_p, c_p, c_p, c_p, c_p, c_p, c_p,
                                  c_p], ctypes.c_int),
     "kcore_server_create": ([ctypes.POINTER(c_p), ctypes.c_int, c_p], ctypes.c_int),

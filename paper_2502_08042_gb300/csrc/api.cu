@@ -22,8 +22,10 @@ struct kcore_ctx {
   size_t ws_bytes = 0;
   bool ws_external = false;
   std::string err;
-  int64_t opt[24] = {0, 0, 0, -1, 2000, 1, 2048, 0, 0, 192, 64, 1024, -1, 0, 32, 0, 1,
-                     0, 0, -1, 1, 1, 0, 64};  // indexed by kcore_option
+  int64_t opt[kc::kNumOptions] = {0, 0, 0, -1, kc::kTimeoutMsDefault, 1, 2048, 0, 0, 192,
+                                  kc::kPollSleepDefault, 1024, -1, 0, kc::kLocalBatchesDefault, 0, 1,
+                                  0, 0, -1, 1, 1, 0, kc::kPrecheckDefault, kc::kTailItemsDefault,
+                                  kc::kTailEntriesDefault, kc::kParkSleepDefault};  // indexed by kcore_option
   cudaStream_t last_stream = nullptr;
   bool pending = false;
   kc::PeelCtl* last_ctl = nullptr;
@@ -165,7 +167,7 @@ int sample_mu(const kcore_ctx* h, long long n) {
 }
 int effective_slice(const kcore_ctx* h) {
   if (h->opt[KCORE_OPT_SLICE_ARCS] > 0) return (int)h->opt[KCORE_OPT_SLICE_ARCS];
-  return effective_mode(h) == 1 ? 512 : 64;
+  return effective_mode(h) == 1 ? 512 : kc::kSliceDefault;
 }
 
 kcore_status ensure_ws(kcore_ctx* h, size_t need) {
@@ -239,8 +241,14 @@ kcore_status kcore_destroy(kcore_handle h) {
 const char* kcore_last_error(kcore_handle h) { return h ? h->err.c_str() : "null handle"; }
 
 kcore_status kcore_set_option(kcore_handle h, kcore_option opt, int64_t value) {
-  if (!h || (int)opt < 0 || (int)opt > 23) return KCORE_ERR_INVALID;
+  if (!h || (int)opt < 0 || (int)opt >= kc::kNumOptions) return KCORE_ERR_INVALID;
   switch (opt) {
+    case KCORE_OPT_TAIL_ITEMS:
+      if (value < 0 || value > (1ll << 30)) return fail(h, KCORE_ERR_INVALID, "tail items in [0, 2^30]");
+      break;
+    case KCORE_OPT_TAIL_ENTRIES:
+      if (value < 0 || value > INT32_MAX - 1) return fail(h, KCORE_ERR_INVALID, "tail entries in [0, 2^31 - 2]");
+      break;
     case KCORE_OPT_BATCH_BLOCK:
       if (value != 256 && value != 512 && value != 1024)
         return fail(h, KCORE_ERR_INVALID, "batch block must be 256, 512 or 1024");
@@ -278,6 +286,7 @@ kcore_status kcore_set_option(kcore_handle h, kcore_option opt, int64_t value) {
       break;
     case KCORE_OPT_IDLE_SLEEP_NS:
     case KCORE_OPT_POLL_SLEEP_NS:
+    case KCORE_OPT_PARK_SLEEP_NS:
       if (value < 0 || value > 100000) return fail(h, KCORE_ERR_INVALID, "sleep must be in [0, 100000] ns");
       break;
     case KCORE_OPT_TRACE:
@@ -316,7 +325,7 @@ kcore_status kcore_set_option(kcore_handle h, kcore_option opt, int64_t value) {
 }
 
 kcore_status kcore_get_option(kcore_handle h, kcore_option opt, int64_t* value) {
-  if (!h || !value || (int)opt < 0 || (int)opt > 23) return KCORE_ERR_INVALID;
+  if (!h || !value || (int)opt < 0 || (int)opt >= kc::kNumOptions) return KCORE_ERR_INVALID;
   *value = h->opt[opt];
   return KCORE_OK;
 }
@@ -371,7 +380,8 @@ kcore_status peel_call(kcore_ctx* h, int64_t n, int64_t m, const int64_t* offset
     return KCORE_OK;
   }
   const int mode = threshold ? 2 : effective_mode(h);
-  const int slice = h->opt[KCORE_OPT_SLICE_ARCS] > 0 ? (int)h->opt[KCORE_OPT_SLICE_ARCS] : (mode == 1 ? 512 : 64);
+  const int slice =
+      h->opt[KCORE_OPT_SLICE_ARCS] > 0 ? (int)h->opt[KCORE_OPT_SLICE_ARCS] : (mode == 1 ? 512 : kc::kSliceDefault);
   const bool hybrid = mode == 2 && !threshold && h->opt[KCORE_OPT_BATCH_UPDATE] != 0 &&
                       h->opt[KCORE_OPT_LEVEL_WINDOW] == 0;
   const bool sample = sampling_on(h, threshold);
@@ -395,10 +405,11 @@ kcore_status peel_call(kcore_ctx* h, int64_t n, int64_t m, const int64_t* offset
   a.max_rounds = L.max_rounds;
   a.ctl = (kc::PeelCtl*)(ws + L.ctl);
   a.slice = slice;
-  a.lq_cap = h->opt[KCORE_OPT_LOCAL_QUEUE] >= 0 ? (int)h->opt[KCORE_OPT_LOCAL_QUEUE] : (mode == 1 ? 32 : 128);
+  a.lq_cap = h->opt[KCORE_OPT_LOCAL_QUEUE] >= 0 ? (int)h->opt[KCORE_OPT_LOCAL_QUEUE]
+                                                : (mode == 1 ? 32 : kc::kLocalQueueDefault);
   a.max_take = 256;
   a.timeout_ns = (unsigned long long)h->opt[KCORE_OPT_TIMEOUT_MS] * 1000000ull;
-  a.scan_min = 2048;
+  a.scan_min = kc::kScanMin;
   a.idle_sleep_ns = (int)h->opt[KCORE_OPT_IDLE_SLEEP_NS];
   a.poll_sleep_ns = (int)h->opt[KCORE_OPT_POLL_SLEEP_NS];
   a.inject_stall = (int)h->opt[KCORE_OPT_TEST_STALL];
@@ -416,6 +427,9 @@ kcore_status peel_call(kcore_ctx* h, int64_t n, int64_t m, const int64_t* offset
   a.size_out = (long long*)size_out;
   a.combine = mode == 2 && h->opt[KCORE_OPT_WARP_COMBINE] != 0 ? 1 : 0;
   a.precheck_items = (int)h->opt[KCORE_OPT_PRECHECK_ITEMS];
+  a.tail_items = mode == 2 ? h->opt[KCORE_OPT_TAIL_ITEMS] : 0;
+  a.tail_entries = mode == 2 ? h->opt[KCORE_OPT_TAIL_ENTRIES] : 0;
+  a.park_sleep_ns = (int)h->opt[KCORE_OPT_PARK_SLEEP_NS];
 
   if (mode != 1 && m >= ((int64_t)1 << 40))
     return fail(h, KCORE_ERR_INVALID, "the bulk-synchronous modes take at most 2^40 arcs");
@@ -818,6 +832,8 @@ kcore_status kcore_sync_status(kcore_handle h) {
   h->stats.sync_mode = h->last_mode;
   h->stats.passes = c.passes;
   h->stats.barriers = c.barriers;
+  h->stats.tail_phases = c.tail_phases;
+  h->stats.tail_episodes = c.tail_episodes;
   h->stats.slice_arcs = h->last_slice;
   switch (c.status) {
     case 0:
@@ -839,8 +855,8 @@ kcore_status kcore_get_trace(kcore_handle h, uint64_t* out, int64_t max_rounds, 
   if (!h->last_trace) return fail(h, KCORE_ERR_INVALID, "the last decomposition ran without tracing");
   DeviceGuard g(h->device);
   // the bulk-synchronous modes record one entry per non-empty level, or per
-  // phase (barrier) with trace mode 2
-  const int64_t have = h->last_trace_phases ? h->stats.barriers
+  // phase (grid barrier or tail phase) with trace mode 2
+  const int64_t have = h->last_trace_phases ? h->stats.barriers + h->stats.tail_phases
                        : h->last_mode != 1  ? h->stats.rounds - h->stats.empty_rounds
                                             : h->stats.rounds;
   int64_t r = std::min<int64_t>(std::min<int64_t>(max_rounds, have), h->last_max_rounds);
@@ -850,6 +866,46 @@ kcore_status kcore_get_trace(kcore_handle h, uint64_t* out, int64_t max_rounds, 
     if (e != cudaSuccess) return cuda_fail(h, e, "read trace");
   }
   *rounds_out = r;
+  return KCORE_OK;
+}
+
+kcore_status kcore_barrier_latency(kcore_handle h, int64_t grid, int32_t iters, double* ns_out) {
+  if (!h || !ns_out || iters < 1 || iters > 1000000 || grid < 0) return KCORE_ERR_INVALID;
+  DeviceGuard g(h->device);
+  if (!g.ok) return fail(h, KCORE_ERR_CUDA, "cudaSetDevice failed");
+  h->err.clear();
+  const long long gmax = (long long)h->sms * h->bsp_max_ctas_per_sm;
+  if (grid > gmax) return fail(h, KCORE_ERR_INVALID, "grid above the co-resident maximum");
+  const int ctas = grid > 0 ? (int)grid : (int)gmax;
+  if (h->pending && h->last_stream) cudaStreamSynchronize(h->last_stream);
+  h->pending = false;
+  h->last_ctl = nullptr;
+  h->last_trace = nullptr;
+  h->last_csr_status = nullptr;
+  h->last_batch_status = nullptr;
+  h->last_validate_status = nullptr;
+  const size_t ctl_bytes = align_up(sizeof(kc::PeelCtl), 256);
+  kcore_status st = ensure_ws(h, ctl_bytes + 256);
+  if (st != KCORE_OK) return st;
+  char* ws = (char*)h->ws;
+  kc::PeelArgs a{};
+  a.ctl = (kc::PeelCtl*)ws;
+  a.timeout_ns = (unsigned long long)h->opt[KCORE_OPT_TIMEOUT_MS] * 1000000ull;
+  a.poll_sleep_ns = (int)h->opt[KCORE_OPT_POLL_SLEEP_NS];
+  unsigned long long* d_ns = (unsigned long long*)(ws + ctl_bytes);
+  cudaError_t e;
+  unsigned long long ns = 0;
+  int status = 0;
+  if ((e = cudaMemset(ws, 0, ctl_bytes + 256)) != cudaSuccess) return cuda_fail(h, e, "memset");
+  if ((e = kc::bsp_barrier_probe(a, ctas, iters, d_ns, nullptr)) != cudaSuccess)
+    return cuda_fail(h, e, "barrier probe launch");
+  if ((e = cudaDeviceSynchronize()) != cudaSuccess) return cuda_fail(h, e, "barrier probe");
+  if ((e = cudaMemcpy(&ns, d_ns, sizeof(ns), cudaMemcpyDeviceToHost)) != cudaSuccess)
+    return cuda_fail(h, e, "read probe");
+  if ((e = cudaMemcpy(&status, &a.ctl->status, sizeof(int), cudaMemcpyDeviceToHost)) != cudaSuccess)
+    return cuda_fail(h, e, "read status");
+  if (status == kc::ST_TIMEOUT) return fail(h, KCORE_ERR_TIMEOUT, "a barrier wait exceeded its time limit");
+  *ns_out = (double)ns / iters;
   return KCORE_OK;
 }
 

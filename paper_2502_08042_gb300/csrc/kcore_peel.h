@@ -9,6 +9,23 @@ namespace kc {
 enum : int { ST_OK = 0, ST_TIMEOUT = 4, ST_NOT_SIMPLE = 5, ST_CAPACITY = 6 };
 
 constexpr int kLocalQueueMax = 128;
+constexpr int kHandoff = 8;  // words of loop state CTA 0 hands the parked CTAs (tail mode)
+// Options of a handle (kcore_option values 0 .. kNumOptions - 1) and the
+// tail-mode defaults: off, because every threshold measured on GB300 was
+// slower on R-MAT scale 24 and the kNN workload (kcore_autotune tries it).
+constexpr int kNumOptions = 27;
+constexpr long long kTailItemsDefault = 0;
+constexpr long long kTailEntriesDefault = 0;
+constexpr long long kParkSleepDefault = 256;
+// Defaults of the bulk-synchronous schedule (sync mode 2), shared by the
+// handle's options and the no-allocation entry point.
+constexpr int kSliceDefault = 64;          // arcs per work item
+constexpr int kLocalQueueDefault = 128;    // per-warp local queue (items)
+constexpr int kLocalBatchesDefault = 32;   // local batches per chunk taken
+constexpr int kPrecheckDefault = 64;       // per-warp share from which d~ is read first
+constexpr int kPollSleepDefault = 64;      // grid-barrier poll sleep (ns)
+constexpr int kTimeoutMsDefault = 2000;    // limit of every device-side wait
+constexpr int kScanMin = 2048;             // active-list entries per scanning CTA (at least)
 constexpr int kMinSlice = 16;  // keeps slice indices below 2^27 (27-bit field of a work item)
 
 // Per-round record (zeroed before launch). Each hot word has its own 128-byte
@@ -69,6 +86,14 @@ struct PeelCtl {
   long long s_miss_vertex;
   int s_redo;  // 1: the sampled run's result is not exact (miss or failed check); rerun without sampling
   int pad8[23];
+  // tail mode (bulk-synchronous mode): CTA 0's releases of the parked CTAs
+  // (bit 63: a status was raised), the loop state it hands over with each
+  // release, and its counts of tail phases and episodes
+  unsigned long long tail_word;
+  char pad9[120];
+  unsigned long long handoff[kHandoff];
+  long long tail_phases, tail_episodes;
+  char pad10[48];
 };
 
 // The bulk-synchronous mode uses round records 0..2 as a ring: phase p uses
@@ -146,6 +171,12 @@ struct PeelArgs {
   // bulk-synchronous mode: the lanes of a warp that decrement the same vertex
   // in the same step send one atomic of their count (warp aggregation)
   int combine;
+  // tail mode (bulk-synchronous mode, plain schedule): a subround pass of at
+  // most tail_items queue items, or a scan of at most tail_entries active-list
+  // entries, runs on CTA 0 alone (0 disables either); the other CTAs park,
+  // sleeping park_sleep_ns between polls
+  long long tail_items, tail_entries;
+  int park_sleep_ns;
 };
 
 // Per-round trace record (KCORE_OPT_TRACE): globaltimer at round start (CTA 0),
@@ -166,6 +197,10 @@ cudaError_t peel_launch(const PeelArgs& args, int grid, cudaStream_t stream);
 int bsp_max_ctas_per_sm();
 int bsp_block_size();
 cudaError_t bsp_launch(const PeelArgs& args, int grid, cudaStream_t stream);
+// Grid-barrier latency probe: `iters` barriers with no work between them
+// (ctl zeroed by the caller); *out_ns (device) receives the elapsed time.
+cudaError_t bsp_barrier_probe(const PeelArgs& args, int grid, int iters, unsigned long long* out_ns,
+                              cudaStream_t stream);
 
 // Final check of a sampled run (sample.cu): every v must have at least
 // core[v] neighbours u with core[u] >= core[v]; a failure sets ctl->s_redo.

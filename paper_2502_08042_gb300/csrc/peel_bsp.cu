@@ -62,6 +62,9 @@ constexpr unsigned long long kAbort = 1ull << 63;
 
 // queue items the CTA appended in the current phase (added to its arrival)
 __shared__ unsigned long long s_app;
+// a thread of this CTA raised a status (ends a tail-mode phase, which has no
+// grid barrier to carry the abort bit)
+__shared__ int s_abort;
 
 struct Shared {
   int excl[kWarps][kWarp];
@@ -87,6 +90,21 @@ struct Shared {
     unsigned long long tail, head, found, alen, rcount, rqtail;
     int minkey, miss;
   } po;
+  RoundRec tring[kPhaseRing];  // tail mode: the phases' records, in shared memory
+  long long ho[kHandoff];      // a parked CTA: the loop state CTA 0 handed over
+  // per-warp counters (lane 0): queue items and local-queue items processed,
+  // local batches run (the heartbeat ticks every 64)
+  long long w_items[kWarps], w_local[kWarps];
+  unsigned w_lb[kWarps];
+  // counters and level timeline kept by CTA 0's thread 0 alone (registers
+  // held across the level loop make the hot loops spill)
+  struct {
+    long long levels, empty, scanned, passes, la_scanned, nscan, level_passes;
+    unsigned long long level_qb, arcs0, decs0, nfound, t_start, t_scan;
+    int kmax, rebuild;
+  } ld;
+  int sphase;         // tail mode: tail phases run (CTA 0)
+  unsigned tail_gen;  // tail episodes begun (thread 0 of every CTA)
 };
 
 // Sampling keeps the vertex of each local-queue entry beside it (a spilled
@@ -99,10 +117,13 @@ struct SharedS : Shared {
 template <bool kSample>
 using ShT = std::conditional_t<kSample, SharedS, Shared>;
 
-// Records the first error and makes every CTA leave at its next barrier.
+// Records the first error and makes every CTA leave at its next barrier (or,
+// parked during a tail episode, at once).
 __device__ __forceinline__ void raise_status(const PeelArgs& a, int code) {
   atomicCAS(&a.ctl->status, 0, code);
   for (int i = 0; i < 3; i++) atomicOr(&a.ctl->bar_ring[i].v, kAbort);
+  atomicOr(&a.ctl->tail_word, kAbort);
+  s_abort = 1;
 }
 
 __device__ __forceinline__ unsigned long long make_item(long long a0, long long len) {
@@ -262,7 +283,6 @@ __device__ bool grid_barrier(const PeelArgs& a, Shared& sh, unsigned long long& 
       }
       __nanosleep(a.poll_sleep_ns);
     }
-    gen++;
     sh.flag = ok;
     if (ok && R) {
       sh.po.head = ld_relaxed_u64(&R->head);
@@ -275,6 +295,7 @@ __device__ bool grid_barrier(const PeelArgs& a, Shared& sh, unsigned long long& 
     }
   }
   __syncthreads();
+  gen++;  // every thread: the barrier count also indexes the phase records
   return sh.flag != 0;
 }
 
@@ -719,8 +740,7 @@ __device__ void process_items(const PeelArgs& a, ShT<kSample>& sh, const PassCtx
 // Runs up to a.local_batches batches from the warp's local queue (vertices
 // that crossed during this pass), then moves what is left to the queue.
 template <bool kWin, bool kSample = false, bool kCombine = false>
-__device__ void drain_local(const PeelArgs& a, ShT<kSample>& sh, const PassCtx& pc, int warp, int lane,
-                            long long& local_items, unsigned& local_batches) {
+__device__ void drain_local(const PeelArgs& a, ShT<kSample>& sh, const PassCtx& pc, int warp, int lane) {
   for (int b = 0;; b++) {
     const int lqn = sh.lqn[warp];
     if (lqn == 0) return;
@@ -751,22 +771,24 @@ __device__ void drain_local(const PeelArgs& a, ShT<kSample>& sh, const PassCtx& 
     if (lane == 0) sh.lqn[warp] = lqn - c;
     __syncwarp();
     process_items<kWin, kSample, kCombine>(a, sh, pc, item, c, warp, lane);
-    local_items += c;
-    if (lane == 0 && ((++local_batches) & 63) == 0) atomicAdd(&a.ctl->progress, 1ull);
+    if (lane == 0) {
+      sh.w_local[warp] += c;
+      if (((++sh.w_lb[warp]) & 63) == 0) atomicAdd(&a.ctl->progress, 1ull);
+    }
   }
 }
 
-// One subround: the queue range [qb, qe) is processed once. Warp gw takes
-// its own contiguous share (len / warps items, one more for the first
-// len % warps warps) in chunks of up to 32 items, so a pass has no claim
+// One subround: the queue range [qb, qe) is processed once by `nctas` CTAs
+// (the grid, or CTA 0 alone in tail mode), this one being number `cta`. Warp
+// gw takes its own contiguous share (len / warps items, one more for the
+// first len % warps warps) in chunks of up to 32 items, so a pass has no claim
 // traffic and ends for a warp as soon as its share and local queue are done.
 template <bool kWin, bool kSample = false, bool kCombine = false>
 __device__ void run_pass(const PeelArgs& a, ShT<kSample>& sh, const PassCtx& pc, unsigned long long qb,
-                         unsigned long long qe, long long& items, long long& local_items,
-                         unsigned& local_batches) {
+                         unsigned long long qe, int cta, int nctas) {
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  const unsigned long long gw = (unsigned long long)blockIdx.x * kWarps + warp;
-  const unsigned long long nw = (unsigned long long)gridDim.x * kWarps;
+  const unsigned long long gw = (unsigned long long)cta * kWarps + warp;
+  const unsigned long long nw = (unsigned long long)nctas * kWarps;
   const unsigned long long len = qe - qb, share = len / nw, rem = len % nw;
   const unsigned long long b = qb + gw * share + (gw < rem ? gw : rem);
   const unsigned long long e = b + share + (gw < rem ? 1 : 0);
@@ -774,8 +796,8 @@ __device__ void run_pass(const PeelArgs& a, ShT<kSample>& sh, const PassCtx& pc,
     const int c = (int)min((unsigned long long)kTake, e - pos);
     const unsigned long long item = lane < c ? __ldcg(a.Q + pos + lane) : 0;
     process_items<kWin, kSample, kCombine>(a, sh, pc, item, c, warp, lane);
-    items += c;
-    drain_local<kWin, kSample, kCombine>(a, sh, pc, warp, lane, local_items, local_batches);
+    if (lane == 0) sh.w_items[warp] += c;
+    drain_local<kWin, kSample, kCombine>(a, sh, pc, warp, lane);
   }
 }
 
@@ -854,7 +876,7 @@ __device__ void hist_items(const PeelArgs& a, Shared& sh, const PassCtx& pc, uns
 
 template <bool kTouched>
 __device__ void run_hist(const PeelArgs& a, Shared& sh, const PassCtx& pc, unsigned long long qb,
-                         unsigned long long qe, long long& items) {
+                         unsigned long long qe) {
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const unsigned long long gw = (unsigned long long)blockIdx.x * kWarps + warp;
   const unsigned long long nw = (unsigned long long)gridDim.x * kWarps;
@@ -865,7 +887,7 @@ __device__ void run_hist(const PeelArgs& a, Shared& sh, const PassCtx& pc, unsig
     const int c = (int)min((unsigned long long)kTake, e - pos);
     const unsigned long long item = lane < c ? __ldcg(a.Q + pos + lane) : 0;
     hist_items<kTouched>(a, sh, pc, item, c, warp, lane);
-    items += c;
+    if (lane == 0) sh.w_items[warp] += c;
   }
 }
 
@@ -1004,75 +1026,100 @@ __device__ void run_recount_apply(const PeelArgs& a, const PassCtx& pc, unsigned
 }
 
 // Instantiations: kOffline (Algorithm 2's subrounds), kWindow (the level
-// window), kHybrid (batch update of heavy subrounds), kSample (sampling) and
-// kCombine (warp-aggregated decrements), each compiled apart so the default
-// kernel carries none of the others.
-template <bool kOffline, bool kWindow, bool kHybrid, bool kSample, bool kCombine = false>
+// window), kHybrid (batch update of heavy subrounds), kSample (sampling),
+// kCombine (warp-aggregated decrements) and kTail (tail mode), each compiled
+// apart so the default kernel carries none of the others.
+template <bool kOffline, bool kWindow, bool kHybrid, bool kSample, bool kCombine = false, bool kTail = false>
 __global__ void __launch_bounds__(kBlock, 2) peel_bsp(PeelArgs a) {
   __shared__ ShT<kSample> sh;
   // a rerun that is not needed ends at once (every CTA reads the same flag)
   if (a.run_if && ld_relaxed_s32(a.run_if) == 0) return;
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   const bool lead = blockIdx.x == 0 && tid == 0;
-  if (tid == 0) s_app = 0;
+  if (tid == 0) {
+    s_app = 0;
+    s_abort = 0;
+  }
   if (lane == 0) {
     sh.lqn[warp] = 0;
     sh.tr_arcs[warp] = sh.tr_decs[warp] = 0;
     sh.ncross[warp] = 0;
+    sh.w_items[warp] = sh.w_local[warp] = 0;
+    sh.w_lb[warp] = 0;
     if constexpr (kSample) sh.heads[warp] = 0;
   }
+  // grid barriers taken; grid phase g uses RoundRec g % 3 and barrier word g % 3
   unsigned long long gen = 0;
-  long long phase = 0;  // RoundRec (phase % 3) belongs to phase `phase`
-  auto reset_next = [&]() {
-    // the records of the next phase were last used two phases ago
-    const int r = (int)((phase + 1) % kPhaseRing);
-    if (blockIdx.x == 0 && warp == 0) {
-      if (lane == 0) {
-        RoundRec* R = a.rounds + r;
-        R->alen = 0;
-        R->found = 0;
-        R->minkey = 0;
-        R->tail = 0;
-        R->head = 0;
-        a.ctl->bar_ring[r].v = 0;
-        if constexpr (kSample) {
-          R->rcount = 0;
-          R->rqtail = 0;
-        }
-      }
+  // Tail mode (the plain schedule only): a phase whose range is small runs on
+  // CTA 0 alone and ends at a CTA barrier; its counters live in the CTA's own
+  // ring of records (tail phase s uses sh.tring[s % 3]).
+  // (sh.sphase: tail phases run; sh.tail_gen: tail episodes begun, kept by
+  // thread 0 of each CTA, the same count in every CTA)
+  bool solo = false;
+  if (tid == 0) {
+    sh.sphase = 0;
+    sh.tail_gen = 0;
+  }
+  auto rec = [&]() -> RoundRec* {
+    return solo ? &sh.tring[sh.sphase % kPhaseRing] : a.rounds + (gen % kPhaseRing);
+  };
+  auto clear_rec = [&](RoundRec* R) {
+    R->alen = 0;
+    R->found = 0;
+    R->minkey = 0;
+    R->tail = 0;
+    R->head = 0;
+    if constexpr (kSample) {
+      R->rcount = 0;
+      R->rqtail = 0;
     }
   };
+  auto reset_next = [&]() {
+    // the records of the next phase were last used two phases ago
+    if (solo) {
+      if (tid == 0) clear_rec(&sh.tring[(sh.sphase + 1) % kPhaseRing]);
+      return;
+    }
+    const int r = (int)((gen + 1) % kPhaseRing);
+    if (lead) {
+      clear_rec(a.rounds + r);
+      a.ctl->bar_ring[r].v = 0;
+    }
+  };
+  auto nscan_of = [&](long long len) {
+    long long ns = (len + a.scan_min - 1) / a.scan_min;
+    return ns < 1 ? 1ll : (ns > (long long)gridDim.x ? (long long)gridDim.x : ns);
+  };
+  auto free_list = [&](const int* x, const int* y) -> int* {
+    return (x != a.A0 && y != a.A0) ? a.A0 : ((x != a.A1 && y != a.A1) ? a.A1 : a.A2);
+  };
+  if constexpr (!kSample) {
   // per-phase timeline (trace mode 2): after each barrier CTA 0 records the
   // time, the phase kind (0 scan, 1 pass, 2 count, 3 apply, 4 second scan),
-  // the level, the range it worked on, its appends, the frontier found and
-  // the arcs read (passes)
+  // the level, the range it worked on, its appends, the frontier found, the
+  // arcs read (passes) and whether CTA 0 ran the phase alone (tail mode)
   // (the record count lives in shared memory: a register held across the
   // whole level loop made the hot loop spill)
   if (lead) {
     sh.trec = 0;
     sh.tarcs = 0;
+    sh.ld = {};
   }
-  // (the appends are read here, from the phase's record, only when tracing:
-  // an argument load at every call site cost a dependent L2 read per phase)
-  auto prec = [&](int kind, int level, unsigned long long range, const RoundRec* rec,
-                  unsigned long long found) {
+  // (the phase's appends come from the counters the barrier already read)
+  auto prec = [&](int kind, int level, unsigned long long range, unsigned long long found) {
     if (!(lead && a.trace_phases && sh.trec < a.max_rounds)) return;
-    const unsigned long long appended = rec ? ld_relaxed_u64(&rec->tail) : 0;
     unsigned long long* tr = a.trace + (size_t)sh.trec * kTraceFields;
     const unsigned long long arcs = ld_relaxed_u64(&a.ctl->tr_arcs);
     tr[0] = globaltimer_ns();
     tr[1] = (unsigned long long)kind;
     tr[2] = (unsigned long long)level;
     tr[3] = range;
-    tr[4] = appended;
+    tr[4] = sh.po.tail;
     tr[5] = found;
     tr[6] = arcs - sh.tarcs;
+    tr[7] = solo ? 1 : 0;
     sh.tarcs = arcs;
     sh.trec++;
-  };
-  auto nscan_of = [&](long long len) {
-    long long ns = (len + a.scan_min - 1) / a.scan_min;
-    return ns < 1 ? 1ll : (ns > (long long)gridDim.x ? (long long)gridDim.x : ns);
   };
   // Window of levels [hi_w - W, hi_w) (bucketing, a.window = W > 0): the
   // active list holds only vertices below hi_w; the others wait in the
@@ -1081,224 +1128,386 @@ __global__ void __launch_bounds__(kBlock, 2) peel_bsp(PeelArgs a) {
   // rebuild scan of the overflow list starts the next window. Three list
   // buffers rotate: active, overflow and the output of the next scan.
   const int W = (kWindow && !kOffline && a.window > 0 && !a.threshold) ? a.window : 0;
-  auto free_list = [&](const int* x, const int* y) -> int* {
-    return (x != a.A0 && y != a.A0) ? a.A0 : ((x != a.A1 && y != a.A1) ? a.A1 : a.A2);
-  };
   const int* Acur = nullptr;   // active list (nullptr without window: all vertices)
   long long la = W ? 0 : a.n;
   const int* Aover = nullptr;  // overflow list (nullptr with window: all vertices, before the first rebuild)
   long long lover = W ? a.n : 0;
   int hi_w = W ? 0 : INT_MAX;
   long long near_extra = 0;    // entries appended to the active list by the passes since its scan
-  int tp = -1, kmax = 0;
-  long long levels = 0, empty = 0, scanned = 0, passes = 0, items = 0, local_items = 0, rebuilds = 0;
-  unsigned local_batches = 0;
+  int tp = -1;                 // the last level peeled
+  int t = 0;                   // the level being peeled
   unsigned long long qend = 0;  // items appended by all completed phases
-  bool was_rebuild = false;
-  if constexpr (!kSample) {
+  unsigned long long qb = 0;    // the current pass's queue range is [qb, qend)
+  // Ends a phase: the grid barrier, or in tail mode a CTA barrier after which
+  // thread 0 copies the phase's counters from the CTA's own record (and ticks
+  // the heartbeat the parked CTAs' bounded wait watches).
+  auto sync = [&](RoundRec* R, bool want_rec) -> bool {
+    if (!solo) return grid_barrier(a, sh, gen, want_rec ? R : nullptr);
+    __syncthreads();
+    if (tid == 0) {
+      sh.po.tail = R->tail;
+      sh.po.head = R->head;
+      sh.po.found = R->found;
+      sh.po.alen = R->alen;
+      sh.po.minkey = R->minkey;
+      s_app = 0;
+      sh.flag = s_abort == 0;
+      sh.sphase++;
+      asm volatile("red.relaxed.gpu.global.add.u64 [%0], 1;" ::"l"(&a.ctl->progress) : "memory");
+    }
+    __syncthreads();
+    return sh.flag != 0;
+  };
+  // The steps of the level loop; a parked CTA resumes at the step CTA 0 hands it.
+  enum : int { kNxScan = 0, kNxPass = 1, kNxEnd = 2, kNxDone = 3 };
+  int nx = kNxScan;
+  const bool tail_ok = kTail && !kOffline && !W && !a.threshold && (a.tail_items > 0 || a.tail_entries > 0);
+  // Starts a tail episode. CTA 0 goes on alone (true); every other CTA parks
+  // (false) until CTA 0 hands the loop back.
+  auto begin_tail = [&]() -> bool {
+    if (tid == 0) sh.tail_gen++;
+    if (blockIdx.x != 0) return false;
+    solo = true;
+    if (tid == 0)
+      for (int r = 0; r < kPhaseRing; r++) clear_rec(&sh.tring[r]);
+    __syncthreads();
+    return true;
+  };
+  // A parked CTA waits (bounded by the heartbeat) for CTA 0's release of the
+  // current episode, then takes the loop state it handed over. False: the
+  // kernel ends (the peel finished in tail mode, a status was raised, or the
+  // wait gave up).
+  auto park = [&]() -> bool {
+    if (tid == 0) {
+      int okp = 1;
+      uint64_t t0 = 0;
+      unsigned long long pg = 0;
+      for (unsigned spins = 0;; spins++) {
+        const unsigned long long v = ld_acquire_u64(&a.ctl->tail_word);
+        if (v & kAbort) {
+          okp = 0;
+          break;
+        }
+        if (v >= (unsigned long long)sh.tail_gen) break;
+        if ((spins & 31) == 0) {
+          const uint64_t now = globaltimer_ns();
+          const unsigned long long p2 = ld_relaxed_u64(&a.ctl->progress);
+          if (spins == 0 || p2 != pg) {
+            pg = p2;
+            t0 = now;
+          } else if (now - t0 > a.timeout_ns) {
+            raise_status(a, ST_TIMEOUT);
+            okp = 0;
+            break;
+          }
+        }
+        __nanosleep(a.park_sleep_ns);
+      }
+      if (okp)
+        for (int i = 0; i < kHandoff; i++) sh.ho[i] = (long long)ld_relaxed_u64(&a.ctl->handoff[i]);
+      sh.flag = okp;
+    }
+    __syncthreads();
+    if (!sh.flag) return false;
+    nx = (int)sh.ho[0];
+    tp = (int)sh.ho[1];
+    qend = (unsigned long long)sh.ho[2];
+    qb = (unsigned long long)sh.ho[3];
+    la = sh.ho[4];
+    Acur = sh.ho[5] == 0 ? a.A0 : sh.ho[5] == 1 ? a.A1 : sh.ho[5] == 2 ? a.A2 : nullptr;
+    t = (int)sh.ho[6];
+    return nx != kNxDone;
+  };
+  // CTA 0 ends the episode: the loop state (next step `next`) goes to the
+  // parked CTAs with one release, and the phases that follow use the grid.
+  auto end_tail = [&](int next) {
+    __syncthreads();  // orders the CTA's writes of the episode before the release
+    if (tid == 0) {
+      unsigned long long* h = a.ctl->handoff;
+      h[0] = (unsigned long long)next;
+      h[1] = (unsigned long long)(long long)tp;
+      h[2] = qend;
+      h[3] = qb;
+      h[4] = (unsigned long long)la;
+      h[5] = Acur == a.A0 ? 0 : Acur == a.A1 ? 1 : Acur == a.A2 ? 2 : 3;
+      h[6] = (unsigned long long)(long long)t;
+      // (test hook: the first release is withheld, so every parked wait runs out)
+      if (!(a.inject_stall && sh.tail_gen == 1))
+        asm volatile("red.release.gpu.global.add.u64 [%0], %1;" ::"l"(&a.ctl->tail_word), "l"(1ull) : "memory");
+    }
+    solo = false;
+  };
   for (;;) {
-    // ---- scan: keep d~ > tp+1, take d~ == tp+1 (a k'-core query: one level,
-    // kprime - 1, taking every d~ below kprime and marking the rest 1)
-    const int tk = a.threshold ? a.kprime - 1 : tp + 1;
-    const bool rebuild = W && tk >= hi_w;
-    was_rebuild = rebuild;
-    const uint64_t t_start = lead && a.trace ? globaltimer_ns() : 0;
-    reset_next();
-    RoundRec* R = a.rounds + (phase % kPhaseRing);
-    const int* Ain = rebuild ? Aover : Acur;
-    const long long lin = rebuild ? lover : la + near_extra;
-    int* Aout = free_list(Acur, Aover);
-    // a rebuild writes the overflow list to the exhausted active list's buffer
-    int* Aov = rebuild ? (Acur ? const_cast<int*>(Acur) : free_list(Aout, Aover)) : nullptr;
-    long long nscan = nscan_of(lin);
-    if (blockIdx.x < nscan) {
-      const long long lo = lin * blockIdx.x / nscan, hi = lin * (blockIdx.x + 1) / nscan;
-      const ScanOut o = a.threshold ? scan_range(a, sh, R, qend, Ain, Aout, lo, hi, tk, tk, true, 0, 1)
-                        : rebuild  ? scan_range(a, sh, R, qend, Ain, Aout, lo, hi, tk, tk, false, -1, -1, Aov,
-                                                tk + W)
-                                   : scan_range(a, sh, R, qend, Ain, Aout, lo, hi, tk, tk);
-      if (tid == 0) {
-        if (o.found) atomicAdd(&R->found, o.found);
-        if (o.dmin != INT_MAX) atomicMax(&R->minkey, INT_MAX - o.dmin);
+    if (nx == kNxScan) {
+      // ---- scan: keep d~ > tp+1, take d~ == tp+1 (a k'-core query: one level,
+      // kprime - 1, taking every d~ below kprime and marking the rest 1)
+      const int tk = a.threshold ? a.kprime - 1 : tp + 1;
+      const bool rebuild = W && tk >= hi_w;
+      const long long lin = rebuild ? lover : la + near_extra;
+      if (tail_ok) {
+        const bool small = lin <= a.tail_entries;
+        if (small && !solo) {
+          if (!begin_tail()) {
+            if (!park()) break;
+            continue;
+          }
+        } else if (!small && solo) {
+          end_tail(kNxScan);
+        }
       }
-    }
-    if (!grid_barrier(a, sh, gen, R)) break;
-    phase++;
-    scanned += lin;
-    const unsigned long long found = sh.po.found;
-    prec(0, tk, (unsigned long long)lin, R, found);
-    const long long alen = (long long)sh.po.alen;
-    const int minkey = sh.po.minkey;
-    unsigned long long qb = qend;
-    qend += sh.po.tail;
-    Acur = Aout;
-    if (rebuild) {
-      Aover = Aov;
-      lover = (long long)sh.po.head;
-      hi_w = tk + W;
-      rebuilds++;
-    }
-    near_extra = 0;
-    const long long la_scanned = lin;
-    la = alen;
-    int t = tk;
-    unsigned long long nfound = found;
-    if (!found && !a.threshold) {
-      if (alen == 0 && lover == 0) break;  // nothing left
-      empty++;
-      if (W && alen == 0) {
-        // nothing left in the window: a rebuild starts the next one at the
-        // least d~ of the overflow list (known if this scan was a rebuild)
-        tp = rebuild ? INT_MAX - minkey - 1 : hi_w - 1;
-        continue;
+      if (lead && a.trace) {
+        sh.ld.t_start = globaltimer_ns();
+        sh.ld.rebuild = rebuild;
       }
-      // level tk is empty: the least induced degree of the kept vertices is the next level
-      t = INT_MAX - minkey;
       reset_next();
-      R = a.rounds + (phase % kPhaseRing);
-      nscan = nscan_of(la);
+      RoundRec* R = rec();
+      const int* Ain = rebuild ? Aover : Acur;
+      int* Aout = free_list(Acur, Aover);
+      // a rebuild writes the overflow list to the exhausted active list's buffer
+      int* Aov = rebuild ? (Acur ? const_cast<int*>(Acur) : free_list(Aout, Aover)) : nullptr;
+      long long nscan = solo ? 1 : nscan_of(lin);
       if (blockIdx.x < nscan) {
-        const long long lo = la * blockIdx.x / nscan, hi = la * (blockIdx.x + 1) / nscan;
-        const ScanOut o = scan_range(a, sh, R, qend, Acur, nullptr, lo, hi, INT_MAX, t);
-        if (tid == 0 && o.found) atomicAdd(&R->found, o.found);
+        const long long lo = lin * blockIdx.x / nscan, hi = lin * (blockIdx.x + 1) / nscan;
+        const ScanOut o = a.threshold ? scan_range(a, sh, R, qend, Ain, Aout, lo, hi, tk, tk, true, 0, 1)
+                          : rebuild  ? scan_range(a, sh, R, qend, Ain, Aout, lo, hi, tk, tk, false, -1, -1, Aov,
+                                                  tk + W)
+                                     : scan_range(a, sh, R, qend, Ain, Aout, lo, hi, tk, tk);
+        if (tid == 0) {
+          if (o.found) atomicAdd(&R->found, o.found);
+          if (o.dmin != INT_MAX) atomicMax(&R->minkey, INT_MAX - o.dmin);
+        }
       }
-      if (!grid_barrier(a, sh, gen, R)) break;
-      phase++;
-      scanned += la;
-      nfound = sh.po.found;
-      prec(4, t, (unsigned long long)la, R, nfound);
+      if (!sync(R, true)) break;
+      const unsigned long long found = sh.po.found;
+      prec(0, tk, (unsigned long long)lin, found);
+      const long long alen = (long long)sh.po.alen;
+      const int minkey = sh.po.minkey;
+      if (lead) {
+        sh.ld.scanned += lin;
+        sh.ld.la_scanned = lin;
+        sh.ld.nscan = nscan;
+        sh.ld.nfound = found;
+      }
+      qb = qend;
       qend += sh.po.tail;
-    }
-    kmax = t;
-    tp = t;
-    levels++;
-    const uint64_t t_scan = lead && a.trace ? globaltimer_ns() : 0;
-    const unsigned long long level_qb = qb;
-    const unsigned long long arcs0 = lead && a.trace ? ld_relaxed_u64(&a.ctl->tr_arcs) : 0;
-    const unsigned long long decs0 = lead && a.trace ? ld_relaxed_u64(&a.ctl->tr_decs) : 0;
-    long long level_passes = 0;
-    bool ok = true;
-    // ---- subround passes; with no vertex left above the level nothing can be decremented
-    if (kOffline) {
-      // Algorithm 1's subrounds exactly: also the last level (nothing left
-      // above it) and a frontier without arcs count as one subround each
-      while (qend > qb) {
-        // histogram phase: counts and the touched list (count in P->head)
+      Acur = Aout;
+      if (rebuild) {
+        Aover = Aov;
+        lover = (long long)sh.po.head;
+        hi_w = tk + W;
+      }
+      near_extra = 0;
+      la = alen;
+      t = tk;
+      if (!found && !a.threshold) {
+        if (alen == 0 && lover == 0) break;  // nothing left
+        if (lead) sh.ld.empty++;
+        if (W && alen == 0) {
+          // nothing left in the window: a rebuild starts the next one at the
+          // least d~ of the overflow list (known if this scan was a rebuild)
+          tp = rebuild ? INT_MAX - minkey - 1 : hi_w - 1;
+          continue;
+        }
+        // level tk is empty: the least induced degree of the kept vertices is the next level
+        t = INT_MAX - minkey;
+        if (tail_ok && !solo && la <= a.tail_entries) {
+          if (!begin_tail()) {
+            if (!park()) break;
+            continue;
+          }
+        }
         reset_next();
-        RoundRec* P = a.rounds + (phase % kPhaseRing);
-        const PassCtx hc{P, qend, t, t, false, -1, nullptr, 0};
-        run_hist<true>(a, sh, hc, qb, qend, items);
-        if (!(ok = grid_barrier(a, sh, gen, P))) break;
-        phase++;
-        const unsigned long long nt = sh.po.head;
-        // apply phase: crossings append the next frontier (count in P2->tail)
-        reset_next();
-        RoundRec* P2 = a.rounds + (phase % kPhaseRing);
-        const PassCtx pc{P2, qend, t, t, false, -1, nullptr, 0};
-        run_apply(a, pc, a.touched, nt);
-        if (!(ok = grid_barrier(a, sh, gen))) break;
-        phase++;
-        passes++;
-        level_passes++;
-        qb = qend;
+        R = rec();
+        nscan = solo ? 1 : nscan_of(la);
+        if (blockIdx.x < nscan) {
+          const long long lo = la * blockIdx.x / nscan, hi = la * (blockIdx.x + 1) / nscan;
+          const ScanOut o = scan_range(a, sh, R, qend, Acur, nullptr, lo, hi, INT_MAX, t);
+          if (tid == 0 && o.found) atomicAdd(&R->found, o.found);
+        }
+        if (!sync(R, true)) break;
+        prec(4, t, (unsigned long long)la, sh.po.found);
+        if (lead) {
+          sh.ld.scanned += la;
+          sh.ld.nscan = nscan;
+          sh.ld.nfound = sh.po.found;
+        }
         qend += sh.po.tail;
       }
-      if (ok && level_passes == 0 && nfound > 0) {
-        passes++;
-        level_passes++;
+      tp = t;
+      if (lead) {
+        sh.ld.kmax = t;
+        sh.ld.levels++;
+        sh.ld.level_qb = qb;
+        sh.ld.level_passes = 0;
+        if (a.trace) {
+          sh.ld.t_scan = globaltimer_ns();
+          sh.ld.arcs0 = ld_relaxed_u64(&a.ctl->tr_arcs);
+          sh.ld.decs0 = ld_relaxed_u64(&a.ctl->tr_decs);
+        }
       }
-    } else if (la > 0 || lover > 0) {
-      while (qend > qb) {
-        if (kHybrid && !W && 4 * (qend - qb) >= (unsigned long long)gridDim.x * kWarps &&
-            (qend - qb) >= (unsigned long long)la) {
-          // a heavy subround over a short active list: count the decrements
-          // per neighbour with reductions, then apply them walking the active
-          // list (Algorithm 2's batch update, the crossing decided once per
-          // vertex by its owner). Reductions need no return trip and run at
-          // about 1.5x the rate of returning atomics on this GPU; the apply
-          // walk costs one pass over the active list and a second barrier.
-          // Measured on R-MAT 24 / R-MAT 22 / kNN: -2.7% / -0.5% / -1.4%.
+      // with no vertex left above the level nothing can be decremented (the
+      // offline schedule still counts the level's one subround)
+      if (kOffline || la > 0 || lover > 0) {
+        nx = kNxPass;
+      } else {
+        qb = qend;
+        nx = kNxEnd;
+      }
+      continue;
+    }
+    if (nx == kNxPass) {
+      if (kOffline) {
+        // Algorithm 1's subrounds exactly: also the last level (nothing left
+        // above it) and a frontier without arcs count as one subround each
+        if (qend > qb) {
+          // histogram phase: counts and the touched list (count in P->head)
           reset_next();
-          RoundRec* P = a.rounds + (phase % kPhaseRing);
+          RoundRec* P = rec();
           const PassCtx hc{P, qend, t, t, false, -1, nullptr, 0};
-          run_hist<false>(a, sh, hc, qb, qend, items);
-          if (!(ok = grid_barrier(a, sh, gen))) break;
-          phase++;
-          prec(2, t, qend - qb, nullptr, 0);
+          run_hist<true>(a, sh, hc, qb, qend);
+          if (!sync(P, true)) break;
+          const unsigned long long nt = sh.po.head;
+          // apply phase: crossings append the next frontier (count in P2->tail)
           reset_next();
-          RoundRec* P2 = a.rounds + (phase % kPhaseRing);
+          RoundRec* P2 = rec();
           const PassCtx pc{P2, qend, t, t, false, -1, nullptr, 0};
-          run_apply(a, pc, Acur, (unsigned long long)la);
-          if (!(ok = grid_barrier(a, sh, gen))) break;
-          phase++;
-          prec(3, t, (unsigned long long)la, P2, 0);
-          passes++;
-          level_passes++;
+          run_apply(a, pc, a.touched, nt);
+          if (!sync(P2, false)) break;
+          if (lead) {
+            sh.ld.passes++;
+            sh.ld.level_passes++;
+          }
           qb = qend;
           qend += sh.po.tail;
           continue;
         }
-        reset_next();
-        RoundRec* P = a.rounds + (phase % kPhaseRing);
-        // a pass whose per-warp share is at least a.precheck_items items is
-        // throughput-bound (measured: kNN's largest level 1,700 items per
-        // warp; R-MAT passes a few)
-        const bool pre = (qend - qb) >= (unsigned long long)a.precheck_items * gridDim.x * kWarps;
-        const PassCtx pc{P, qend, t, a.threshold ? 0 : t, pre, W ? hi_w : -1, const_cast<int*>(Acur),
-                         (unsigned long long)(la + near_extra)};
-        run_pass<kWindow, false, kCombine>(a, sh, pc, qb, qend, items, local_items, local_batches);
-        if (a.threshold && lane == 0 && sh.ncross[warp]) {
-          atomicAdd(&a.ctl->crossed, (unsigned long long)sh.ncross[warp]);
-          sh.ncross[warp] = 0;
+        if (lead && sh.ld.level_passes == 0 && sh.ld.nfound > 0) {
+          sh.ld.passes++;
+          sh.ld.level_passes++;
         }
-        if (a.trace) {
-          // one pair of atomics per CTA (per warp, 9,728 same-address atomics
-          // would add several microseconds to every traced pass)
-          __syncthreads();
-          if (tid == 0) {
-            unsigned long long ta = 0, td = 0;
-            for (int w = 0; w < kWarps; w++) {
-              ta += sh.tr_arcs[w];
-              td += sh.tr_decs[w];
-              sh.tr_arcs[w] = sh.tr_decs[w] = 0;
-            }
-            if (ta) atomicAdd(&a.ctl->tr_arcs, ta);
-            if (td) atomicAdd(&a.ctl->tr_decs, td);
+        nx = kNxEnd;
+        continue;
+      }
+      if (qend <= qb) {
+        nx = kNxEnd;
+        continue;
+      }
+      if (tail_ok) {
+        const bool small = qend - qb <= (unsigned long long)a.tail_items;
+        if (small && !solo) {
+          if (!begin_tail()) {
+            if (!park()) break;
+            continue;
           }
+        } else if (!small && solo) {
+          end_tail(kNxPass);
         }
-        if (!(ok = grid_barrier(a, sh, gen, W ? P : nullptr))) break;
-        phase++;
-        passes++;
-        level_passes++;
-        prec(1, t, qend - qb, P, 0);
+      }
+      if (kHybrid && !W && !solo && 4 * (qend - qb) >= (unsigned long long)gridDim.x * kWarps &&
+          (qend - qb) >= (unsigned long long)la) {
+        // a heavy subround over a short active list: count the decrements
+        // per neighbour with reductions, then apply them walking the active
+        // list (Algorithm 2's batch update, the crossing decided once per
+        // vertex by its owner). Reductions need no return trip and run at
+        // about 1.5x the rate of returning atomics on this GPU; the apply
+        // walk costs one pass over the active list and a second barrier.
+        // Measured on R-MAT 24 / R-MAT 22 / kNN: -2.7% / -0.5% / -1.4%.
+        reset_next();
+        RoundRec* P = rec();
+        const PassCtx hc{P, qend, t, t, false, -1, nullptr, 0};
+        run_hist<false>(a, sh, hc, qb, qend);
+        if (!sync(P, false)) break;
+        prec(2, t, qend - qb, 0);
+        reset_next();
+        RoundRec* P2 = rec();
+        const PassCtx pc{P2, qend, t, t, false, -1, nullptr, 0};
+        run_apply(a, pc, Acur, (unsigned long long)la);
+        if (!sync(P2, false)) break;
+        prec(3, t, (unsigned long long)la, 0);
+        if (lead) {
+          sh.ld.passes++;
+          sh.ld.level_passes++;
+        }
         qb = qend;
         qend += sh.po.tail;
-        if (W) near_extra += (long long)sh.po.found;
+        continue;
       }
-    } else {
+      reset_next();
+      RoundRec* P = rec();
+      const int nctas = solo ? 1 : (int)gridDim.x;
+      // a pass whose per-warp share is at least a.precheck_items items is
+      // throughput-bound (measured: kNN's largest level 1,700 items per
+      // warp; R-MAT passes a few)
+      const bool pre = (qend - qb) >= (unsigned long long)a.precheck_items * nctas * kWarps;
+      const PassCtx pc{P, qend, t, a.threshold ? 0 : t, pre, W ? hi_w : -1, const_cast<int*>(Acur),
+                       (unsigned long long)(la + near_extra)};
+      run_pass<kWindow, false, kCombine>(a, sh, pc, qb, qend, solo ? 0 : (int)blockIdx.x, nctas);
+      if (a.threshold && lane == 0 && sh.ncross[warp]) {
+        atomicAdd(&a.ctl->crossed, (unsigned long long)sh.ncross[warp]);
+        sh.ncross[warp] = 0;
+      }
+      if (a.trace) {
+        // one pair of atomics per CTA (per warp, 9,728 same-address atomics
+        // would add several microseconds to every traced pass)
+        __syncthreads();
+        if (tid == 0) {
+          unsigned long long ta = 0, td = 0;
+          for (int w = 0; w < kWarps; w++) {
+            ta += sh.tr_arcs[w];
+            td += sh.tr_decs[w];
+            sh.tr_arcs[w] = sh.tr_decs[w] = 0;
+          }
+          if (ta) atomicAdd(&a.ctl->tr_arcs, ta);
+          if (td) atomicAdd(&a.ctl->tr_decs, td);
+        }
+      }
+      if (!sync(P, W != 0)) break;
+      if (lead) {
+        sh.ld.passes++;
+        sh.ld.level_passes++;
+      }
+      prec(1, t, qend - qb, 0);
       qb = qend;
+      qend += sh.po.tail;
+      if (W) near_extra += (long long)sh.po.found;
+      continue;
     }
-    if (lead && a.trace && !a.trace_phases && levels - 1 < a.max_rounds) {
-      unsigned long long* tr = a.trace + (size_t)(levels - 1) * kTraceFields;
-      tr[0] = t_start;
-      tr[1] = t_scan;
+    // ---- nx == kNxEnd: the level is finished
+    if (lead && a.trace && !a.trace_phases && sh.ld.levels - 1 < a.max_rounds) {
+      unsigned long long* tr = a.trace + (size_t)(sh.ld.levels - 1) * kTraceFields;
+      tr[0] = sh.ld.t_start;
+      tr[1] = sh.ld.t_scan;
       tr[2] = globaltimer_ns();
       tr[3] = (unsigned long long)t;
-      tr[4] = (unsigned long long)la_scanned;
-      tr[5] = nfound;
-      tr[6] = qend - level_qb;
-      tr[7] = (unsigned long long)nscan;
-      tr[8] = ld_relaxed_u64(&a.ctl->tr_arcs) - arcs0;
-      tr[9] = ld_relaxed_u64(&a.ctl->tr_decs) - decs0;
-      tr[10] = was_rebuild ? 1 : 0;
-      tr[13] = (unsigned long long)level_passes;
+      tr[4] = (unsigned long long)sh.ld.la_scanned;
+      tr[5] = sh.ld.nfound;
+      tr[6] = qend - sh.ld.level_qb;
+      tr[7] = (unsigned long long)sh.ld.nscan;
+      tr[8] = ld_relaxed_u64(&a.ctl->tr_arcs) - sh.ld.arcs0;
+      tr[9] = ld_relaxed_u64(&a.ctl->tr_decs) - sh.ld.decs0;
+      tr[10] = sh.ld.rebuild ? 1 : 0;
+      tr[13] = (unsigned long long)sh.ld.level_passes;
     }
     if (a.threshold) {
       // the k'-core: the vertices kept by the scan that no decrement removed
-      if (ok && lead && a.size_out) *a.size_out = la - (long long)ld_relaxed_u64(&a.ctl->crossed);
+      if (lead && a.size_out) *a.size_out = la - (long long)ld_relaxed_u64(&a.ctl->crossed);
       break;
     }
-    if (!ok || (la == 0 && lover == 0 && near_extra == 0)) break;
+    if (la == 0 && lover == 0 && near_extra == 0) break;
+    nx = kNxScan;
+  }
+  // the parked CTAs leave with the loop
+  if (solo) end_tail(kNxDone);
+  if (lead) {
+    if (a.kmax_out) *a.kmax_out = sh.ld.kmax;
+    a.ctl->rounds = sh.ld.levels + sh.ld.empty;
+    a.ctl->empty_rounds = sh.ld.empty;
+    a.ctl->scanned = sh.ld.scanned;
+    a.ctl->kmax = sh.ld.kmax;
+    a.ctl->passes = sh.ld.passes;
+    a.ctl->barriers = (long long)gen;
+    a.ctl->tail_phases = sh.sphase;
+    a.ctl->tail_episodes = (long long)sh.tail_gen;
   }
   } else {
     // ---- Algorithm 4 with the sampling Peel of Algorithm 5. A level is a
@@ -1312,10 +1521,15 @@ __global__ void __launch_bounds__(kBlock, 2) peel_bsp(PeelArgs a) {
     // for a vertex in sample mode the first level its validation could fail
     // at. A recount that finds a missed level ends the run (the result is
     // then recomputed without sampling).
+    const int* Acur = nullptr;  // active list (nullptr: all vertices)
+    long long la = a.n;
+    int tp = -1, kmax = 0;
+    long long levels = 0, empty = 0, scanned = 0, passes = 0;
+    unsigned long long qend = 0;  // items appended by all completed phases
     for (;;) {
       const int tk = tp + 1;
       reset_next();
-      RoundRec* R = a.rounds + (phase % kPhaseRing);
+      RoundRec* R = rec();
       int* Aout = free_list(Acur, nullptr);
       const long long lin = la;
       const long long nscan = nscan_of(lin);
@@ -1329,7 +1543,6 @@ __global__ void __launch_bounds__(kBlock, 2) peel_bsp(PeelArgs a) {
         }
       }
       if (!grid_barrier(a, sh, gen, R)) break;
-      phase++;
       scanned += lin;
       unsigned long long nfound = sh.po.found;
       la = (long long)sh.po.alen;
@@ -1350,13 +1563,11 @@ __global__ void __launch_bounds__(kBlock, 2) peel_bsp(PeelArgs a) {
         reset_next();
         run_recount_count(a, nrqv, passes, level_pass);
         if (!(ok = grid_barrier(a, sh, gen))) return;
-        phase++;
         reset_next();
-        RoundRec* P = a.rounds + (phase % kPhaseRing);
+        RoundRec* P = rec();
         const PassCtx pc{P, qend, tk, tk, false, -1, nullptr, 0, (int)passes};
         run_recount_apply(a, pc, nrv, tk, (int)passes);
         if (!(ok = grid_barrier(a, sh, gen, P))) return;
-        phase++;
         nfound += sh.po.found;
         qend += sh.po.tail;
         const int mk2 = sh.po.minkey;
@@ -1377,11 +1588,10 @@ __global__ void __launch_bounds__(kBlock, 2) peel_bsp(PeelArgs a) {
       levels++;
       while (qend > qb) {
         reset_next();
-        RoundRec* P = a.rounds + (phase % kPhaseRing);
+        RoundRec* P = rec();
         const PassCtx pc{P, qend, tk, tk, true, -1, nullptr, 0, (int)passes};
-        run_pass<false, true>(a, sh, pc, qb, qend, items, local_items, local_batches);
+        run_pass<false, true>(a, sh, pc, qb, qend, (int)blockIdx.x, (int)gridDim.x);
         if (!(ok = grid_barrier(a, sh, gen, P))) break;
-        phase++;
         passes++;
         qb = qend;
         qend += sh.po.tail;
@@ -1395,23 +1605,50 @@ __global__ void __launch_bounds__(kBlock, 2) peel_bsp(PeelArgs a) {
       if (!ok || miss || la == 0) break;
     }
     if (lane == 0 && sh.heads[warp]) atomicAdd((unsigned long long*)&a.ctl->s_heads, sh.heads[warp]);
+    if (lead) {
+      if (a.kmax_out) *a.kmax_out = kmax;
+      a.ctl->rounds = levels + empty;
+      a.ctl->empty_rounds = empty;
+      a.ctl->scanned = scanned;
+      a.ctl->kmax = kmax;
+      a.ctl->passes = passes;
+      a.ctl->barriers = (long long)gen;
+    }
   }
   if (lane == 0) {
-    if (items) atomicAdd(&a.ctl->items, (unsigned long long)items);
-    if (local_items) atomicAdd(&a.ctl->local_items, (unsigned long long)local_items);
-  }
-  if (lead) {
-    if (a.kmax_out) *a.kmax_out = kmax;
-    a.ctl->rounds = levels + empty;
-    a.ctl->empty_rounds = empty;
-    a.ctl->scanned = scanned;
-    a.ctl->kmax = kmax;
-    a.ctl->passes = passes;
-    a.ctl->barriers = (long long)gen;
+    if (sh.w_items[warp]) atomicAdd(&a.ctl->items, (unsigned long long)sh.w_items[warp]);
+    if (sh.w_local[warp]) atomicAdd(&a.ctl->local_items, (unsigned long long)sh.w_local[warp]);
   }
 }
 
+// Measures the grid barrier alone: `iters` barriers back to back with no work
+// between them, on the same words and with the same waits as the peel; CTA 0
+// writes the elapsed device time (ns) to *out.
+__global__ void __launch_bounds__(kBlock, 2) barrier_probe(PeelArgs a, int iters, unsigned long long* out) {
+  __shared__ Shared sh;
+  if (threadIdx.x == 0) {
+    s_app = 0;
+    s_abort = 0;
+  }
+  unsigned long long gen = 0;
+  __syncthreads();
+  const uint64_t t0 = globaltimer_ns();
+  for (int i = 0; i < iters; i++) {
+    // the word of the next barrier was last polled two barriers ago
+    if (blockIdx.x == 0 && threadIdx.x == 0) a.ctl->bar_ring[(gen + 1) % kPhaseRing].v = 0;
+    if (!grid_barrier(a, sh, gen)) break;
+  }
+  if (blockIdx.x == 0 && threadIdx.x == 0) *out = globaltimer_ns() - t0;
+}
+
 }  // namespace
+
+cudaError_t bsp_barrier_probe(const PeelArgs& args, int grid, int iters, unsigned long long* out_ns,
+                              cudaStream_t stream) {
+  PeelArgs a = args;
+  void* params[] = {&a, &iters, &out_ns};
+  return cudaLaunchCooperativeKernel((const void*)barrier_probe, dim3(grid), dim3(kBlock), params, 0, stream);
+}
 
 int bsp_max_ctas_per_sm() {
   const void* fns[] = {(const void*)peel_bsp<false, false, false, false>,
@@ -1420,7 +1657,11 @@ int bsp_max_ctas_per_sm() {
                        (const void*)peel_bsp<false, false, true, false>,
                        (const void*)peel_bsp<false, false, false, true>,
                        (const void*)peel_bsp<false, false, true, false, true>,
-                       (const void*)peel_bsp<false, false, false, false, true>};
+                       (const void*)peel_bsp<false, false, false, false, true>,
+                       (const void*)peel_bsp<false, false, true, false, false, true>,
+                       (const void*)peel_bsp<false, false, false, false, false, true>,
+                       (const void*)peel_bsp<false, false, true, false, true, true>,
+                       (const void*)peel_bsp<false, false, false, false, true, true>};
   int best = 1 << 30;
   for (const void* f : fns) {
     int nb = 0;
@@ -1435,14 +1676,23 @@ int bsp_block_size() { return kBlock; }
 cudaError_t bsp_launch(const PeelArgs& args, int grid, cudaStream_t stream) {
   PeelArgs a = args;
   void* params[] = {&a};
-  const void* fn = a.sample       ? (const void*)peel_bsp<false, false, false, true>
-                   : a.offline    ? (const void*)peel_bsp<true, false, false, false>
-                   : a.combine && a.window == 0
-                       ? (a.hybrid ? (const void*)peel_bsp<false, false, true, false, true>
-                                   : (const void*)peel_bsp<false, false, false, false, true>)
-                   : a.window > 0 ? (const void*)peel_bsp<false, true, false, false>
-                   : a.hybrid     ? (const void*)peel_bsp<false, false, true, false>
-                                  : (const void*)peel_bsp<false, false, false, false>;
+  // tail mode has instantiations of its own (the plain schedule, with or
+  // without batch update and warp aggregation)
+  const bool tail = !a.sample && !a.offline && a.window == 0 && !a.threshold &&
+                    (a.tail_items > 0 || a.tail_entries > 0);
+  const void* fn =
+      a.sample    ? (const void*)peel_bsp<false, false, false, true>
+      : a.offline ? (const void*)peel_bsp<true, false, false, false>
+      : tail      ? (a.combine ? (a.hybrid ? (const void*)peel_bsp<false, false, true, false, true, true>
+                                           : (const void*)peel_bsp<false, false, false, false, true, true>)
+                               : (a.hybrid ? (const void*)peel_bsp<false, false, true, false, false, true>
+                                           : (const void*)peel_bsp<false, false, false, false, false, true>))
+      : a.combine && a.window == 0
+          ? (a.hybrid ? (const void*)peel_bsp<false, false, true, false, true>
+                      : (const void*)peel_bsp<false, false, false, false, true>)
+      : a.window > 0 ? (const void*)peel_bsp<false, true, false, false>
+      : a.hybrid     ? (const void*)peel_bsp<false, false, true, false>
+                     : (const void*)peel_bsp<false, false, false, false>;
   return cudaLaunchCooperativeKernel(fn, dim3(grid), dim3(kBlock), params, 0, stream);
 }
 

@@ -19,7 +19,8 @@ OPTIONS = {"sync_mode": 0, "ctas_per_sm": 1, "slice_arcs": 2, "local_queue": 3, 
            "trace": 8, "idle_sleep_ns": 9, "poll_sleep_ns": 10, "batch_block": 11,
            "batch_smem_vertices": 12, "batch_ctas_per_sm": 13, "local_batches": 14, "level_window": 15,
            "batch_update": 16, "sampling": 17, "sample_mu": 18, "sample_threshold": 19, "sample_seed": 20,
-           "sample_check": 21, "warp_combine": 22, "precheck_items": 23}
+           "sample_check": 21, "warp_combine": 22, "precheck_items": 23, "tail_items": 24,
+           "tail_entries": 25, "park_sleep_ns": 26}
 TRACE_FIELDS = ("t_start", "t_scanned", "t_done", "level", "scanned", "found", "queued", "scan_ctas",
                 "arcs", "decrements", "max_cta_scan_ns", "max_cta_start_delay_ns", "busy_ns",
                 "batches")
@@ -120,12 +121,19 @@ class KCore:
         self._check(self._L.kcore_get_stats(self._h, ctypes.byref(s)))
         return {f: int(getattr(s, f)) for f, _ in _native.Stats._fields_}
 
+    def barrier_latency_ns(self, grid: int = 0, iters: int = 2000) -> float:
+        """Mean time of one grid barrier of the bulk-synchronous schedule
+        (grid CTAs, 0 = the large-graph grid), measured on the device."""
+        v = ctypes.c_double()
+        self._check(self._L.kcore_barrier_latency(self._h, int(grid), int(iters), ctypes.byref(v)))
+        return float(v.value)
+
     def trace(self) -> np.ndarray:
         """Timeline of the last decomposition: one row of TRACE_FIELDS per
         round with trace=1, one row per phase with trace=2 (fields as
         kcore_get_trace documents)."""
         st = self.stats()
-        max_r = max(st["barriers"] if self.get_option("trace") == 2 else st["rounds"], 0)
+        max_r = max(st["barriers"] + st["tail_phases"] if self.get_option("trace") == 2 else st["rounds"], 0)
         buf = np.zeros((max(max_r, 1), len(TRACE_FIELDS)), np.uint64)
         got = ctypes.c_int64()
         self._check(self._L.kcore_get_trace(self._h, buf.ctypes.data, max_r, ctypes.byref(got)))
@@ -206,6 +214,22 @@ class KCore:
         if sync:
             self.sync()
         return coreness, kmax
+
+    def autotune(self, offsets, adj, coreness=None, kmax=None, repeats: int = 2, stream=None):
+        """Times the single-graph peel's candidate schedules on this graph,
+        keeps the fastest in the handle's options and returns (coreness, kmax,
+        tuning dict) computed with it."""
+        torch = _torch()
+        n = offsets.numel() - 1
+        dev = offsets.device
+        if coreness is None:
+            coreness = torch.empty(max(n, 0), dtype=torch.int32, device=dev)
+        if kmax is None:
+            kmax = torch.empty(1, dtype=torch.int32, device=dev)
+        t = _native.Tuning()
+        self._check(self._L.kcore_autotune(self._h, n, adj.numel(), _ptr(offsets), _ptr(adj), _ptr(coreness),
+                                           _ptr(kmax), int(repeats), ctypes.byref(t), _stream_ptr(stream)))
+        return coreness, kmax, {f: getattr(t, f) for f, _ in t._fields_}
 
     def autotune_batched(self, graph_vertex_offsets, offsets, adj, coreness=None, kmax=None,
                          repeats: int = 2, stream=None):

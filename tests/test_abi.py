@@ -104,7 +104,8 @@ def _struct_fields(name):
 
 
 def test_other_mirrored_structs_match_the_header():
-    for cname, mirror in (("kcore_batch_tuning", _native.BatchTuning), ("kcore_server_config", _native.ServerConfig)):
+    for cname, mirror in (("kcore_batch_tuning", _native.BatchTuning), ("kcore_server_config", _native.ServerConfig),
+                          ("kcore_tuning", _native.Tuning)):
         fields = _struct_fields(cname)
         assert [n for n, _ in mirror._fields_] == [n for n, _ in fields], cname
         for (n, ct), (_, cty) in zip(mirror._fields_, fields):

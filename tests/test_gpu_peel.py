@@ -173,17 +173,19 @@ def test_caller_workspace(mode):
         assert e.value.code == "OOM"
 
 
-@pytest.mark.parametrize("mode", MODES)
-def test_timeout_is_reported_and_context_survives(mode):
+@pytest.mark.parametrize("mode,tail", [(1, None), (2, None), (3, None), (2, (0, 0)), (2, (1 << 30, 1 << 30))],
+                         ids=["async", "bsp", "offline", "bsp-no-tail", "bsp-all-tail"])
+def test_timeout_is_reported_and_context_survives(mode, tail):
     """A wait that can never be satisfied (CTA 0 withholds its completion
-    token, or its arrival at the first grid barrier) must end at the time
-    limit with KCORE_ERR_TIMEOUT, and the same context must then decompose
-    normally."""
+    token, its arrival at the first grid barrier, or -- in tail mode -- its
+    first release of the parked CTAs) must end at the time limit with
+    KCORE_ERR_TIMEOUT, and the same context must then decompose normally."""
     n = 5000
     s, d = gg.rmat_n(n, 40000, seed=1)
     off, adj = _csr(n, s, d)
     o, a = to_dev(off, adj)
-    with KCore(0, timeout_ms=200, test_stall=1, sync_mode=mode) as k:
+    extra = {} if tail is None else dict(tail_items=tail[0], tail_entries=tail[1])
+    with KCore(0, timeout_ms=200, test_stall=1, sync_mode=mode, **extra) as k:
         with pytest.raises(KCoreError) as e:
             k.decompose(o, a)
         assert e.value.code == "TIMEOUT"
@@ -234,7 +236,8 @@ def test_bsp_counters_and_trace():
         tr = k.trace()
     assert st["sync_mode"] == 2
     assert st["passes"] > 0
-    assert st["barriers"] - (st["rounds"] + st["passes"]) in (0, 1)
+    # a phase ends at a grid barrier, or at a CTA barrier in tail mode
+    assert st["barriers"] + st["tail_phases"] - (st["rounds"] + st["passes"]) in (0, 1)
     levels = tr[:, 3].astype(np.int64)
     assert len(levels) == st["rounds"] - st["empty_rounds"]
     np.testing.assert_array_equal(levels, np.unique(want))
@@ -256,10 +259,13 @@ def test_bsp_phase_trace(batch_update):
         assert_parity(k, n, off, adj, want)
         st = k.stats()
         tr = k.trace().astype(np.int64)
-    assert len(tr) == st["barriers"]
+    assert len(tr) == st["barriers"] + st["tail_phases"]
     assert (np.diff(tr[:, 0]) >= 0).all()
     kinds = tr[:, 1]
     assert set(np.unique(kinds)) <= {0, 1, 2, 3, 4}
+    # field 7 flags the phases CTA 0 ran alone; no counting or apply phase is among them
+    assert int(tr[:, 7].sum()) == st["tail_phases"]
+    assert not ((tr[:, 7] == 1) & ((kinds == 2) | (kinds == 3))).any()
     assert (np.diff(tr[:, 2]) >= 0).all()
     assert int(np.count_nonzero(kinds == 1)) + int(np.count_nonzero(kinds == 3)) == st["passes"]
     # a scan per visited level (two for an empty one), and perhaps a last
