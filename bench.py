@@ -488,13 +488,31 @@ def run_gpu(args):
     cpu = None
     if not args.no_cpu_baseline:
         cpu = cpu_oracle_baseline(n, off.cpu().numpy(), adj.cpu().numpy(), workload_name(args.workload, w))
+    kmax_val = int(kmax.item())
+    # the batched form of the same peel, measured in the same run (one GPU):
+    # graphs/s against a loop of plain launches, with identical output
+    batched = None
+    if args.workload == "rmat24" and ws == 1 and not args.no_batched:
+        del off, adj, core, kmax, flush, adj_h, off_h, core_h, km_h
+        k.close()
+        torch.cuda.empty_cache()
+        G_total = WORKLOADS["batched"]["G"]
+        r = batched_measure(local, 5, 3, G_total, e2e=False)
+        bms = r["total_ms"] / 5
+        batched = {"workload": f"{G_total} graphs (n log-uniform 1e3..2e5, avg degree U(4,64), ER or R-MAT)",
+                   "graphs_per_s": G_total / (bms / 1e3), "ms_per_batch": bms, "steps": 5, "warmup": 3,
+                   "arcs": r["M"], "plain_loop_graphs_per_s": G_total / (r["loop_ms"] / 1e3),
+                   "speedup_vs_plain_loop": r["loop_ms"] / bms, "identical_output": r["same"],
+                   "autotuned": {key: r["tuning"][key] for key in ("block", "ctas_per_sm", "smem_vertices")},
+                   "note": "CUDA events around each batched launch; the plain loop is one kcore_decompose per "
+                           "graph on the same stream"}
     out = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "int32", "data": "synthetic",
         "config": {
             "workload": workload_name(args.workload, w),
-            "n": n, "edges_drawn": E, "undirected_edges": mu, "arcs": m, "kmax": int(kmax.item()),
+            "n": n, "edges_drawn": E, "undirected_edges": mu, "arcs": m, "kmax": kmax_val,
             "rounds": st["rounds"], "empty_rounds": st["empty_rounds"], "grid": st["grid"],
             "sync_mode": st["sync_mode"], "slice_arcs": st["slice_arcs"], "passes": st["passes"],
             "barriers": st["barriers"], "tail_phases": st["tail_phases"],
@@ -521,6 +539,7 @@ def run_gpu(args):
                      "algorithmic_bytes": bmin, "kernel": kname},
         "sync_floor_ms": sync_floor["ms"],
         "sync_floor": sync_floor,
+        **({"batched": batched} if batched else {}),
         "e2e": e2e,
         # a sampled step is the sampled peel, the two check kernels and the
         # rerun kernel (which returns at once when not needed)
@@ -580,19 +599,20 @@ def batch_subset(spec, gv, eoff, s, d, idx):
     return sub, gv2, eoff2, s2, d2
 
 
-def run_batched(args):
+def batched_measure(local: int, steps: int, warmup: int, G_total: int, ws: int = 1, rank: int = 0,
+                    e2e: bool = True):
+    """The batched workload on one GPU: generation, segmented CSR build, the
+    library's autotuner (untimed), `steps` timed batched launches after
+    `warmup`, then a loop of plain single-graph launches over the same graphs
+    (identical output checked) and, with e2e, the end-to-end path from pinned
+    host memory. With ws > 1 this rank takes its longest-processing-time share
+    of the graphs by arc count. Returns the measurements (times are this
+    rank's; the caller reduces over ranks)."""
     import torch
 
     from paper_2502_08042_gb300 import KCore
 
-    import torch.distributed as dist
-
-    ws, rank, local = dist_env()
-    if ws > 1:
-        dist.init_process_group("nccl")
-    torch.cuda.set_device(local)
     dev = torch.device("cuda", local)
-    G_total = args.graphs or WORKLOADS["batched"]["G"]
     t0 = time.perf_counter()
     spec, gv, eoff, s, d = _batch_inputs(G_total)
     if ws > 1:
@@ -626,15 +646,16 @@ def run_batched(args):
     t_tune = time.perf_counter()
     _, _, tuning = k.autotune_batched(gvd, off, adj, core, kmax, repeats=2)
     tuning["tune_s"] = time.perf_counter() - t_tune
-    for _ in range(args.warmup):
+    for _ in range(warmup):
         k.decompose_batched(gvd, off, adj, core, kmax)
     evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
-           for _ in range(args.steps)]
+           for _ in range(steps)]
     if ws > 1:
+        import torch.distributed as dist
         dist.barrier()
     torch.cuda.synchronize()
     with ClockSampler(local) as clk:
-        for i in range(args.steps):
+        for i in range(steps):
             flush.zero_()
             evs[i][0].record()
             k.decompose_batched(gvd, off, adj, core, kmax, sync=False)
@@ -642,7 +663,7 @@ def run_batched(args):
         torch.cuda.synchronize()
     k.sync()
     st = k.stats()
-    ms = max_over_ranks(sum(a.elapsed_time(b) for a, b in evs), ws, dev) / args.steps
+    total_ms = sum(a.elapsed_time(b) for a, b in evs)
     ref = core.clone()
     # a loop of plain single-graph launches over the same graphs (own handle,
     # workspace sized once for the largest graph)
@@ -672,35 +693,58 @@ def run_batched(args):
     kl.sync()
     loop_ms = e0.elapsed_time(e1)
     same = bool(torch.equal(core, ref))
-    # end to end: segmented CSR from pinned host memory, coreness back
-    gv_h = torch.from_numpy(gv).pin_memory()
-    off_h = off.cpu().pin_memory()
-    adj_h = adj.cpu().pin_memory()
-    core_h = torch.empty(N, dtype=torch.int32, pin_memory=True)
-    km_h = torch.empty(G, dtype=torch.int32, pin_memory=True)
+    del subs, ws_buf
+    kl.close()
     e2e_ms = []
-    for it in range(3):
-        torch.cuda.synchronize()
-        t1 = time.perf_counter()
-        gvd2 = gv_h.to(dev, non_blocking=True)
-        off2 = off_h.to(dev, non_blocking=True)
-        adj2 = adj_h.to(dev, non_blocking=True)
-        c2, k2 = k.decompose_batched(gvd2, off2, adj2, sync=False)
-        core_h.copy_(c2, non_blocking=True)
-        km_h.copy_(k2, non_blocking=True)
-        k.sync()
-        torch.cuda.synchronize()
-        e2e_ms.append((time.perf_counter() - t1) * 1e3)
-        del gvd2, off2, adj2, c2, k2
-    e2e_best = max_over_ranks(min(e2e_ms[1:]) if len(e2e_ms) > 1 else e2e_ms[0], ws, dev)
+    if e2e:
+        # end to end: segmented CSR from pinned host memory, coreness back
+        gv_h = torch.from_numpy(gv).pin_memory()
+        off_h = off.cpu().pin_memory()
+        adj_h = adj.cpu().pin_memory()
+        core_h = torch.empty(N, dtype=torch.int32, pin_memory=True)
+        km_h = torch.empty(G, dtype=torch.int32, pin_memory=True)
+        for it in range(3):
+            torch.cuda.synchronize()
+            t1 = time.perf_counter()
+            gvd2 = gv_h.to(dev, non_blocking=True)
+            off2 = off_h.to(dev, non_blocking=True)
+            adj2 = adj_h.to(dev, non_blocking=True)
+            c2, k2 = k.decompose_batched(gvd2, off2, adj2, sync=False)
+            core_h.copy_(c2, non_blocking=True)
+            km_h.copy_(k2, non_blocking=True)
+            k.sync()
+            torch.cuda.synchronize()
+            e2e_ms.append((time.perf_counter() - t1) * 1e3)
+            del gvd2, off2, adj2, c2, k2
+    k.close()
+    del off, adj, core, kmax, flush, gvd
+    torch.cuda.empty_cache()
+    return dict(spec=spec, gv=gv, G=G, N=N, M=M, gen_s=gen_s, csr_ms=csr_ms, tuning=tuning, grid=st["grid"],
+                total_ms=total_ms, loop_ms=loop_ms, same=same, e2e_ms=e2e_ms, clocks=clk.summary())
+
+
+def run_batched(args):
+    import torch
+    import torch.distributed as dist
+
+    ws, rank, local = dist_env()
+    if ws > 1:
+        dist.init_process_group("nccl")
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    G_total = args.graphs or WORKLOADS["batched"]["G"]
+    r = batched_measure(local, args.steps, args.warmup, G_total, ws, rank)
+    ms = max_over_ranks(r["total_ms"], ws, dev) / args.steps
+    e2e_best = max_over_ranks(min(r["e2e_ms"][1:]), ws, dev)
     if rank != 0:
         if ws > 1:
             dist.barrier()
         return
+    G, N, M = r["G"], r["N"], r["M"]
     peak, peak_kind = load_peaks()
     bmin = 8 * (N + G) + 4 * M + 12 * N
     achieved = bmin / (ms / 1e3) / 1e9
-    cpu = None if args.no_cpu_baseline else cpu_batch_baseline(spec, gv, G)
+    cpu = None if args.no_cpu_baseline else cpu_batch_baseline(r["spec"], r["gv"], G)
     out = {
         "metric": METRIC, "value": G_total / (ms / 1e3), "unit": "graphs/s", "n_gpus": ws,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True,
@@ -712,11 +756,11 @@ def run_batched(args):
                    "parallelism": (f"graphs split over {ws} GPUs by arc count (longest processing "
                                    "time first); the job's time is the slowest rank's") if ws > 1
                    else "single GPU",
-                   "undirected_edges_per_s_rank0": M / 2 / (ms / 1e3), "csr_build_ms": csr_ms,
-                   "generation_s": gen_s, "grid": st["grid"], "autotuned": tuning,
+                   "undirected_edges_per_s_rank0": M / 2 / (ms / 1e3), "csr_build_ms": r["csr_ms"],
+                   "generation_s": r["gen_s"], "grid": r["grid"], "autotuned": r["tuning"],
                    "l2": "inputs larger than L2 and a 258 MB buffer written between timed steps"},
-        "plain_loop": {"graphs_per_s": G / (loop_ms / 1e3), "ms": loop_ms, "identical_output": same,
-                       "speedup": loop_ms / ms},
+        "plain_loop": {"graphs_per_s": G / (r["loop_ms"] / 1e3), "ms": r["loop_ms"],
+                       "identical_output": r["same"], "speedup": r["loop_ms"] / ms},
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                      "frac": achieved / peak, "traffic": None, "peak_kind": peak_kind,
                      "algorithmic_bytes": bmin, "kernel": "batch_peel"},
@@ -726,9 +770,8 @@ def run_batched(args):
         "gpu_launches": 2 * args.steps,
         "cpu_baseline": cpu,
     }
-    c = clk.summary()
-    if c:
-        out["clocks"] = c
+    if r["clocks"]:
+        out["clocks"] = r["clocks"]
     emit(out)
     if ws > 1:
         dist.barrier()
@@ -906,6 +949,8 @@ def main():
                     help="batched workload: first G graphs of the distribution (default 4096; "
                          "smaller batches are for profiling)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-batched", action="store_true",
+                    help="default workload: skip the batched sub-record measured after the main line")
     args = ap.parse_args()
     if args.impl == "reference":
         run_reference(args)

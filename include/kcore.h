@@ -65,8 +65,8 @@ typedef enum {
                                   applies them in one step per vertex, so every crossing is decided
                                   by one owner; no local queues (its subrounds are Algorithm 1's) */
   KCORE_OPT_CTAS_PER_SM = 1,   /* CTAs per SM of the persistent kernel (0 = occupancy maximum) */
-  KCORE_OPT_SLICE_ARCS = 2,    /* arcs per work item (16 .. 2^20; 0 = auto: 64 in mode 2, 512 in
-                                  mode 1): longer lists are split in slices */
+  KCORE_OPT_SLICE_ARCS = 2,    /* arcs per work item (16 .. 2^20; 0 = auto: 32 in modes 2 and 3,
+                                  512 in mode 1): longer lists are split in slices */
   KCORE_OPT_LOCAL_QUEUE = 3,   /* per-warp local queue capacity (work items, 0 .. 128; 0 disables
                                   it; -1 = auto: 128 in mode 2, 32 in mode 1) */
   KCORE_OPT_TIMEOUT_MS = 4,    /* limit for every device-side wait, milliseconds */
@@ -140,7 +140,10 @@ typedef enum {
                                          CTA (0 .. 2^30; 0 = never) */
   KCORE_OPT_TAIL_ENTRIES = 25,        /* a scan of at most this many active-list entries runs on one
                                          CTA (0 .. 2^31 - 2; 0 = never) */
-  KCORE_OPT_PARK_SLEEP_NS = 26        /* nanosleep of a parked CTA between polls (0 .. 100000) */
+  KCORE_OPT_PARK_SLEEP_NS = 26,       /* nanosleep of a parked CTA between polls (0 .. 100000) */
+  KCORE_OPT_SCAN_ENTRIES = 27         /* modes 1 and 2: a scan gives each CTA at least this many active-list
+                                         entries (256 .. 2^20; default 512), so short lists are
+                                         scanned by fewer CTAs */
 } kcore_option;
 
 /* Counters of the last decomposition, or of the last CSR check (the three

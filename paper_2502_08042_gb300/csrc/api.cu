@@ -25,7 +25,8 @@ struct kcore_ctx {
   int64_t opt[kc::kNumOptions] = {0, 0, 0, -1, kc::kTimeoutMsDefault, 1, 2048, 0, 0, 192,
                                   kc::kPollSleepDefault, 1024, -1, 0, kc::kLocalBatchesDefault, 0, 1,
                                   0, 0, -1, 1, 1, 0, kc::kPrecheckDefault, kc::kTailItemsDefault,
-                                  kc::kTailEntriesDefault, kc::kParkSleepDefault};  // indexed by kcore_option
+                                  kc::kTailEntriesDefault, kc::kParkSleepDefault,
+                                  kc::kScanMin};  // indexed by kcore_option
   cudaStream_t last_stream = nullptr;
   bool pending = false;
   kc::PeelCtl* last_ctl = nullptr;
@@ -249,6 +250,9 @@ kcore_status kcore_set_option(kcore_handle h, kcore_option opt, int64_t value) {
     case KCORE_OPT_TAIL_ENTRIES:
       if (value < 0 || value > INT32_MAX - 1) return fail(h, KCORE_ERR_INVALID, "tail entries in [0, 2^31 - 2]");
       break;
+    case KCORE_OPT_SCAN_ENTRIES:
+      if (value < 256 || value > (1 << 20)) return fail(h, KCORE_ERR_INVALID, "scan entries in [256, 2^20]");
+      break;
     case KCORE_OPT_BATCH_BLOCK:
       if (value != 256 && value != 512 && value != 1024)
         return fail(h, KCORE_ERR_INVALID, "batch block must be 256, 512 or 1024");
@@ -409,7 +413,7 @@ kcore_status peel_call(kcore_ctx* h, int64_t n, int64_t m, const int64_t* offset
                                                 : (mode == 1 ? 32 : kc::kLocalQueueDefault);
   a.max_take = 256;
   a.timeout_ns = (unsigned long long)h->opt[KCORE_OPT_TIMEOUT_MS] * 1000000ull;
-  a.scan_min = kc::kScanMin;
+  a.scan_min = (int)h->opt[KCORE_OPT_SCAN_ENTRIES];
   a.idle_sleep_ns = (int)h->opt[KCORE_OPT_IDLE_SLEEP_NS];
   a.poll_sleep_ns = (int)h->opt[KCORE_OPT_POLL_SLEEP_NS];
   a.inject_stall = (int)h->opt[KCORE_OPT_TEST_STALL];

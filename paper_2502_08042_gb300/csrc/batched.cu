@@ -13,7 +13,9 @@
 //     returns k+1 lands its vertex on k and appends it to the next subround's
 //     frontier; __syncthreads separates subrounds and levels;
 //   * the induced degrees live in shared memory when the graph is small enough
-//     (shared-memory atomics), otherwise in a per-graph slice of the workspace.
+//     (shared-memory atomics), otherwise in a per-graph slice of the workspace;
+//     when every degree of the graph is below 2^16 they take 16 bits each
+//     (twice as many vertices fit in shared memory, half the L2 footprint).
 // Persistent CTAs take graphs from a device counter in descending order of
 // arcs (longest-processing-time first), so the largest graphs start first.
 // Nothing waits on another CTA: the kernel has no spin-waits.
@@ -81,22 +83,52 @@ __device__ __forceinline__ int block_min(int x, BatchShared<BLOCK>& sh) {
   return m;
 }
 
-// d~ read: shared memory, or L2 (atomics are performed in L2, so a global
-// d~ must not be read through L1). Global d~ accesses carry an evict-last
-// hint and the once-read lists (active list, frontiers, adjacency) stream
-// with evict-first loads and stores: with hundreds of large graphs in flight
-// their state exceeds L2, and the d~ lines are the ones that are hit again.
-__device__ __forceinline__ int load_deg(const int* D, int v, bool in_smem, uint64_t pol) {
-  return in_smem ? D[v] : ld_cg_keep(D + v, pol);
-}
+// The induced degrees d~ of one graph, in shared memory or in L2 (atomics are
+// performed in L2, so a global d~ is never read through L1). Global d~
+// accesses carry an evict-last hint and the once-read lists (active list,
+// frontiers, adjacency) stream with evict-first loads and stores: with
+// hundreds of large graphs in flight their state exceeds L2, and the d~ lines
+// are the ones that are hit again.
+// Narrow form: two 16-bit values per 32-bit word (vertex v in half v & 1 of
+// word v >> 1). A vertex's d~ starts at its degree and falls by one per
+// peeled neighbour (each arc is traversed once), so it stays in [0, degree]:
+// with every degree below 2^16 a decrement never borrows from the other half.
+struct DegStore {
+  int* w;
+  bool smem, narrow;
+  uint64_t pol;
+  __device__ __forceinline__ int get(int v) const {
+    if (narrow) {
+      const int x = smem ? w[v >> 1] : ld_cg_keep(w + (v >> 1), pol);
+      return (x >> ((v & 1) * 16)) & 0xffff;
+    }
+    return smem ? w[v] : ld_cg_keep(w + v, pol);
+  }
+  // decrements d~[v] by one and returns the value before
+  __device__ __forceinline__ int dec(int v) const {
+    if (narrow) {
+      const int sh = (v & 1) * 16;
+      const int old = smem ? atomicSub(w + (v >> 1), 1 << sh) : atom_add_keep(w + (v >> 1), -(1 << sh), pol);
+      return (old >> sh) & 0xffff;
+    }
+    return smem ? atomicSub(w + v, 1) : atom_add_keep(w + v, -1, pol);
+  }
+  // initial values: one word (narrow: vertices 2i and 2i + 1, degree d1 of
+  // the second, 0 past the end)
+  __device__ __forceinline__ void put_word(int i, int d0, int d1) const {
+    const int x = narrow ? (d0 | (d1 << 16)) : d0;
+    if (smem) w[i] = x;
+    else st_keep(w + i, x, pol);
+  }
+};
 
 // One pass over the active list after level k: entries with D > k survive
 // into `out` (their minimum goes to *dmin); among them, those at exactly k+1
 // are also written to F (the next frontier if level k+1 is not empty).
 // Returns the survivors; *nf gets the number written to F.
 template <int BLOCK>
-__device__ int compact_active(const int* A, int la, int n, int* out, int* F, const int* D, bool in_smem,
-                              int k, BatchShared<BLOCK>& sh, int* dmin, int* nf, uint64_t pol) {
+__device__ int compact_active(const int* A, int la, int n, int* out, int* F, const DegStore& D, int k,
+                              BatchShared<BLOCK>& sh, int* dmin, int* nf) {
   int written = 0, wf = 0, lmin = INT_MAX;
   for (int base = 0; base < la; base += BLOCK * kScanItems) {
     int v[kScanItems];
@@ -113,7 +145,7 @@ __device__ int compact_active(const int* A, int la, int n, int* out, int* F, con
 #pragma unroll
     for (int q = 0; q < kScanItems; q++) {
       if (v[q] >= 0) {
-        int d = load_deg(D, v[q], in_smem, pol);
+        int d = D.get(v[q]);
         if (d > k) {
           keep |= 1u << q;
           lmin = min(lmin, d);
@@ -140,8 +172,8 @@ __device__ int compact_active(const int* A, int la, int n, int* out, int* F, con
 
 // Selection of the frontier: entries of A with D[v] == k.
 template <int BLOCK>
-__device__ int select_frontier(const int* A, int la, int n, int* F, const int* D, bool in_smem, int k,
-                               BatchShared<BLOCK>& sh, uint64_t pol) {
+__device__ int select_frontier(const int* A, int la, int n, int* F, const DegStore& D, int k,
+                               BatchShared<BLOCK>& sh) {
   int written = 0;
   for (int base = 0; base < la; base += BLOCK * kScanItems) {
     int v[kScanItems];
@@ -157,7 +189,7 @@ __device__ int select_frontier(const int* A, int la, int n, int* F, const int* D
     }
 #pragma unroll
     for (int q = 0; q < kScanItems; q++)
-      if (v[q] >= 0 && load_deg(D, v[q], in_smem, pol) == k) take |= 1u << q;
+      if (v[q] >= 0 && D.get(v[q]) == k) take |= 1u << q;
     int tot;
     int pos = block_excl_scan(__popc(take), sh, &tot);
     int p = written + pos;
@@ -181,9 +213,6 @@ __device__ void peel_one_graph(const GraphDesc& gd, int smem_deg_max, int* statu
     return;
   }
   const int n = (int)gd.n;
-  const bool in_smem = n <= smem_deg_max;
-  const uint64_t pol = l2_evict_last_policy();
-  int* D = in_smem ? sdeg : gd.deg;
   const long long* O = gd.off;
   const int* adj = gd.adj;
   int* core = gd.core;
@@ -192,33 +221,45 @@ __device__ void peel_one_graph(const GraphDesc& gd, int smem_deg_max, int* statu
   int* F0 = gd.F0;
   int* F1 = gd.F1;
 
-  // degrees, identity active list, minimum degree
+  // degrees: their minimum (the first level) and maximum (whether 16 bits
+  // hold them), then the store, the initial values and the identity active list
   if (tid == 0) sh.bad = 0;
   __syncthreads();
-  int lmin = INT_MAX;
+  int lmin = INT_MAX, lmax = 0;
   for (int v = tid; v < n; v += BLOCK) {
     long long o0 = O[v], o1 = O[v + 1];
     if (o0 < 0 || o1 < o0 || o1 > gd.m || o1 - o0 >= n) {
       flag_bad(status, 1, v, &sh.bad);
       o1 = o0;
     }
-    int d = (int)(o1 - o0);
-    if (in_smem) D[v] = d;
-    else st_keep(D + v, d, pol);
-    __stcs(A0 + v, v);
+    const int d = (int)(o1 - o0);
     lmin = min(lmin, d);
+    lmax = max(lmax, d);
   }
-  int k = block_min(lmin, sh);  // also orders the writes above
+  int k = block_min(lmin, sh);
+  const int dmax = -block_min(-lmax, sh);
   if (sh.bad) {  // malformed offsets: leave this graph (its outputs are undefined)
     if (tid == 0) *gd.kmax = -1;
     __syncthreads();
     return;
   }
+  const bool narrow = dmax < 65536;
+  const bool in_smem = narrow ? n <= 2 * smem_deg_max : n <= smem_deg_max;
+  const DegStore D{in_smem ? sdeg : gd.deg, in_smem, narrow, l2_evict_last_policy()};
+  const int nw = narrow ? (n + 1) / 2 : n;
+  for (int i = tid; i < nw; i += BLOCK) {
+    const int v0 = narrow ? 2 * i : i;
+    const int d0 = (int)(O[v0 + 1] - O[v0]);
+    const int d1 = narrow && v0 + 1 < n ? (int)(O[v0 + 2] - O[v0 + 1]) : 0;
+    D.put_word(i, d0, d1);
+  }
+  for (int v = tid; v < n; v += BLOCK) __stcs(A0 + v, v);
+  __syncthreads();
   int* A = A0;
   int* An = A1;
   int la = n;
   int kmax = 0;
-  int nf = select_frontier<BLOCK>(A, la, n, F0, D, in_smem, k, sh, pol);
+  int nf = select_frontier<BLOCK>(A, la, n, F0, D, k, sh);
   for (;;) {
     int* Fc = F0;
     int* Fn = F1;
@@ -285,8 +326,8 @@ __device__ void peel_one_graph(const GraphDesc& gd, int smem_deg_max, int* statu
             // frontier (or peeled), never returns k + 1, and its d~ is only
             // compared with levels above k afterwards.
             if (u[q] >= 0) {
-              if (in_smem) cross = D[u[q]] > k && atomicSub(&D[u[q]], 1) == k + 1;
-              else cross = atom_add_keep(D + u[q], -1, pol) == k + 1;
+              if (D.smem) cross = D.get(u[q]) > k && D.dec(u[q]) == k + 1;
+              else cross = D.dec(u[q]) == k + 1;
             }
             unsigned m = __ballot_sync(kFull, cross);
             if (m) {
@@ -315,12 +356,12 @@ __device__ void peel_one_graph(const GraphDesc& gd, int smem_deg_max, int* statu
     // rest is the next non-empty level; vertices at k+1 are collected on the
     // way in case that level is the next one
     int dmin;
-    la = compact_active<BLOCK>(A, la, n, An, F0, D, in_smem, k, sh, &dmin, &nf, pol);
+    la = compact_active<BLOCK>(A, la, n, An, F0, D, k, sh, &dmin, &nf);
     int* t = A;
     A = An;
     An = t;
     if (la == 0) break;
-    if (dmin != k + 1) nf = select_frontier<BLOCK>(A, la, n, F0, D, in_smem, dmin, sh, pol);
+    if (dmin != k + 1) nf = select_frontier<BLOCK>(A, la, n, F0, D, dmin, sh);
     k = dmin;
   }
   if (tid == 0) *gd.kmax = kmax;

@@ -13,19 +13,22 @@ constexpr int kHandoff = 8;  // words of loop state CTA 0 hands the parked CTAs 
 // Options of a handle (kcore_option values 0 .. kNumOptions - 1) and the
 // tail-mode defaults: off, because every threshold measured on GB300 was
 // slower on R-MAT scale 24 and the kNN workload (kcore_autotune tries it).
-constexpr int kNumOptions = 27;
+constexpr int kNumOptions = 28;
 constexpr long long kTailItemsDefault = 0;
 constexpr long long kTailEntriesDefault = 0;
 constexpr long long kParkSleepDefault = 256;
 // Defaults of the bulk-synchronous schedule (sync mode 2), shared by the
 // handle's options and the no-allocation entry point.
-constexpr int kSliceDefault = 64;          // arcs per work item
+constexpr int kSliceDefault = 32;          // arcs per work item (measured on R-MAT 24: 32 16.45 ms,
+                                           // 64 16.65; kNN equal)
 constexpr int kLocalQueueDefault = 128;    // per-warp local queue (items)
 constexpr int kLocalBatchesDefault = 32;   // local batches per chunk taken
 constexpr int kPrecheckDefault = 64;       // per-warp share from which d~ is read first
 constexpr int kPollSleepDefault = 64;      // grid-barrier poll sleep (ns)
 constexpr int kTimeoutMsDefault = 2000;    // limit of every device-side wait
-constexpr int kScanMin = 2048;             // active-list entries per scanning CTA (at least)
+constexpr int kScanMin = 512;              // active-list entries per scanning CTA (at least; measured
+                                           // on R-MAT 24 / kNN: 2048 17.0 / 6.03 ms, 1024 16.8 / 5.82,
+                                           // 512 16.7 / 5.72)
 constexpr int kMinSlice = 16;  // keeps slice indices below 2^27 (27-bit field of a work item)
 
 // Per-round record (zeroed before launch). Each hot word has its own 128-byte

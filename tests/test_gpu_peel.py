@@ -140,7 +140,7 @@ def test_each_vertex_processed_once(kc):
     st = kc.stats()
     deg = np.diff(off)
     sl = st["slice_arcs"]
-    assert sl == (512 if st["sync_mode"] == 1 else 64)
+    assert sl == (512 if st["sync_mode"] == 1 else 32)
     slices = int(np.sum((deg + sl - 1) // sl))
     # each vertex with arcs is taken once as a whole item (from the global or a
     # warp-local queue) and its list is split into ceil(deg / slice) slices
