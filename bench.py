@@ -922,11 +922,14 @@ PEEL_KERNELS = {1: ("peel_persistent", "peel.cu"), 2: ("peel_bsp", "peel_bsp.cu"
 
 
 def kernel_revision(src: str = "peel_bsp.cu") -> str:
-    """Hash of a peel kernel source, to tie recorded ncu traffic to it."""
+    """Hash of a peel kernel source and the header of its shared layout and
+    defaults, to tie recorded ncu traffic to them."""
     import hashlib
-    p = os.path.join(ROOT, "paper_2502_08042_gb300", "csrc", src)
-    with open(p, "rb") as f:
-        return hashlib.sha1(f.read()).hexdigest()[:12]
+    h = hashlib.sha1()
+    for name in (src, "kcore_peel.h"):
+        with open(os.path.join(ROOT, "paper_2502_08042_gb300", "csrc", name), "rb") as f:
+            h.update(f.read())
+    return h.hexdigest()[:12]
 
 
 def main():
