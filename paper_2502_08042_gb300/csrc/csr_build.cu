@@ -213,16 +213,27 @@ __global__ void __launch_bounds__(kCsrBlock, 6) rs_downsweep(const unsigned long
   }
 }
 
-// Unique keys of each CTA chunk (a key differing from its predecessor).
+// Unique keys of each CTA chunk (a key differing from its predecessor); each
+// thread reads kKeysPerThread keys per tile, with their predecessors.
 __global__ void __launch_bounds__(kCsrBlock) csr_count_unique(const unsigned long long* k, long long N,
                                                               long long chunk, unsigned* cnt) {
   __shared__ unsigned part[kCsrBlock / 32];
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   long long lo = (long long)blockIdx.x * chunk, hi = min(N, lo + chunk);
   unsigned c = 0;
-  for (long long i = lo + tid; i < hi; i += kCsrBlock) {
-    unsigned long long x = k[i];
-    if (x != kSentinel && (i == 0 || k[i - 1] != x)) c++;
+  for (long long ts = lo; ts < hi; ts += kTile) {
+    unsigned long long x[kKeysPerThread], p[kKeysPerThread];
+#pragma unroll
+    for (int q = 0; q < kKeysPerThread; q++) {
+      const long long i = ts + (long long)q * kCsrBlock + tid;
+      x[q] = i < hi ? __ldcs(k + i) : kSentinel;
+      p[q] = i < hi && i > 0 ? __ldcg(k + i - 1) : kSentinel;
+    }
+#pragma unroll
+    for (int q = 0; q < kKeysPerThread; q++) {
+      const long long i = ts + (long long)q * kCsrBlock + tid;
+      if (i < hi && x[q] != kSentinel && (i == 0 || p[q] != x[q])) c++;
+    }
   }
   c = warp_sum(c);
   if (lane == 0) part[warp] = c;
@@ -237,54 +248,74 @@ __global__ void __launch_bounds__(kCsrBlock) csr_count_unique(const unsigned lon
 // Ordered emission of the unique keys: adj[pos] = low Bd bits; the first arc
 // of each source fixes offsets[] for that source and every source without
 // arcs just below it; the last arc fills the offsets of the sources above it.
+// A tile of kTile keys is read coalesced into shared memory, each thread then
+// takes kKeysPerThread consecutive keys (one block scan orders the whole
+// tile), and the tile's unique targets leave through shared memory too.
 __global__ void __launch_bounds__(kCsrBlock) csr_emit(const unsigned long long* k, long long N,
                                                       long long chunk, int B, long long n,
                                                       const unsigned long long* base, int* adj,
                                                       long long* off, long long* m_out) {
+  __shared__ unsigned long long tk[kTile + 2];  // tk[0]: the key before the tile, tk[kTile + 1]: after it
+  __shared__ int ta[kTile];
   __shared__ unsigned part[kCsrBlock / 32];
   __shared__ unsigned long long running;
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   const unsigned long long mask = (1ull << B) - 1;
   long long lo = (long long)blockIdx.x * chunk, hi = min(N, lo + chunk);
   if (tid == 0) running = base[blockIdx.x];
-  __syncthreads();
-  for (long long ts = lo; ts < hi; ts += kCsrBlock) {
-    long long i = ts + tid;
-    bool f = false;
-    unsigned long long x = 0, prev = kSentinel;
-    if (i < hi) {
-      x = k[i];
-      prev = i > 0 ? k[i - 1] : kSentinel;
-      f = x != kSentinel && (i == 0 || prev != x);
+  for (long long ts = lo; ts < hi; ts += kTile) {
+    const int tn = (int)min((long long)kTile, hi - ts);
+    // tk[j + 1] = key ts + j for j < tn, then the key after the tile (if any)
+    for (int j = tid; j <= kTile; j += kCsrBlock) tk[j + 1] = j <= tn && ts + j < N ? k[ts + j] : kSentinel;
+    if (tid == 0) tk[0] = ts > 0 ? k[ts - 1] : kSentinel;
+    __syncthreads();
+    const int j0 = tid * kKeysPerThread;  // this thread's first key, in the tile
+    unsigned flags = 0;
+#pragma unroll
+    for (int q = 0; q < kKeysPerThread; q++) {
+      const int j = j0 + q;
+      const unsigned long long cur = tk[j + 1], prev = tk[j];
+      if (j < tn && cur != kSentinel && (ts + j == 0 || prev != cur)) flags |= 1u << q;
     }
-    unsigned flag = f ? 1u : 0u;
-    unsigned incl = warp_incl_scan(flag, lane);
+    const unsigned cntf = __popc(flags);
+    const unsigned incl = warp_incl_scan(cntf, lane);
     if (lane == 31) part[warp] = incl;
     __syncthreads();
     if (warp == 0) {
-      unsigned p = lane < kCsrBlock / 32 ? part[lane] : 0;
-      unsigned pi = warp_incl_scan(p, lane);
-      if (lane < kCsrBlock / 32) part[lane] = pi - p;
+      unsigned pp = lane < kCsrBlock / 32 ? part[lane] : 0;
+      unsigned pi = warp_incl_scan(pp, lane);
+      if (lane < kCsrBlock / 32) part[lane] = pi - pp;
     }
     __syncthreads();
-    unsigned long long r0 = running;
-    // position of the latest unique key at or before i (this one when f)
-    unsigned long long pos = r0 + part[warp] + incl - 1;
-    if (f) {
-      adj[pos] = (int)(x & mask);
-      long long s = (long long)(x >> B);
-      long long ps = (i == 0 || prev == kSentinel) ? -1 : (long long)(prev >> B);
-      if (s != ps)
-        for (long long v = ps + 1; v <= s; v++) off[v] = (long long)pos;
-    }
-    // the last valid key (unique or a repeat) closes the offsets above its source
-    if (i < hi && x != kSentinel && ((i + 1 == N) || k[i + 1] == kSentinel)) {
-      long long s = (long long)(x >> B);
-      for (long long v = s + 1; v <= n; v++) off[v] = (long long)pos + 1;
-      *m_out = (long long)pos + 1;
+    const unsigned long long r0 = running;
+    unsigned local = part[warp] + incl - cntf;  // unique keys of the tile before this thread's first
+#pragma unroll
+    for (int q = 0; q < kKeysPerThread; q++) {
+      const int j = j0 + q;
+      if (j >= tn) break;
+      const unsigned long long cur = tk[j + 1], prev = tk[j];
+      if ((flags >> q) & 1u) {
+        const unsigned long long pos = r0 + local;
+        ta[local++] = (int)(cur & mask);
+        const long long s = (long long)(cur >> B);
+        const long long ps = (ts + j == 0 || prev == kSentinel) ? -1 : (long long)(prev >> B);
+        if (s != ps)
+          for (long long v = ps + 1; v <= s; v++) off[v] = (long long)pos;
+      }
+      // the last valid key (unique or a repeat) closes the offsets above its source
+      if (cur != kSentinel && tk[j + 2] == kSentinel) {
+        const long long s = (long long)(cur >> B);
+        const long long last = (long long)(r0 + local) - 1;  // position of the latest unique key
+        for (long long v = s + 1; v <= n; v++) off[v] = last + 1;
+        *m_out = last + 1;
+      }
     }
     __syncthreads();
-    if (tid == kCsrBlock - 1) running = r0 + part[warp] + incl;
+    // the tile's unique targets, coalesced
+    if (tid == kCsrBlock - 1) running = r0 + local;
+    __syncthreads();
+    const unsigned nu = (unsigned)(running - r0);
+    for (unsigned j = tid; j < nu; j += kCsrBlock) adj[r0 + j] = ta[j];
     __syncthreads();
   }
 }
