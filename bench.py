@@ -506,6 +506,16 @@ def run_gpu(args):
                    "autotuned": {key: r["tuning"][key] for key in ("block", "ctas_per_sm", "smem_vertices")},
                    "note": "CUDA events around each batched launch; the plain loop is one kcore_decompose per "
                            "graph on the same stream"}
+    served = None
+    if args.workload == "rmat24" and ws == 1 and not args.no_served:
+        R = WORKLOADS["served"]["requests"]
+        runs, serial, _, _ = served_measure(local, R)
+        served = {"workload": f"{R} requests, 95% from 256 graphs of the batch distribution, 5% R-MAT scale "
+                              "20..24 (edge factor 16), host CSR in and coreness out",
+                  "saturation_graphs_per_s": runs[0]["graphs_per_s"],
+                  "poisson": [{key: r[key] for key in ("rate", "graphs_per_s", "p50_ms", "p99_ms")} for r in runs[1:]],
+                  "serial_plain": {key: serial[key] for key in ("graphs_per_s", "p50_ms", "p99_ms", "rate")},
+                  "serial_note": SERIAL_NOTE}
     out = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True,
@@ -540,6 +550,7 @@ def run_gpu(args):
         "sync_floor_ms": sync_floor["ms"],
         "sync_floor": sync_floor,
         **({"batched": batched} if batched else {}),
+        **({"served": served} if served else {}),
         "e2e": e2e,
         # a sampled step is the sampled peel, the two check kernels and the
         # rerun kernel (which returns at once when not needed)
@@ -806,16 +817,23 @@ def cpu_batch_baseline(spec, gv, G, sample: int = 256):
 
 
 # ------------------------------------------------------------------ served
-def run_served(args):
+SERIAL_NOTE = ("serial plain launches (kcore_decompose_host per request): each service time measured back to "
+               "back, then placed on the same arrival timeline (a request starts at its arrival or when the "
+               "previous one finishes); arrivals are not replayed")
+
+
+def served_measure(local: int, R: int):
+    """The served workload on one GPU: R requests (95% drawn from 256 graphs of
+    the batch distribution, 5% from one R-MAT graph per scale 20..24) through a
+    KCoreServer, all at once (saturation) and as Poisson arrivals at 0.5x and
+    0.8x the saturation rate; then serial plain launches over the same
+    requests. Returns (runs, serial, h2d bytes, d2h bytes)."""
     import torch
 
     import graphgen as gg
     from paper_2502_08042_gb300 import KCore, KCoreServer
 
-    ws, rank, local = dist_env()
-    torch.cuda.set_device(local)
     dev = torch.device("cuda", local)
-    R = WORKLOADS["served"]["requests"]
     rng = np.random.default_rng(11)
     k = KCore(local)
     # distinct graphs: 256 from the batch distribution, one R-MAT per scale 20..24
@@ -899,8 +917,23 @@ def run_served(args):
         busy += dt
     lat = (fin - arrive) * 1e3
     serial = {"graphs_per_s": R / busy, "p50_ms": float(np.percentile(lat, 50)),
-              "p99_ms": float(np.percentile(lat, 99)), "rate": rate,
-              "note": "latency of serial service at the same arrival times"}
+              "p99_ms": float(np.percentile(lat, 99)), "rate": rate, "note": SERIAL_NOTE}
+    h2d = int(sum(8 * len(o) + 4 * len(a) for o, a in reqs))
+    d2h = int(sum(4 * (len(o) - 1) + 4 for o, _ in reqs))
+    k.close()
+    del graphs, large, reqs, outs
+    torch.cuda.empty_cache()
+    return runs, serial, h2d, d2h
+
+
+def run_served(args):
+    import torch
+
+    ws, rank, local = dist_env()
+    torch.cuda.set_device(local)
+    R = WORKLOADS["served"]["requests"]
+    runs, serial, h2d, d2h = served_measure(local, R)
+    sat = runs[0]
     out = {
         "metric": METRIC, "value": sat["graphs_per_s"], "unit": "graphs/s", "n_gpus": 1,
         "steps": 1, "warmup": 1, "ms_per_step": sat["wall_s"] * 1e3, "higher_is_better": True,
@@ -910,8 +943,7 @@ def run_served(args):
                    "requests": R},
         "served": runs, "serial_plain": serial,
         "e2e": {"value": sat["graphs_per_s"], "unit": "graphs/s",
-                "h2d_bytes_per_step": int(sum(8 * len(o) + 4 * len(a) for o, a in reqs)),
-                "d2h_bytes_per_step": int(sum(4 * (len(o) - 1) + 4 for o, _ in reqs))},
+                "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
         "gpu_launches": None,
     }
     emit(out)
@@ -954,6 +986,8 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-batched", action="store_true",
                     help="default workload: skip the batched sub-record measured after the main line")
+    ap.add_argument("--no-served", action="store_true",
+                    help="default workload: skip the served sub-record measured after the main line")
     args = ap.parse_args()
     if args.impl == "reference":
         run_reference(args)

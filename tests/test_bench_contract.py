@@ -54,3 +54,31 @@ def test_recorded_traffic_is_tied_to_a_kernel_revision():
     assert len(rec["kernel_rev"]) == len(rev) == 12
     # traffic at or above the algorithmic bytes (a copy cannot move less)
     assert rec["dram_bytes_per_launch"] >= bench.algorithmic_bytes(1 << 24, 520762754)
+
+
+def test_cpu_baseline_protocol_on_a_small_graph():
+    """The oracle is timed on the graph it is given, one warm-up then the mean
+    of the runs (the paper's protocol, Sec. 6), one host core; the value is
+    undirected edges per second of the mean."""
+    import graphgen as gg
+    import oracle
+    n, s, d = gg.disjoint_union((2000, *gg.er(2000, 9000, seed=4)), gg.staircase(30))
+    off, adj = oracle.build_csr(n, s, d)
+    cb = bench.cpu_oracle_baseline(n, off, adj, "a test graph", warmup=1, runs=3)
+    assert cb["kind"] == "oracle" and cb["cores"] == 1 and cb["unit"] == bench.UNIT
+    assert cb["s_min"] <= cb["s_mean"]
+    assert abs(cb["value"] - (len(adj) // 2) / cb["s_mean"]) <= 1e-6 * cb["value"]
+    assert "a test graph" in cb["sample"] and "mean of 3 runs" in cb["sample"]
+
+
+def test_reference_arm_names_the_gpu_arms_workload():
+    """The reference arm decomposes the GPU arm's own graph and names it the
+    same way, so both lines describe the same configuration."""
+    import inspect
+    src = inspect.getsource(bench.run_reference)
+    assert "workload_name(args.workload, w)" in src and "make_edges(w)" in src
+    assert bench.workload_name("rmat24", bench.WORKLOADS["rmat24"]) == "rmat24: R-MAT scale 24 edge factor 16"
+
+
+def test_serial_baseline_is_described_as_placed_on_the_timeline():
+    assert "not replayed" in bench.SERIAL_NOTE and "arrival timeline" in bench.SERIAL_NOTE
