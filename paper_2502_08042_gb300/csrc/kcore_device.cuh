@@ -53,6 +53,28 @@ __device__ __forceinline__ int ld_cg_keep(const int* a, uint64_t pol) {
 __device__ __forceinline__ void st_keep(int* a, int v, uint64_t pol) {
   asm volatile("st.global.L2::cache_hint.s32 [%0], %1, %2;" ::"l"(a), "r"(v), "l"(pol) : "memory");
 }
+// Loads of data written by other CTAs earlier in the same kernel and read
+// once (queue items, active-list entries): read from L2 only (L1 lines are
+// not coherent), evict-first in L2 so the induced degrees stay resident.
+__device__ __forceinline__ uint64_t l2_evict_first_policy() {
+  uint64_t p;
+  asm volatile("createpolicy.fractional.L2::evict_first.b64 %0, 1.0;" : "=l"(p));
+  return p;
+}
+__device__ __forceinline__ unsigned long long ld_once_u64(const unsigned long long* a, uint64_t pol) {
+  unsigned long long v;
+  asm volatile("ld.global.cg.L2::cache_hint.u64 %0, [%1], %2;" : "=l"(v) : "l"(a), "l"(pol) : "memory");
+  return v;
+}
+__device__ __forceinline__ int ld_once_s32(const int* a, uint64_t pol) {
+  int v;
+  asm volatile("ld.global.cg.L2::cache_hint.s32 %0, [%1], %2;" : "=r"(v) : "l"(a), "l"(pol) : "memory");
+  return v;
+}
+__device__ __forceinline__ void st_once_s32(int* a, int v, uint64_t pol) {
+  asm volatile("st.global.cg.L2::cache_hint.s32 [%0], %1, %2;" ::"l"(a), "r"(v), "l"(pol) : "memory");
+}
+
 // atomic add returning the old value, with an L2 eviction-priority hint
 __device__ __forceinline__ int atom_add_keep(int* a, int v, uint64_t pol) {
   int old;

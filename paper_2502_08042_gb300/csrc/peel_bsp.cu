@@ -358,7 +358,7 @@ __device__ ScanOut scan_range(const PeelArgs& a, Shared& sh, RoundRec* R, unsign
 #pragma unroll
     for (int q = 0; q < kTile; q++) {
       const long long i = tile + (long long)q * kBlock + tid;
-      v[q] = i < hi ? (Ain ? __ldcg(Ain + i) : (int)i) : -1;
+      v[q] = i < hi ? (Ain ? ld_once_s32(Ain + i, l2_evict_first_policy()) : (int)i) : -1;
     }
 #pragma unroll
     for (int q = 0; q < kTile; q++) {
@@ -435,7 +435,7 @@ __device__ ScanOut scan_range(const PeelArgs& a, Shared& sh, RoundRec* R, unsign
     int ps = ex >> 16;
 #pragma unroll
     for (int q = 0; q < kTile; q++) {
-      if ((keep >> q) & 1u) Aout[pa++] = v[q];
+      if ((keep >> q) & 1u) st_once_s32(Aout + pa++, v[q], l2_evict_first_policy());
       if ((take >> q) & 1u) sh.stage[ps++] = v[q];
     }
     if (Aover) {
@@ -461,8 +461,8 @@ __device__ ScanOut scan_range(const PeelArgs& a, Shared& sh, RoundRec* R, unsign
         e0[k] = e1[k] = 0;
         if (i < ntaken) {
           const int x = sh.stage[i];
-          e0[k] = a.off[x];
-          e1[k] = a.off[x + 1];
+          e0[k] = __ldcs(a.off + x);
+          e1[k] = __ldcs(a.off + x + 1);
           a.core[x] = take_val;
           if constexpr (kSample) a.stamp[x] = stamp_val;
         }
@@ -566,8 +566,8 @@ __device__ __forceinline__ void push_crossed(const PeelArgs& a, ShT<kSample>& sh
   long long e0 = 0, e1 = 0;
   int nsl = 0;
   if (flag) {
-    e0 = a.off[u];
-    e1 = a.off[u + 1];
+    e0 = __ldcs(a.off + u);
+    e1 = __ldcs(a.off + u + 1);
     nsl = (int)((e1 - e0 + a.slice - 1) / a.slice);
     // its first adjacency line is read next, here or by another warp
     if (e1 > e0) asm volatile("prefetch.global.L2 [%0];" ::"l"(a.adj + e0));
@@ -794,7 +794,7 @@ __device__ void run_pass(const PeelArgs& a, ShT<kSample>& sh, const PassCtx& pc,
   const unsigned long long e = b + share + (gw < rem ? 1 : 0);
   for (unsigned long long pos = b; pos < e; pos += kTake) {
     const int c = (int)min((unsigned long long)kTake, e - pos);
-    const unsigned long long item = lane < c ? __ldcg(a.Q + pos + lane) : 0;
+    const unsigned long long item = lane < c ? ld_once_u64(a.Q + pos + lane, l2_evict_first_policy()) : 0;
     process_items<kWin, kSample, kCombine>(a, sh, pc, item, c, warp, lane);
     if (lane == 0) sh.w_items[warp] += c;
     drain_local<kWin, kSample, kCombine>(a, sh, pc, warp, lane);
@@ -885,7 +885,7 @@ __device__ void run_hist(const PeelArgs& a, Shared& sh, const PassCtx& pc, unsig
   const unsigned long long e = b + share + (gw < rem ? 1 : 0);
   for (unsigned long long pos = b; pos < e; pos += kTake) {
     const int c = (int)min((unsigned long long)kTake, e - pos);
-    const unsigned long long item = lane < c ? __ldcg(a.Q + pos + lane) : 0;
+    const unsigned long long item = lane < c ? ld_once_u64(a.Q + pos + lane, l2_evict_first_policy()) : 0;
     hist_items<kTouched>(a, sh, pc, item, c, warp, lane);
     if (lane == 0) sh.w_items[warp] += c;
   }
