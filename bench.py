@@ -610,6 +610,35 @@ def batch_subset(spec, gv, eoff, s, d, idx):
     return sub, gv2, eoff2, s2, d2
 
 
+def gather_batch_results(core_local, kmax_local, own, gv_global, ws: int, rank: int):
+    """Multi-GPU batched run: assembles on rank 0 the coreness of every graph
+    of the batch from the ranks' shares. Rank r peeled the graphs own[r]
+    (ascending global indices) and holds their coreness concatenated in that
+    order (graph-local vertex order) and their k_max. Returns (coreness over
+    all vertices of the batch, k_max of every graph) on rank 0, None elsewhere.
+    No device collective: host objects are gathered over the process group."""
+    import torch.distributed as dist
+    parts = [None] * ws if rank == 0 else None
+    dist.gather_object((np.asarray(own, np.int64), np.asarray(core_local, np.int32),
+                        np.asarray(kmax_local, np.int32)), parts, dst=0)
+    if rank != 0:
+        return None
+    gv = np.asarray(gv_global, np.int64)
+    G = len(gv) - 1
+    core = np.full(int(gv[-1]), -1, np.int32)
+    kmax = np.full(G, -1, np.int32)
+    for idx, c, km in parts:
+        pos = 0
+        for j, g in enumerate(idx):
+            n = int(gv[g + 1] - gv[g])
+            core[gv[g]:gv[g + 1]] = c[pos:pos + n]
+            kmax[g] = km[j]
+            pos += n
+        if pos != len(c):
+            raise ValueError("a rank's coreness does not match its graphs")
+    return core, kmax
+
+
 def batched_measure(local: int, steps: int, warmup: int, G_total: int, ws: int = 1, rank: int = 0,
                     e2e: bool = True):
     """The batched workload on one GPU: generation, segmented CSR build, the
@@ -626,6 +655,7 @@ def batched_measure(local: int, steps: int, warmup: int, G_total: int, ws: int =
     dev = torch.device("cuda", local)
     t0 = time.perf_counter()
     spec, gv, eoff, s, d = _batch_inputs(G_total)
+    gv_global, own = gv, None
     if ws > 1:
         # graphs are independent: each rank peels its longest-processing-time
         # share by arc count (strong scaling, no data-path collective)
@@ -676,6 +706,13 @@ def batched_measure(local: int, steps: int, warmup: int, G_total: int, ws: int =
     st = k.stats()
     total_ms = sum(a.elapsed_time(b) for a, b in evs)
     ref = core.clone()
+    gathered = None
+    if ws > 1:
+        # the batch's result assembled on rank 0's host from every rank's share
+        res = gather_batch_results(core.cpu().numpy(), kmax.cpu().numpy(), own, gv_global, ws, rank)
+        if res is not None:
+            gathered = {"vertices": int(len(res[0])), "graphs": int(len(res[1])),
+                        "all_assigned": bool((res[1] >= 0).all())}
     # a loop of plain single-graph launches over the same graphs (own handle,
     # workspace sized once for the largest graph)
     offh = off.cpu().numpy()
@@ -731,7 +768,8 @@ def batched_measure(local: int, steps: int, warmup: int, G_total: int, ws: int =
     del off, adj, core, kmax, flush, gvd
     torch.cuda.empty_cache()
     return dict(spec=spec, gv=gv, G=G, N=N, M=M, gen_s=gen_s, csr_ms=csr_ms, tuning=tuning, grid=st["grid"],
-                total_ms=total_ms, loop_ms=loop_ms, same=same, e2e_ms=e2e_ms, clocks=clk.summary())
+                total_ms=total_ms, loop_ms=loop_ms, same=same, e2e_ms=e2e_ms, clocks=clk.summary(),
+                gathered=gathered)
 
 
 def run_batched(args):
@@ -772,6 +810,7 @@ def run_batched(args):
                    "l2": "inputs larger than L2 and a 258 MB buffer written between timed steps"},
         "plain_loop": {"graphs_per_s": G / (r["loop_ms"] / 1e3), "ms": r["loop_ms"],
                        "identical_output": r["same"], "speedup": r["loop_ms"] / ms},
+        **({"gathered_on_host": r["gathered"]} if r["gathered"] else {}),
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                      "frac": achieved / peak, "traffic": None, "peak_kind": peak_kind,
                      "algorithmic_bytes": bmin, "kernel": "batch_peel"},

@@ -125,3 +125,63 @@ def test_lpt_partition_and_subset():
     for j, g in enumerate(idx):
         np.testing.assert_array_equal(s2[eoff2[j]:eoff2[j + 1]], s[eoff[g]:eoff[g + 1]])
         np.testing.assert_array_equal(d2[eoff2[j]:eoff2[j + 1]], d[eoff[g]:eoff[g + 1]])
+
+
+def _gather_rank(rank, ws, port, G, out):
+    os.environ.update(MASTER_ADDR="127.0.0.1", MASTER_PORT=str(port), WORLD_SIZE=str(ws), RANK=str(rank),
+                      LOCAL_RANK=str(rank))
+    sys.path.insert(0, ROOT)
+    import numpy as np
+    import bench
+    import oracle
+    dist.init_process_group("gloo", rank=rank, world_size=ws)
+    try:
+        spec, gv, eoff, s, d = bench._batch_inputs(G)
+        own = bench.lpt_partition(eoff[1:] - eoff[:-1], ws)[rank]
+        sub, gv2, eoff2, s2, d2 = bench.batch_subset(spec, gv, eoff, s, d, own)
+        # this rank's share peeled by the oracle, graph by graph
+        cores, kms = [], []
+        for j in range(len(own)):
+            n = int(gv2[j + 1] - gv2[j])
+            off, adj = oracle.build_csr(n, s2[eoff2[j]:eoff2[j + 1]], d2[eoff2[j]:eoff2[j + 1]])
+            c = oracle.bz(n, off, adj)
+            cores.append(c)
+            kms.append(int(c.max()) if n else 0)
+        core = np.concatenate(cores) if cores else np.zeros(0, np.int32)
+        res = bench.gather_batch_results(core, np.array(kms, np.int32), own, gv, ws, rank)
+        out.put((rank, None if res is None else (res[0].tolist(), res[1].tolist())))
+        dist.barrier()
+    finally:
+        dist.destroy_process_group()
+
+
+def test_batched_results_gathered_on_rank_0():
+    """Two gloo ranks each peel their longest-processing-time share of a batch;
+    rank 0 assembles the coreness of every graph in the batch's own vertex
+    order, equal to peeling the whole batch in one process."""
+    ws, port, G = 2, _free_port(), 10
+    ctx = mp.get_context("spawn")
+    out = ctx.Queue()
+    procs = [ctx.Process(target=_gather_rank, args=(r, ws, port, G, out)) for r in range(ws)]
+    for p in procs:
+        p.start()
+    res = dict(out.get(timeout=300) for _ in range(ws))
+    for p in procs:
+        p.join(timeout=60)
+        assert p.exitcode == 0
+    assert res[1] is None and res[0] is not None
+    sys.path.insert(0, ROOT)
+    import numpy as np
+    import bench
+    import oracle
+    spec, gv, eoff, s, d = bench._batch_inputs(G)
+    want, want_km = [], []
+    for g in range(G):
+        n = int(gv[g + 1] - gv[g])
+        off, adj = oracle.build_csr(n, s[eoff[g]:eoff[g + 1]], d[eoff[g]:eoff[g + 1]])
+        c = oracle.bz(n, off, adj)
+        want.append(c)
+        want_km.append(int(c.max()) if n else 0)
+    core, km = res[0]
+    np.testing.assert_array_equal(np.array(core, np.int32), np.concatenate(want))
+    assert km == want_km
