@@ -8,14 +8,19 @@
 //      error status).
 //   2. stable LSD radix sort of the keys over their 2B significant bits, 8-bit
 //      digits. Each CTA owns a contiguous chunk; a pass is an upsweep (digit
-//      histogram per CTA), a scan of the 256 x CTAs histogram, and a downsweep
-//      that ranks each 2,048-key tile in shared memory (warp match for the
-//      within-iteration rank) and writes runs of equal digits contiguously,
-//      while the next tile arrives by asynchronous copy (cp.async).
+//      histogram per CTA), a scan of each digit's row of the 256 x CTAs
+//      histogram (one CTA per digit), and a downsweep that ranks each
+//      2,048-key tile in shared memory and writes runs of equal digits
+//      contiguously, while the next tile arrives by asynchronous copy
+//      (cp.async). A key's rank within its warp and digit comes from one pass:
+//      the lanes holding a digit elect a leader (warp match), which adds their
+//      number to the warp's counter for that digit and hands the old value on.
 //   3. unique + emit: keys equal to their predecessor are dropped; the rest
 //      are written in order as adj[] (low B bits), and the first arc of each
 //      source vertex fixes offsets[] (vertices without arcs take the next
-//      vertex's offset).
+//      vertex's offset). Keys are read striped (a warp reads 32 consecutive
+//      keys), the predecessor comes from the next lower lane, and the
+//      positions from warp ballots, so no key passes through shared memory.
 // Lists come out ascending and duplicate-free, the canonical form of the CPU
 // builder, so the two are comparable bit for bit.
 #include <climits>
@@ -84,12 +89,16 @@ __global__ void __launch_bounds__(kCsrBlock) rs_upsweep(const unsigned long long
   hist[(long long)tid * gridDim.x + blockIdx.x] = s;
 }
 
-// Exclusive scan of a uint32 array into uint64 (one CTA of 1024 threads).
+// Exclusive scans of uint32 rows into uint64: CTA r (1024 threads) scans
+// in[r * len, (r + 1) * len) into out[] at the same place and, if totals is
+// given, writes the row's sum to totals[r].
 __global__ void __launch_bounds__(1024) scan_u32_to_u64(const unsigned* in, unsigned long long* out,
-                                                        long long len) {
+                                                        long long len, unsigned long long* totals) {
   __shared__ unsigned long long part[32];
   __shared__ unsigned long long carry;
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  in += (long long)blockIdx.x * len;
+  out += (long long)blockIdx.x * len;
   if (tid == 0) carry = 0;
   __syncthreads();
   for (long long base = 0; base < len; base += 1024) {
@@ -110,24 +119,40 @@ __global__ void __launch_bounds__(1024) scan_u32_to_u64(const unsigned* in, unsi
     if (tid == 1023) carry = c + part[warp] + incl;
     __syncthreads();
   }
+  if (totals && tid == 0) totals[blockIdx.x] = carry;
 }
 
 // Stable scatter of one radix pass. Each CTA walks its chunk tile by tile, in
-// order; offs[d * G + g] is where its first key of digit d goes.
-__global__ void __launch_bounds__(kCsrBlock, 6) rs_downsweep(const unsigned long long* in,
+// order. offs[d * G + g] counts the keys of digit d in the chunks before g,
+// rowtot[d] all keys of digit d; so the CTA's first key of digit d goes after
+// every key of a smaller digit and the digit-d keys of earlier chunks.
+static_assert(kCsrBlock == 256, "one thread per 8-bit digit");
+__global__ void __launch_bounds__(kCsrBlock, 5) rs_downsweep(const unsigned long long* in,
                                                           unsigned long long* out, long long N,
                                                           long long chunk, int shift,
-                                                          const unsigned long long* offs) {
+                                                          const unsigned long long* offs,
+                                                          const unsigned long long* rowtot) {
   __shared__ unsigned long long buf[kTile];
   __shared__ __align__(16) unsigned long long stage[kTile];  // the next tile, copied asynchronously
-  __shared__ unsigned wbase[kCsrBlock / 32][256];
-  __shared__ unsigned local_off[256];
-  __shared__ unsigned tile_cnt[256];
-  __shared__ unsigned long long run[256];
+  __shared__ unsigned wcnt[kCsrBlock / 32][256];  // keys per (warp, digit), then their tile offsets
+  __shared__ unsigned long long dstb[256];        // output position of the tile's first key of digit d, minus its tile offset
+  __shared__ unsigned long long part64[kCsrBlock / 32];
   __shared__ unsigned part[kCsrBlock / 32];
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   const int G = gridDim.x;
-  run[tid] = offs[(long long)tid * G + blockIdx.x];
+  const unsigned lt = lanemask_lt();
+  // run: where this CTA's next key of digit tid goes
+  unsigned long long run;
+  {
+    const unsigned long long rt = rowtot[tid];
+    const unsigned long long incl = warp_incl_scan(rt, lane);
+    if (lane == 31) part64[warp] = incl;
+    for (int i = tid; i < (kCsrBlock / 32) * 256; i += kCsrBlock) (&wcnt[0][0])[i] = 0;
+    __syncthreads();
+    unsigned long long before = 0;
+    for (int w = 0; w < warp; w++) before += part64[w];
+    run = before + incl - rt + offs[(long long)tid * G + blockIdx.x];
+  }
   long long lo = (long long)blockIdx.x * chunk, hi = min(N, lo + chunk);
   // 16-byte asynchronous copies of a tile's keys into `stage` (pairs of keys;
   // a last odd key is copied with its neighbour, which lies inside the
@@ -143,32 +168,36 @@ __global__ void __launch_bounds__(kCsrBlock, 6) rs_downsweep(const unsigned long
   if (lo < hi) prefetch(lo);
   for (long long ts = lo; ts < hi; ts += kTile) {
     const long long tn = min((long long)kTile, hi - ts);
-    for (int i = tid; i < (kCsrBlock / 32) * 256; i += kCsrBlock) (&wbase[0][0])[i] = 0;
     asm volatile("cp.async.wait_all;" ::: "memory");
     __syncthreads();
     unsigned long long k[kKeysPerThread];
-    int dg[kKeysPerThread];
+    unsigned rk[kKeysPerThread / 2];  // ranks below 2,048: two per word
+    // key it of this thread is key j_of(it) of the tile; 256 is the digit of no key
+    auto j_of = [&](int it) { return warp * (kKeysPerThread * 32) + it * 32 + lane; };
+    auto dg_of = [&](int it) { return j_of(it) < tn ? digit_of(k[it], shift) : 256; };
 #pragma unroll
-    for (int it = 0; it < kKeysPerThread; it++) {
-      long long j = (long long)warp * (kKeysPerThread * 32) + it * 32 + lane;
-      k[it] = j < tn ? stage[j] : 0;
-    }
+    for (int it = 0; it < kKeysPerThread; it++) k[it] = j_of(it) < tn ? stage[j_of(it)] : 0;
     __syncthreads();  // the stage is read: copy the next tile into it
     if (ts + kTile < hi) prefetch(ts + kTile);
+    // rank within (warp, digit) in key order: iterations in order, lanes in
+    // order within an iteration
 #pragma unroll
     for (int it = 0; it < kKeysPerThread; it++) {
-      long long j = (long long)warp * (kKeysPerThread * 32) + it * 32 + lane;
-      dg[it] = 256;  // invalid lane
-      if (j < tn) {
-        dg[it] = digit_of(k[it], shift);
-        atomicAdd(&wbase[warp][dg[it]], 1u);
-      }
+      const int dg = dg_of(it);
+      const unsigned peers = __match_any_sync(kFull, dg);
+      const int leader = __ffs(peers) - 1;
+      unsigned old = 0;
+      if (lane == leader && dg < 256) old = atomicAdd(&wcnt[warp][dg], (unsigned)__popc(peers));
+      old = __shfl_sync(kFull, old, leader);
+      const unsigned r = old + __popc(peers & lt);
+      if (it & 1) rk[it >> 1] |= r << 16;
+      else rk[it >> 1] = r;
     }
     __syncthreads();
-    // per digit (thread d): tile count, then exclusive scan over digits
+    // per digit (thread d): tile count, exclusive offsets over digits, then
+    // over warps
     unsigned tc = 0;
-    for (int w = 0; w < kCsrBlock / 32; w++) tc += wbase[w][tid];
-    tile_cnt[tid] = tc;
+    for (int w = 0; w < kCsrBlock / 32; w++) tc += wcnt[w][tid];
     unsigned incl = warp_incl_scan(tc, lane);
     if (lane == 31) part[warp] = incl;
     __syncthreads();
@@ -178,62 +207,96 @@ __global__ void __launch_bounds__(kCsrBlock, 6) rs_downsweep(const unsigned long
       if (lane < kCsrBlock / 32) part[lane] = pi - p;
     }
     __syncthreads();
-    unsigned lo_d = part[warp] + incl - tc;
-    local_off[tid] = lo_d;
+    const unsigned lo_d = part[warp] + incl - tc;
     unsigned acc = lo_d;
     for (int w = 0; w < kCsrBlock / 32; w++) {
-      unsigned c = wbase[w][tid];
-      wbase[w][tid] = acc;
+      unsigned c = wcnt[w][tid];
+      wcnt[w][tid] = acc;
       acc += c;
     }
+    dstb[tid] = run - lo_d;  // modulo 2^64: adding a tile offset of digit tid lands at or after run
+    run += tc;
     __syncthreads();
-    // ranks in key order: warps own consecutive sub-ranges, iterations go in order
 #pragma unroll
     for (int it = 0; it < kKeysPerThread; it++) {
-      unsigned peers = __match_any_sync(kFull, dg[it]);
-      int rank = __popc(peers & lanemask_lt());
-      unsigned b = 0;
-      if (dg[it] < 256) {
-        b = wbase[warp][dg[it]];
-        buf[b + rank] = k[it];
-      }
-      __syncwarp();
-      if (dg[it] < 256 && rank == 0) wbase[warp][dg[it]] = b + __popc(peers);
-      __syncwarp();
+      const int dg = dg_of(it);
+      if (dg < 256) buf[wcnt[warp][dg] + ((rk[it >> 1] >> (16 * (it & 1))) & 0xffffu)] = k[it];
     }
     __syncthreads();
+    for (int w = 0; w < kCsrBlock / 32; w++) wcnt[w][tid] = 0;  // for the next tile
     for (int j = tid; j < tn; j += kCsrBlock) {
-      unsigned long long key = buf[j];
-      int d = digit_of(key, shift);
-      out[run[d] + (unsigned long long)(j - local_off[d])] = key;
+      const unsigned long long key = buf[j];
+      out[dstb[digit_of(key, shift)] + (unsigned long long)j] = key;
     }
-    __syncthreads();
-    run[tid] += tile_cnt[tid];
-    __syncthreads();
   }
 }
 
-// Unique keys of each CTA chunk (a key differing from its predecessor); each
-// thread reads kKeysPerThread keys per tile, with their predecessors.
-__global__ void __launch_bounds__(kCsrBlock) csr_count_unique(const unsigned long long* k, long long N,
+// A tile is kRows rows of kCsrBlock consecutive keys; a thread takes one key
+// per row (a warp 32 consecutive keys). A key's neighbours come from
+// the next lower and higher lanes; at a warp's edges from the keys the
+// neighbouring warps publish in shared memory, and at the tile's edges from
+// the keys just before and after it (read by threads 0 and kCsrBlock - 1).
+template <int kRows>
+struct TileEdges {
+  unsigned long long first[kRows][kCsrBlock / 32];
+  unsigned long long last[kRows][kCsrBlock / 32];
+};
+
+template <int kRows>
+__device__ __forceinline__ void publish_edges(TileEdges<kRows>& e, const unsigned long long* x, int lane, int warp) {
+#pragma unroll
+  for (int q = 0; q < kRows; q++) {
+    if (lane == 0) e.first[q][warp] = x[q];
+    if (lane == 31) e.last[q][warp] = x[q];
+  }
+}
+
+// predecessor of this thread's key in row q (pre: the key before the tile, held by thread 0)
+template <int kRows>
+__device__ __forceinline__ unsigned long long pred_key(const TileEdges<kRows>& e, unsigned long long xq, int q, int lane,
+                                                       int warp, unsigned long long pre) {
+  const unsigned long long up = __shfl_up_sync(kFull, xq, 1);
+  if (lane > 0) return up;
+  if (warp > 0) return e.last[q][warp - 1];
+  return q > 0 ? e.last[q - 1][kCsrBlock / 32 - 1] : pre;
+}
+
+// successor (post: the key after the tile, held by thread kCsrBlock - 1)
+template <int kRows>
+__device__ __forceinline__ unsigned long long succ_key(const TileEdges<kRows>& e, unsigned long long xq, int q, int lane,
+                                                       int warp, unsigned long long post) {
+  const unsigned long long dn = __shfl_down_sync(kFull, xq, 1);
+  if (lane < 31) return dn;
+  if (warp < kCsrBlock / 32 - 1) return e.first[q][warp + 1];
+  return q < kRows - 1 ? e.first[q + 1][0] : post;
+}
+
+// Unique keys of each CTA chunk (a key differing from its predecessor).
+__global__ void __launch_bounds__(kCsrBlock, 5) csr_count_unique(const unsigned long long* k, long long N,
                                                               long long chunk, unsigned* cnt) {
+  constexpr int kRows = kKeysPerThread;
+  __shared__ TileEdges<kRows> edges;
   __shared__ unsigned part[kCsrBlock / 32];
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   long long lo = (long long)blockIdx.x * chunk, hi = min(N, lo + chunk);
   unsigned c = 0;
   for (long long ts = lo; ts < hi; ts += kTile) {
-    unsigned long long x[kKeysPerThread], p[kKeysPerThread];
+    unsigned long long x[kRows];
 #pragma unroll
-    for (int q = 0; q < kKeysPerThread; q++) {
+    for (int q = 0; q < kRows; q++) {
       const long long i = ts + (long long)q * kCsrBlock + tid;
       x[q] = i < hi ? __ldcs(k + i) : kSentinel;
-      p[q] = i < hi && i > 0 ? __ldcg(k + i - 1) : kSentinel;
     }
+    const unsigned long long pre = tid == 0 && ts > 0 ? __ldcg(k + ts - 1) : kSentinel;
+    publish_edges(edges, x, lane, warp);
+    __syncthreads();
 #pragma unroll
-    for (int q = 0; q < kKeysPerThread; q++) {
+    for (int q = 0; q < kRows; q++) {
       const long long i = ts + (long long)q * kCsrBlock + tid;
-      if (i < hi && x[q] != kSentinel && (i == 0 || p[q] != x[q])) c++;
+      const unsigned long long p = pred_key(edges, x[q], q, lane, warp, pre);
+      if (i < hi && x[q] != kSentinel && (i == 0 || p != x[q])) c++;
     }
+    __syncthreads();  // the edges are read: the next tile may publish its own
   }
   c = warp_sum(c);
   if (lane == 0) part[warp] = c;
@@ -245,78 +308,82 @@ __global__ void __launch_bounds__(kCsrBlock) csr_count_unique(const unsigned lon
   }
 }
 
-// Ordered emission of the unique keys: adj[pos] = low Bd bits; the first arc
-// of each source fixes offsets[] for that source and every source without
-// arcs just below it; the last arc fills the offsets of the sources above it.
-// A tile of kTile keys is read coalesced into shared memory, each thread then
-// takes kKeysPerThread consecutive keys (one block scan orders the whole
-// tile), and the tile's unique targets leave through shared memory too.
-__global__ void __launch_bounds__(kCsrBlock) csr_emit(const unsigned long long* k, long long N,
+// Ordered emission of the unique keys: adj[pos] = low B bits; the first arc of
+// each source fixes offsets[] for that source and every source without arcs
+// just below it; the last arc fills the offsets of the sources above it. A
+// unique key's position is the chunk's base, plus the unique keys of earlier
+// rows and of earlier warps in its row (one warp scans the tile's rows x warps
+// counts), plus those of lower lanes (a ballot).
+__global__ void __launch_bounds__(kCsrBlock, 5) csr_emit(const unsigned long long* k, long long N,
                                                       long long chunk, int B, long long n,
                                                       const unsigned long long* base, int* adj,
                                                       long long* off, long long* m_out) {
-  __shared__ unsigned long long tk[kTile + 2];  // tk[0]: the key before the tile, tk[kTile + 1]: after it
-  __shared__ int ta[kTile];
-  __shared__ unsigned part[kCsrBlock / 32];
-  __shared__ unsigned long long running;
+  constexpr int kW = kCsrBlock / 32;
+  constexpr int kRows = 4;  // a tile of kRows * kCsrBlock keys (chunks are whole tiles of either size)
+  constexpr int kT = kRows * kCsrBlock;
+  static_assert(kRows * kW == 32 && kTile % kT == 0, "the tile's counts are scanned by one warp, one per lane");
+  __shared__ TileEdges<kRows> edges;
+  __shared__ unsigned cnt[kRows * kW];  // unique keys per (row, warp), then their offsets in the tile
+  __shared__ unsigned tile_total;
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   const unsigned long long mask = (1ull << B) - 1;
+  const unsigned lt = lanemask_lt();
   long long lo = (long long)blockIdx.x * chunk, hi = min(N, lo + chunk);
-  if (tid == 0) running = base[blockIdx.x];
-  for (long long ts = lo; ts < hi; ts += kTile) {
-    const int tn = (int)min((long long)kTile, hi - ts);
-    // tk[j + 1] = key ts + j for j < tn, then the key after the tile (if any)
-    for (int j = tid; j <= kTile; j += kCsrBlock) tk[j + 1] = j <= tn && ts + j < N ? k[ts + j] : kSentinel;
-    if (tid == 0) tk[0] = ts > 0 ? k[ts - 1] : kSentinel;
-    __syncthreads();
-    const int j0 = tid * kKeysPerThread;  // this thread's first key, in the tile
-    unsigned flags = 0;
+  unsigned long long running = base[blockIdx.x];
+  for (long long ts = lo; ts < hi; ts += kT) {
+    unsigned long long x[kRows];
 #pragma unroll
-    for (int q = 0; q < kKeysPerThread; q++) {
-      const int j = j0 + q;
-      const unsigned long long cur = tk[j + 1], prev = tk[j];
-      if (j < tn && cur != kSentinel && (ts + j == 0 || prev != cur)) flags |= 1u << q;
+    for (int q = 0; q < kRows; q++) {
+      const long long i = ts + (long long)q * kCsrBlock + tid;
+      x[q] = i < hi ? __ldcs(k + i) : kSentinel;
     }
-    const unsigned cntf = __popc(flags);
-    const unsigned incl = warp_incl_scan(cntf, lane);
-    if (lane == 31) part[warp] = incl;
+    const unsigned long long pre = tid == 0 && ts > 0 ? __ldcg(k + ts - 1) : kSentinel;
+    // chunks are whole tiles, so a key past the tile's end lies in the next chunk or past N
+    const unsigned long long post = tid == kCsrBlock - 1 && ts + kT < N ? __ldcg(k + ts + kT) : kSentinel;
+    publish_edges(edges, x, lane, warp);
+    __syncthreads();
+    unsigned bal[kRows];
+    int ps[kRows];  // source of the predecessor (-1: none)
+    unsigned closing = 0;    // bit q: the key of row q is the last valid key
+    unsigned mine = 0;
+#pragma unroll
+    for (int q = 0; q < kRows; q++) {
+      const long long i = ts + (long long)q * kCsrBlock + tid;
+      const unsigned long long p = pred_key(edges, x[q], q, lane, warp, pre);
+      const unsigned long long sk = succ_key(edges, x[q], q, lane, warp, post);  // every lane: a shuffle
+      const unsigned long long nx = i + 1 < N ? sk : kSentinel;
+      const bool valid = i < hi && x[q] != kSentinel;
+      ps[q] = (i == 0 || p == kSentinel) ? -1 : (int)(p >> B);
+      if (valid && nx == kSentinel) closing |= 1u << q;
+      bal[q] = __ballot_sync(kFull, valid && (i == 0 || p != x[q]));
+      if (lane == q) mine = __popc(bal[q]);
+    }
+    if (lane < kRows) cnt[lane * kW + warp] = mine;
     __syncthreads();
     if (warp == 0) {
-      unsigned pp = lane < kCsrBlock / 32 ? part[lane] : 0;
-      unsigned pi = warp_incl_scan(pp, lane);
-      if (lane < kCsrBlock / 32) part[lane] = pi - pp;
+      const unsigned c0 = cnt[lane];
+      const unsigned incl = warp_incl_scan(c0, lane);
+      cnt[lane] = incl - c0;
+      if (lane == 31) tile_total = incl;
     }
     __syncthreads();
-    const unsigned long long r0 = running;
-    unsigned local = part[warp] + incl - cntf;  // unique keys of the tile before this thread's first
 #pragma unroll
-    for (int q = 0; q < kKeysPerThread; q++) {
-      const int j = j0 + q;
-      if (j >= tn) break;
-      const unsigned long long cur = tk[j + 1], prev = tk[j];
-      if ((flags >> q) & 1u) {
-        const unsigned long long pos = r0 + local;
-        ta[local++] = (int)(cur & mask);
-        const long long s = (long long)(cur >> B);
-        const long long ps = (ts + j == 0 || prev == kSentinel) ? -1 : (long long)(prev >> B);
-        if (s != ps)
-          for (long long v = ps + 1; v <= s; v++) off[v] = (long long)pos;
+    for (int q = 0; q < kRows; q++) {
+      const bool u = (bal[q] >> lane) & 1u;
+      const unsigned long long before = running + cnt[q * kW + warp] + __popc(bal[q] & lt);
+      const long long s = (long long)(x[q] >> B);
+      if (u) {
+        adj[before] = (int)(x[q] & mask);
+        for (long long v = (long long)ps[q] + 1; v <= s; v++) off[v] = (long long)before;
       }
       // the last valid key (unique or a repeat) closes the offsets above its source
-      if (cur != kSentinel && tk[j + 2] == kSentinel) {
-        const long long s = (long long)(cur >> B);
-        const long long last = (long long)(r0 + local) - 1;  // position of the latest unique key
-        for (long long v = s + 1; v <= n; v++) off[v] = last + 1;
-        *m_out = last + 1;
+      if ((closing >> q) & 1u) {
+        const long long m_val = (long long)before + (u ? 1 : 0);
+        for (long long v = s + 1; v <= n; v++) off[v] = m_val;
+        *m_out = m_val;
       }
     }
-    __syncthreads();
-    // the tile's unique targets, coalesced
-    if (tid == kCsrBlock - 1) running = r0 + local;
-    __syncthreads();
-    const unsigned nu = (unsigned)(running - r0);
-    for (unsigned j = tid; j < nu; j += kCsrBlock) adj[r0 + j] = ta[j];
-    __syncthreads();
+    running += tile_total;
   }
 }
 
@@ -362,6 +429,8 @@ CsrLayout csr_layout(long long n, long long E, int sms, long long max_graph_n) {
   off = al(off + 4 * 256 * (size_t)G);
   L.offs = off;
   off = al(off + 8 * 256 * (size_t)G);
+  L.rowtot = off;
+  off = al(off + 8 * 256);
   L.total = off;
   return L;
 }
@@ -375,6 +444,7 @@ cudaError_t csr_build_launch(const CsrLayout& L, char* ws, long long n, long lon
   unsigned long long* k1 = (unsigned long long*)(ws + L.keys1);
   unsigned* hist = (unsigned*)(ws + L.hist);
   unsigned long long* offs = (unsigned long long*)(ws + L.offs);
+  unsigned long long* rowtot = (unsigned long long*)(ws + L.rowtot);
   if ((e = cudaMemsetAsync(status, 0, 256, stream)) != cudaSuccess) return e;
   if ((e = cudaMemsetAsync(off_out, 0, 8 * (size_t)(n + 1), stream)) != cudaSuccess) return e;
   if ((e = cudaMemsetAsync(m_out, 0, 8, stream)) != cudaSuccess) return e;
@@ -387,14 +457,14 @@ cudaError_t csr_build_launch(const CsrLayout& L, char* ws, long long n, long lon
   for (int p = 0; p < passes; p++) {
     int shift = 8 * p;
     rs_upsweep<<<G, kCsrBlock, 0, stream>>>(k0, N, L.chunk, shift, hist);
-    scan_u32_to_u64<<<1, 1024, 0, stream>>>(hist, offs, 256ll * G);
-    rs_downsweep<<<G, kCsrBlock, 0, stream>>>(k0, k1, N, L.chunk, shift, offs);
+    scan_u32_to_u64<<<256, 1024, 0, stream>>>(hist, offs, G, rowtot);
+    rs_downsweep<<<G, kCsrBlock, 0, stream>>>(k0, k1, N, L.chunk, shift, offs, rowtot);
     unsigned long long* t = k0;
     k0 = k1;
     k1 = t;
   }
   csr_count_unique<<<G, kCsrBlock, 0, stream>>>(k0, N, L.chunk, hist);
-  scan_u32_to_u64<<<1, 1024, 0, stream>>>(hist, offs, G);
+  scan_u32_to_u64<<<1, 1024, 0, stream>>>(hist, offs, G, nullptr);
   csr_emit<<<G, kCsrBlock, 0, stream>>>(k0, N, L.chunk, L.B, n, offs, adj_out, off_out, m_out);
   return cudaGetLastError();
 }
