@@ -7,7 +7,7 @@
 // the device-wide synchronisation an allocation can cause. This entry point
 // runs the same peel kernel as kcore_decompose, with the same launch settings
 // as a handle's defaults (bulk-synchronous schedule, batch-updated heavy
-// subrounds, tail mode), but its scratch memory (the induced degrees, the two
+// subrounds, tail mode off), but its scratch memory (the induced degrees, the two
 // active lists, the work queue, the batch-update counts, the three phase
 // records and the control block) lives in one file-scope __device__ array of
 // fixed size. The caller still provides the graph and the output arrays.
