@@ -5,7 +5,8 @@
 //   1. keys: each pair (a, b) with a != b gives the arcs a->b and b->a as
 //      integers (a << B) | b with B = bits of n-1; self-loops and ids out of
 //      range become a sentinel that sorts last (ids out of range also set an
-//      error status).
+//      error status). The keys are not stored: the first radix pass (which
+//      need not be stable) makes them from the edge arrays as it reads them.
 //   2. stable LSD radix sort of the keys over their 2B significant bits, 8-bit
 //      digits. Each CTA owns a contiguous chunk; a pass is an upsweep (digit
 //      histogram per CTA), a scan of each digit's row of the 256 x CTAs
@@ -39,33 +40,38 @@ constexpr unsigned long long kSentinel = ~0ull;
 // Batch (gv != nullptr): edge i belongs to the graph g with eoff[g] <= i <
 // eoff[g+1]; its ids are graph-local in [0, gv[g+1] - gv[g]); the source part
 // is the global id gv[g] + local, the target part stays local.
-__global__ void csr_make_keys(const int* src, const int* dst, long long E, long long n, int Bd,
-                              const long long* gv, const long long* eoff, long long G,
-                              unsigned long long* keys, int* status) {
-  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < E;
-       i += (long long)gridDim.x * blockDim.x) {
-    int a = src[i], b = dst[i];
-    long long base = 0, lim = n;
-    if (gv) {
-      long long lo = 0, hi = G;  // last g with eoff[g] <= i
-      while (hi - lo > 1) {
-        long long mid = (lo + hi) >> 1;
-        if (eoff[mid] <= i) lo = mid;
-        else hi = mid;
-      }
-      base = gv[lo];
-      lim = gv[lo + 1] - base;
+struct EdgeList {
+  const int* src;
+  const int* dst;
+  long long n;
+  int Bd;
+  const long long* gv;
+  const long long* eoff;
+  long long G;
+  int* status;
+};
+
+// the arcs of edge i = (a, b): keys 2i (a -> b) and 2i + 1 (b -> a)
+__device__ __forceinline__ void edge_keys(const EdgeList& es, long long i, int a, int b, unsigned long long& k0,
+                                          unsigned long long& k1) {
+  long long base = 0, lim = es.n;
+  if (es.gv) {
+    long long lo = 0, hi = es.G;  // last g with eoff[g] <= i
+    while (hi - lo > 1) {
+      long long mid = (lo + hi) >> 1;
+      if (es.eoff[mid] <= i) lo = mid;
+      else hi = mid;
     }
-    unsigned long long k0 = kSentinel, k1 = kSentinel;
-    if ((unsigned long long)(unsigned)a >= (unsigned long long)lim ||
-        (unsigned long long)(unsigned)b >= (unsigned long long)lim) {
-      atomicCAS(status, 0, 1);
-    } else if (a != b) {
-      k0 = ((unsigned long long)(base + a) << Bd) | (unsigned long long)b;
-      k1 = ((unsigned long long)(base + b) << Bd) | (unsigned long long)a;
-    }
-    keys[2 * i] = k0;
-    keys[2 * i + 1] = k1;
+    base = es.gv[lo];
+    lim = es.gv[lo + 1] - base;
+  }
+  k0 = k1 = kSentinel;
+  if ((unsigned long long)(unsigned)a >= (unsigned long long)lim ||
+      (unsigned long long)(unsigned)b >= (unsigned long long)lim) {
+    atomicCAS(es.status, 0, 1);
+  } else if (a != b) {
+    k0 = ((unsigned long long)(base + a) << es.Bd) | (unsigned long long)b;
+    k1 = ((unsigned long long)(base + b) << es.Bd) | (unsigned long long)a;
   }
 }
 
@@ -73,16 +79,41 @@ __device__ __forceinline__ int digit_of(unsigned long long k, int shift) {
   return (int)((k >> shift) & 0xffull);
 }
 
-// Per-CTA digit histogram of its chunk: hist[d * G + g].
-__global__ void __launch_bounds__(kCsrBlock) rs_upsweep(const unsigned long long* keys, long long N,
-                                                        long long chunk, int shift,
+// Per-CTA digit histogram of its chunk: hist[d * G + g]. kFromEdges: the keys
+// are made from the edge list (chunks hold whole edges: chunk and lo are even).
+template <bool kFromEdges>
+__global__ void __launch_bounds__(kCsrBlock) rs_upsweep(const unsigned long long* keys, EdgeList es,
+                                                        long long N, long long chunk, int shift,
                                                         unsigned* hist) {
   __shared__ unsigned cnt[kCsrBlock / 32][256];
   const int tid = threadIdx.x, warp = tid >> 5;
   for (int i = tid; i < (kCsrBlock / 32) * 256; i += kCsrBlock) (&cnt[0][0])[i] = 0;
   __syncthreads();
   long long lo = (long long)blockIdx.x * chunk, hi = min(N, lo + chunk);
-  for (long long i = lo + tid; i < hi; i += kCsrBlock) atomicAdd(&cnt[warp][digit_of(keys[i], shift)], 1u);
+  if constexpr (kFromEdges) {
+    constexpr int kU = 4;  // edges per thread per step, loaded before any count
+    for (long long e0 = lo / 2 + tid; e0 < hi / 2; e0 += kU * kCsrBlock) {
+      int a[kU], b[kU];
+#pragma unroll
+      for (int u = 0; u < kU; u++) {
+        const long long e = e0 + u * kCsrBlock;
+        a[u] = e < hi / 2 ? __ldcs(es.src + e) : 0;
+        b[u] = e < hi / 2 ? __ldcs(es.dst + e) : 0;
+      }
+#pragma unroll
+      for (int u = 0; u < kU; u++) {
+        const long long e = e0 + u * kCsrBlock;
+        if (e < hi / 2) {
+          unsigned long long k0, k1;
+          edge_keys(es, e, a[u], b[u], k0, k1);
+          atomicAdd(&cnt[warp][digit_of(k0, shift)], 1u);
+          atomicAdd(&cnt[warp][digit_of(k1, shift)], 1u);
+        }
+      }
+    }
+  } else {
+    for (long long i = lo + tid; i < hi; i += kCsrBlock) atomicAdd(&cnt[warp][digit_of(keys[i], shift)], 1u);
+  }
   __syncthreads();
   unsigned s = 0;
   for (int w = 0; w < kCsrBlock / 32; w++) s += cnt[w][tid];
@@ -126,8 +157,13 @@ __global__ void __launch_bounds__(1024) scan_u32_to_u64(const unsigned* in, unsi
 // order. offs[d * G + g] counts the keys of digit d in the chunks before g,
 // rowtot[d] all keys of digit d; so the CTA's first key of digit d goes after
 // every key of a smaller digit and the digit-d keys of earlier chunks.
+// kFromEdges: the first pass, whose keys are made from the edge list (a tile
+// is 1,024 edges; the order within a tile does not matter in the first pass).
+// Pos: the type of an output position (32 bits when there are at most 2^32
+// keys: positions are then computed modulo 2^32).
 static_assert(kCsrBlock == 256, "one thread per 8-bit digit");
-__global__ void __launch_bounds__(kCsrBlock, 5) rs_downsweep(const unsigned long long* in,
+template <bool kFromEdges, typename Pos>
+__global__ void __launch_bounds__(kCsrBlock, 5) rs_downsweep(const unsigned long long* in, EdgeList es,
                                                           unsigned long long* out, long long N,
                                                           long long chunk, int shift,
                                                           const unsigned long long* offs,
@@ -135,7 +171,7 @@ __global__ void __launch_bounds__(kCsrBlock, 5) rs_downsweep(const unsigned long
   __shared__ unsigned long long buf[kTile];
   __shared__ __align__(16) unsigned long long stage[kTile];  // the next tile, copied asynchronously
   __shared__ unsigned wcnt[kCsrBlock / 32][256];  // keys per (warp, digit), then their tile offsets
-  __shared__ unsigned long long dstb[256];        // output position of the tile's first key of digit d, minus its tile offset
+  __shared__ Pos dstb[256];  // output position of the tile's first key of digit d, minus its tile offset
   __shared__ unsigned long long part64[kCsrBlock / 32];
   __shared__ unsigned part[kCsrBlock / 32];
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
@@ -156,27 +192,63 @@ __global__ void __launch_bounds__(kCsrBlock, 5) rs_downsweep(const unsigned long
   long long lo = (long long)blockIdx.x * chunk, hi = min(N, lo + chunk);
   // 16-byte asynchronous copies of a tile's keys into `stage` (pairs of keys;
   // a last odd key is copied with its neighbour, which lies inside the
-  // 256-byte-aligned key buffer and is not used)
+  // 256-byte-aligned key buffer and is not used). kFromEdges: the tile's
+  // sources and targets go to the stage's first and second 4 KB, by 16-byte
+  // copies when both arrays are 16-byte aligned and the tile is whole, else
+  // by 4-byte copies (nothing past the last edge is read).
+  const unsigned sbase = (unsigned)__cvta_generic_to_shared(stage);
+  const bool al16 =
+      ((reinterpret_cast<unsigned long long>(es.src) | reinterpret_cast<unsigned long long>(es.dst)) & 15) == 0;
   auto prefetch = [&](long long t0) {
     const long long tn = min((long long)kTile, hi - t0);
-    const unsigned sbase = (unsigned)__cvta_generic_to_shared(stage);
-    for (int c = tid; 2 * c < tn; c += kCsrBlock)
-      asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(sbase + 16u * c), "l"(in + t0 + 2 * c)
-                   : "memory");
+    if constexpr (kFromEdges) {
+      const long long e0 = t0 / 2, ne = tn / 2;
+      if (al16 && ne == kTile / 2) {
+        static_assert(kTile / 2 / 4 == kCsrBlock, "one 16-byte copy per thread and array");
+        asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(sbase + 16u * tid), "l"(es.src + e0 + 4 * tid)
+                     : "memory");
+        asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(sbase + 4096u + 16u * tid),
+                     "l"(es.dst + e0 + 4 * tid)
+                     : "memory");
+      } else {
+        for (int c = tid; c < ne; c += kCsrBlock) {
+          asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" ::"r"(sbase + 4u * c), "l"(es.src + e0 + c)
+                       : "memory");
+          asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" ::"r"(sbase + 4096u + 4u * c), "l"(es.dst + e0 + c)
+                       : "memory");
+        }
+      }
+    } else {
+      for (int c = tid; 2 * c < tn; c += kCsrBlock)
+        asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(sbase + 16u * c), "l"(in + t0 + 2 * c)
+                     : "memory");
+    }
     asm volatile("cp.async.commit_group;" ::: "memory");
   };
   if (lo < hi) prefetch(lo);
   for (long long ts = lo; ts < hi; ts += kTile) {
     const long long tn = min((long long)kTile, hi - ts);
-    asm volatile("cp.async.wait_all;" ::: "memory");
-    __syncthreads();
     unsigned long long k[kKeysPerThread];
     unsigned rk[kKeysPerThread / 2];  // ranks below 2,048: two per word
-    // key it of this thread is key j_of(it) of the tile; 256 is the digit of no key
+    // key it of this thread is key j_of(it) of the tile (kFromEdges: arc it & 1
+    // of the tile's edge el_of(it)); 256 is the digit of no key
     auto j_of = [&](int it) { return warp * (kKeysPerThread * 32) + it * 32 + lane; };
-    auto dg_of = [&](int it) { return j_of(it) < tn ? digit_of(k[it], shift) : 256; };
+    auto el_of = [&](int it) { return warp * (kKeysPerThread * 16) + (it >> 1) * 32 + lane; };
+    auto valid = [&](int it) { return kFromEdges ? el_of(it) < tn / 2 : j_of(it) < tn; };
+    auto dg_of = [&](int it) { return valid(it) ? digit_of(k[it], shift) : 256; };
+    asm volatile("cp.async.wait_all;" ::: "memory");
+    __syncthreads();
+    if constexpr (kFromEdges) {
+      const int* sa = reinterpret_cast<const int*>(stage);
 #pragma unroll
-    for (int it = 0; it < kKeysPerThread; it++) k[it] = j_of(it) < tn ? stage[j_of(it)] : 0;
+      for (int it = 0; it < kKeysPerThread; it += 2) {
+        k[it] = k[it + 1] = 0;
+        if (valid(it)) edge_keys(es, ts / 2 + el_of(it), sa[el_of(it)], sa[1024 + el_of(it)], k[it], k[it + 1]);
+      }
+    } else {
+#pragma unroll
+      for (int it = 0; it < kKeysPerThread; it++) k[it] = j_of(it) < tn ? stage[j_of(it)] : 0;
+    }
     __syncthreads();  // the stage is read: copy the next tile into it
     if (ts + kTile < hi) prefetch(ts + kTile);
     // rank within (warp, digit) in key order: iterations in order, lanes in
@@ -214,7 +286,7 @@ __global__ void __launch_bounds__(kCsrBlock, 5) rs_downsweep(const unsigned long
       wcnt[w][tid] = acc;
       acc += c;
     }
-    dstb[tid] = run - lo_d;  // modulo 2^64: adding a tile offset of digit tid lands at or after run
+    dstb[tid] = (Pos)(run - lo_d);  // modulo 2^64 (2^32): adding a tile offset of digit tid lands at or after run
     run += tc;
     __syncthreads();
 #pragma unroll
@@ -226,7 +298,7 @@ __global__ void __launch_bounds__(kCsrBlock, 5) rs_downsweep(const unsigned long
     for (int w = 0; w < kCsrBlock / 32; w++) wcnt[w][tid] = 0;  // for the next tile
     for (int j = tid; j < tn; j += kCsrBlock) {
       const unsigned long long key = buf[j];
-      out[dstb[digit_of(key, shift)] + (unsigned long long)j] = key;
+      out[(unsigned long long)(Pos)(dstb[digit_of(key, shift)] + (Pos)j)] = key;
     }
   }
 }
@@ -451,14 +523,24 @@ cudaError_t csr_build_launch(const CsrLayout& L, char* ws, long long n, long lon
   if (E == 0) return cudaSuccess;
   const long long N = L.N;
   const int G = L.grid;
-  int kb = (int)std::min<long long>((E + kCsrBlock - 1) / kCsrBlock, 65536);
-  csr_make_keys<<<kb, kCsrBlock, 0, stream>>>(src, dst, E, n, L.B, gv, eoff, ngraphs, k0, status);
+  const EdgeList es{src, dst, n, L.B, gv, eoff, ngraphs, status};
+  const bool narrow = N <= (1ll << 32);  // output positions fit in 32 bits
   const int passes = (L.Bs + L.B + 7) / 8;
   for (int p = 0; p < passes; p++) {
     int shift = 8 * p;
-    rs_upsweep<<<G, kCsrBlock, 0, stream>>>(k0, N, L.chunk, shift, hist);
+    if (p == 0) rs_upsweep<true><<<G, kCsrBlock, 0, stream>>>(nullptr, es, N, L.chunk, shift, hist);
+    else rs_upsweep<false><<<G, kCsrBlock, 0, stream>>>(k0, es, N, L.chunk, shift, hist);
     scan_u32_to_u64<<<256, 1024, 0, stream>>>(hist, offs, G, rowtot);
-    rs_downsweep<<<G, kCsrBlock, 0, stream>>>(k0, k1, N, L.chunk, shift, offs, rowtot);
+    if (p == 0 && narrow)
+      rs_downsweep<true, unsigned><<<G, kCsrBlock, 0, stream>>>(nullptr, es, k1, N, L.chunk, shift, offs, rowtot);
+    else if (p == 0)
+      rs_downsweep<true, unsigned long long><<<G, kCsrBlock, 0, stream>>>(nullptr, es, k1, N, L.chunk, shift, offs,
+                                                                        rowtot);
+    else if (narrow)
+      rs_downsweep<false, unsigned><<<G, kCsrBlock, 0, stream>>>(k0, es, k1, N, L.chunk, shift, offs, rowtot);
+    else
+      rs_downsweep<false, unsigned long long><<<G, kCsrBlock, 0, stream>>>(k0, es, k1, N, L.chunk, shift, offs,
+                                                                         rowtot);
     unsigned long long* t = k0;
     k0 = k1;
     k1 = t;

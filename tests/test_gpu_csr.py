@@ -97,3 +97,22 @@ def test_csr_then_peel_matches_oracle(kc):
     o2, a2 = oracle.build_csr(n, s, d)
     want = oracle.bz(n, o2, a2)
     np.testing.assert_array_equal(core.cpu().numpy(), want)
+
+
+@pytest.mark.parametrize("shift", [1, 2, 3])
+def test_edge_arrays_not_16_byte_aligned(kc, shift):
+    """Edge arrays that start 4, 8 or 12 bytes past a 16-byte boundary (views
+    into larger tensors): the first radix pass then reads them with 4-byte
+    copies. Several whole 1,024-edge tiles and a ragged last one."""
+    s, d = gg.rmat(14, 16, seed=3, perm_seed=4)
+    n = 1 << 14
+    S = torch.zeros(s.size + 8, dtype=torch.int32, device="cuda")
+    D = torch.zeros(d.size + 8, dtype=torch.int32, device="cuda")
+    S[shift:shift + s.size] = torch.from_numpy(s).cuda()
+    D[4 - shift:4 - shift + d.size] = torch.from_numpy(d).cuda()
+    Sv, Dv = S[shift:shift + s.size], D[4 - shift:4 - shift + d.size]
+    assert Sv.data_ptr() % 16 != 0 or Dv.data_ptr() % 16 != 0
+    off, adj = kc.build_csr(n, Sv, Dv)
+    want_off, want_adj = oracle.build_csr(n, s, d)
+    np.testing.assert_array_equal(off.cpu().numpy(), want_off)
+    np.testing.assert_array_equal(adj.cpu().numpy(), want_adj)
