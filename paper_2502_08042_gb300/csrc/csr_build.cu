@@ -22,6 +22,17 @@
 //      vertex's offset). Keys are read striped (a warp reads 32 consecutive
 //      keys), the predecessor comes from the next lower lane, and the
 //      positions from warp ballots, so no key passes through shared memory.
+// A single graph takes a shorter route through steps 1-3: each pair (a, b)
+// with a != b gives ONE key (min << B) | max; sorting these E keys by both
+// fields gives every vertex's upper neighbours in order (A), and a stable
+// sort of A by its low B bits (the larger endpoint) gives every vertex's
+// lower neighbours in order (B). A vertex's list is its lower neighbours
+// followed by its upper ones, both ascending, so emission writes the CSR from
+// A and B directly: 2B + B digit passes over E keys instead of 2B over 2E.
+// Repeats stay in both sequences as adjacent equal keys and are dropped on
+// emission (a repeat cannot become the sentinel: in B it would sort among the
+// keys whose larger endpoint has all B bits set).
+//
 // Lists come out ascending and duplicate-free, the canonical form of the CPU
 // builder, so the two are comparable bit for bit.
 #include <climits>
@@ -75,22 +86,56 @@ __device__ __forceinline__ void edge_keys(const EdgeList& es, long long i, int a
   }
 }
 
-__device__ __forceinline__ int digit_of(unsigned long long k, int shift) {
-  return (int)((k >> shift) & 0xffull);
+// a single graph's edge i = (a, b) as one key (min << B) | max
+__device__ __forceinline__ unsigned long long edge_canon(const EdgeList& es, int a, int b) {
+  if ((unsigned long long)(unsigned)a >= (unsigned long long)es.n ||
+      (unsigned long long)(unsigned)b >= (unsigned long long)es.n) {
+    atomicCAS(es.status, 0, 1);
+    return kSentinel;
+  }
+  if (a == b) return kSentinel;
+  const unsigned lo = (unsigned)min(a, b), hi = (unsigned)max(a, b);
+  return ((unsigned long long)lo << es.Bd) | (unsigned long long)hi;
 }
 
-// Per-CTA digit histogram of its chunk: hist[d * G + g]. kFromEdges: the keys
-// are made from the edge list (chunks hold whole edges: chunk and lo are even).
-template <bool kFromEdges>
+// Where a pass's keys come from: a key array, the edge list as two arcs per
+// edge (the first pass of the general build), or the edge list as one key per
+// edge (the first pass of a single graph's build).
+enum KeySrc : int { kKeys = 0, kArcs = 1, kCanon = 2 };
+
+// digit of a pass: bits [shift, shift + 8) of the key, masked by dmask (the
+// last pass over a field narrower than a multiple of 8 bits keeps only its bits)
+__device__ __forceinline__ int digit_of(unsigned long long k, int shift, int dmask) {
+  return (int)((k >> shift) & (unsigned long long)dmask);
+}
+
+// Per-CTA digit histogram of its chunk: hist[d * G + g]. kArcs: the keys are
+// made from the edge list, two per edge (chunks hold whole edges: chunk and lo
+// are even); kCanon: one per edge.
+template <int kSrc>
 __global__ void __launch_bounds__(kCsrBlock) rs_upsweep(const unsigned long long* keys, EdgeList es,
-                                                        long long N, long long chunk, int shift,
+                                                        long long N, long long chunk, int shift, int dmask,
                                                         unsigned* hist) {
   __shared__ unsigned cnt[kCsrBlock / 32][256];
   const int tid = threadIdx.x, warp = tid >> 5;
   for (int i = tid; i < (kCsrBlock / 32) * 256; i += kCsrBlock) (&cnt[0][0])[i] = 0;
   __syncthreads();
   long long lo = (long long)blockIdx.x * chunk, hi = min(N, lo + chunk);
-  if constexpr (kFromEdges) {
+  if constexpr (kSrc == kCanon) {
+    constexpr int kU = 4;
+    for (long long e0 = lo + tid; e0 < hi; e0 += kU * kCsrBlock) {
+      int a[kU], b[kU];
+#pragma unroll
+      for (int u = 0; u < kU; u++) {
+        const long long e = e0 + u * kCsrBlock;
+        a[u] = e < hi ? __ldcs(es.src + e) : 0;
+        b[u] = e < hi ? __ldcs(es.dst + e) : 0;
+      }
+#pragma unroll
+      for (int u = 0; u < kU; u++)
+        if (e0 + u * kCsrBlock < hi) atomicAdd(&cnt[warp][digit_of(edge_canon(es, a[u], b[u]), shift, dmask)], 1u);
+    }
+  } else if constexpr (kSrc == kArcs) {
     constexpr int kU = 4;  // edges per thread per step, loaded before any count
     for (long long e0 = lo / 2 + tid; e0 < hi / 2; e0 += kU * kCsrBlock) {
       int a[kU], b[kU];
@@ -106,13 +151,13 @@ __global__ void __launch_bounds__(kCsrBlock) rs_upsweep(const unsigned long long
         if (e < hi / 2) {
           unsigned long long k0, k1;
           edge_keys(es, e, a[u], b[u], k0, k1);
-          atomicAdd(&cnt[warp][digit_of(k0, shift)], 1u);
-          atomicAdd(&cnt[warp][digit_of(k1, shift)], 1u);
+          atomicAdd(&cnt[warp][digit_of(k0, shift, dmask)], 1u);
+          atomicAdd(&cnt[warp][digit_of(k1, shift, dmask)], 1u);
         }
       }
     }
   } else {
-    for (long long i = lo + tid; i < hi; i += kCsrBlock) atomicAdd(&cnt[warp][digit_of(keys[i], shift)], 1u);
+    for (long long i = lo + tid; i < hi; i += kCsrBlock) atomicAdd(&cnt[warp][digit_of(keys[i], shift, dmask)], 1u);
   }
   __syncthreads();
   unsigned s = 0;
@@ -157,15 +202,16 @@ __global__ void __launch_bounds__(1024) scan_u32_to_u64(const unsigned* in, unsi
 // order. offs[d * G + g] counts the keys of digit d in the chunks before g,
 // rowtot[d] all keys of digit d; so the CTA's first key of digit d goes after
 // every key of a smaller digit and the digit-d keys of earlier chunks.
-// kFromEdges: the first pass, whose keys are made from the edge list (a tile
-// is 1,024 edges; the order within a tile does not matter in the first pass).
+// kArcs / kCanon: the first pass, whose keys are made from the edge list (a
+// tile is 1,024 edges / 2,048 edges; the order within a tile does not matter
+// in the first pass).
 // Pos: the type of an output position (32 bits when there are at most 2^32
 // keys: positions are then computed modulo 2^32).
 static_assert(kCsrBlock == 256, "one thread per 8-bit digit");
-template <bool kFromEdges, typename Pos>
+template <int kSrc, typename Pos>
 __global__ void __launch_bounds__(kCsrBlock, 5) rs_downsweep(const unsigned long long* in, EdgeList es,
                                                           unsigned long long* out, long long N,
-                                                          long long chunk, int shift,
+                                                          long long chunk, int shift, int dmask,
                                                           const unsigned long long* offs,
                                                           const unsigned long long* rowtot) {
   __shared__ unsigned long long buf[kTile];
@@ -192,29 +238,32 @@ __global__ void __launch_bounds__(kCsrBlock, 5) rs_downsweep(const unsigned long
   long long lo = (long long)blockIdx.x * chunk, hi = min(N, lo + chunk);
   // 16-byte asynchronous copies of a tile's keys into `stage` (pairs of keys;
   // a last odd key is copied with its neighbour, which lies inside the
-  // 256-byte-aligned key buffer and is not used). kFromEdges: the tile's
-  // sources and targets go to the stage's first and second 4 KB, by 16-byte
-  // copies when both arrays are 16-byte aligned and the tile is whole, else
-  // by 4-byte copies (nothing past the last edge is read).
+  // key buffer and is not used). kArcs / kCanon: the tile's sources and
+  // targets go to the stage's two halves (4 KB each for kArcs, 8 KB for
+  // kCanon), by 16-byte copies when both arrays are 16-byte aligned and the
+  // tile is whole, else by 4-byte copies (nothing past the last edge is read).
   const unsigned sbase = (unsigned)__cvta_generic_to_shared(stage);
   const bool al16 =
       ((reinterpret_cast<unsigned long long>(es.src) | reinterpret_cast<unsigned long long>(es.dst)) & 15) == 0;
   auto prefetch = [&](long long t0) {
     const long long tn = min((long long)kTile, hi - t0);
-    if constexpr (kFromEdges) {
-      const long long e0 = t0 / 2, ne = tn / 2;
-      if (al16 && ne == kTile / 2) {
-        static_assert(kTile / 2 / 4 == kCsrBlock, "one 16-byte copy per thread and array");
-        asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(sbase + 16u * tid), "l"(es.src + e0 + 4 * tid)
-                     : "memory");
-        asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(sbase + 4096u + 16u * tid),
-                     "l"(es.dst + e0 + 4 * tid)
-                     : "memory");
+    if constexpr (kSrc != kKeys) {
+      constexpr int kE = kSrc == kArcs ? kTile / 2 : kTile;  // edges per tile
+      constexpr unsigned kHalf = 4u * kE;                     // bytes of one array's share
+      const long long e0 = kSrc == kArcs ? t0 / 2 : t0, ne = kSrc == kArcs ? tn / 2 : tn;
+      if (al16 && ne == kE) {
+        for (int c = tid; 4 * c < kE; c += kCsrBlock) {
+          asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(sbase + 16u * c), "l"(es.src + e0 + 4 * c)
+                       : "memory");
+          asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(sbase + kHalf + 16u * c),
+                       "l"(es.dst + e0 + 4 * c)
+                       : "memory");
+        }
       } else {
         for (int c = tid; c < ne; c += kCsrBlock) {
           asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" ::"r"(sbase + 4u * c), "l"(es.src + e0 + c)
                        : "memory");
-          asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" ::"r"(sbase + 4096u + 4u * c), "l"(es.dst + e0 + c)
+          asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" ::"r"(sbase + kHalf + 4u * c), "l"(es.dst + e0 + c)
                        : "memory");
         }
       }
@@ -230,15 +279,20 @@ __global__ void __launch_bounds__(kCsrBlock, 5) rs_downsweep(const unsigned long
     const long long tn = min((long long)kTile, hi - ts);
     unsigned long long k[kKeysPerThread];
     unsigned rk[kKeysPerThread / 2];  // ranks below 2,048: two per word
-    // key it of this thread is key j_of(it) of the tile (kFromEdges: arc it & 1
-    // of the tile's edge el_of(it)); 256 is the digit of no key
+    // key it of this thread is key j_of(it) of the tile (kArcs: arc it & 1 of
+    // the tile's edge el_of(it); kCanon: edge j_of(it)); 256 is the digit of no key
     auto j_of = [&](int it) { return warp * (kKeysPerThread * 32) + it * 32 + lane; };
     auto el_of = [&](int it) { return warp * (kKeysPerThread * 16) + (it >> 1) * 32 + lane; };
-    auto valid = [&](int it) { return kFromEdges ? el_of(it) < tn / 2 : j_of(it) < tn; };
-    auto dg_of = [&](int it) { return valid(it) ? digit_of(k[it], shift) : 256; };
+    auto valid = [&](int it) { return kSrc == kArcs ? el_of(it) < tn / 2 : j_of(it) < tn; };
+    auto dg_of = [&](int it) { return valid(it) ? digit_of(k[it], shift, dmask) : 256; };
     asm volatile("cp.async.wait_all;" ::: "memory");
     __syncthreads();
-    if constexpr (kFromEdges) {
+    if constexpr (kSrc == kCanon) {
+      const int* sa = reinterpret_cast<const int*>(stage);
+#pragma unroll
+      for (int it = 0; it < kKeysPerThread; it++)
+        k[it] = valid(it) ? edge_canon(es, sa[j_of(it)], sa[kTile + j_of(it)]) : 0;
+    } else if constexpr (kSrc == kArcs) {
       const int* sa = reinterpret_cast<const int*>(stage);
 #pragma unroll
       for (int it = 0; it < kKeysPerThread; it += 2) {
@@ -298,7 +352,7 @@ __global__ void __launch_bounds__(kCsrBlock, 5) rs_downsweep(const unsigned long
     for (int w = 0; w < kCsrBlock / 32; w++) wcnt[w][tid] = 0;  // for the next tile
     for (int j = tid; j < tn; j += kCsrBlock) {
       const unsigned long long key = buf[j];
-      out[(unsigned long long)(Pos)(dstb[digit_of(key, shift)] + (Pos)j)] = key;
+      out[(unsigned long long)(Pos)(dstb[digit_of(key, shift, dmask)] + (Pos)j)] = key;
     }
   }
 }
@@ -380,16 +434,32 @@ __global__ void __launch_bounds__(kCsrBlock, 5) csr_count_unique(const unsigned 
   }
 }
 
-// Ordered emission of the unique keys: adj[pos] = low B bits; the first arc of
-// each source fixes offsets[] for that source and every source without arcs
-// just below it; the last arc fills the offsets of the sources above it. A
-// unique key's position is the chunk's base, plus the unique keys of earlier
-// rows and of earlier warps in its row (one warp scans the tile's rows x warps
-// counts), plus those of lower lanes (a ballot).
-__global__ void __launch_bounds__(kCsrBlock, 5) csr_emit(const unsigned long long* k, long long N,
+// Ordered emission of the unique keys. A unique key's position ("before":
+// unique keys ahead of it) is the chunk's base, plus the unique keys of
+// earlier rows and of earlier warps in its row (one warp scans the tile's rows
+// x warps counts), plus those of lower lanes (a ballot). A key's group is its
+// high field (source) in kEmitAll and kEmitUpper, its low B bits (the larger
+// endpoint) in kStartsLow and kEmitLower.
+//   kEmitAll: adj[pos] = low B bits; the first arc of each source fixes
+//     offsets[] for that source and every source without arcs just below it;
+//     the last arc fills the offsets of the sources above it.
+//   kStartsLow (sequence B): starts[x] = unique keys of B whose larger
+//     endpoint is below x, for x in [0, n].
+//   kEmitUpper (sequence A): vertex u's upper neighbours go after its lower
+//     ones: adj[pos + starts[u + 1]] = larger endpoint, and offsets[x] = A's
+//     unique keys with smaller endpoint below x (csr_finish_offsets adds
+//     starts[x]); m = twice A's unique keys.
+//   kEmitLower (sequence B): vertex v's lower neighbours open its list:
+//     adj[offsets[v] + pos - starts[v]] = smaller endpoint.
+enum EmitMode : int { kEmitAll = 0, kStartsLow = 1, kEmitUpper = 2, kEmitLower = 3 };
+template <int kMode>
+__global__ void __launch_bounds__(kCsrBlock, 5) csr_emit(const unsigned long long* __restrict__ k, long long N,
                                                       long long chunk, int B, long long n,
-                                                      const unsigned long long* base, int* adj,
-                                                      long long* off, long long* m_out) {
+                                                      const unsigned long long* __restrict__ base,
+                                                      int* __restrict__ adj, long long* __restrict__ off,
+                                                      long long* __restrict__ m_out,
+                                                      unsigned long long* __restrict__ starts,
+                                                      long long* __restrict__ tail) {
   constexpr int kW = kCsrBlock / 32;
   constexpr int kRows = 4;  // a tile of kRows * kCsrBlock keys (chunks are whole tiles of either size)
   constexpr int kT = kRows * kCsrBlock;
@@ -425,7 +495,8 @@ __global__ void __launch_bounds__(kCsrBlock, 5) csr_emit(const unsigned long lon
       const unsigned long long sk = succ_key(edges, x[q], q, lane, warp, post);  // every lane: a shuffle
       const unsigned long long nx = i + 1 < N ? sk : kSentinel;
       const bool valid = i < hi && x[q] != kSentinel;
-      ps[q] = (i == 0 || p == kSentinel) ? -1 : (int)(p >> B);
+      const bool low = kMode == kStartsLow || kMode == kEmitLower;
+      ps[q] = (i == 0 || p == kSentinel) ? -1 : (int)(low ? (p & mask) : (p >> B));
       if (valid && nx == kSentinel) closing |= 1u << q;
       bal[q] = __ballot_sync(kFull, valid && (i == 0 || p != x[q]));
       if (lane == q) mine = __popc(bal[q]);
@@ -438,25 +509,79 @@ __global__ void __launch_bounds__(kCsrBlock, 5) csr_emit(const unsigned long lon
       cnt[lane] = incl - c0;
       if (lane == 31) tile_total = incl;
     }
+    // the lookups of each unique key, all issued before any store
+    unsigned long long look0[kRows];
+#pragma unroll
+    for (int q = 0; q < kRows; q++) {
+      look0[q] = 0;
+      if ((bal[q] >> lane) & 1u) {
+        if constexpr (kMode == kEmitUpper) {
+          const long long u = (long long)(x[q] >> B);
+          look0[q] = starts[u + 1];  // the lower neighbours of u come first
+        } else if constexpr (kMode == kEmitLower) {
+          const long long v = (long long)(x[q] & mask);
+          look0[q] = (unsigned long long)off[v] - starts[v];  // where v's lower neighbours start, minus B's offset
+        }
+      }
+    }
     __syncthreads();
 #pragma unroll
     for (int q = 0; q < kRows; q++) {
       const bool u = (bal[q] >> lane) & 1u;
       const unsigned long long before = running + cnt[q * kW + warp] + __popc(bal[q] & lt);
-      const long long s = (long long)(x[q] >> B);
+      const long long hi_f = (long long)(x[q] >> B), lo_f = (long long)(x[q] & mask);
+      const long long s = (kMode == kStartsLow || kMode == kEmitLower) ? lo_f : hi_f;  // the key's group
       if (u) {
-        adj[before] = (int)(x[q] & mask);
-        for (long long v = (long long)ps[q] + 1; v <= s; v++) off[v] = (long long)before;
+        if constexpr (kMode == kEmitAll) {
+          adj[before] = (int)lo_f;
+          for (long long v = (long long)ps[q] + 1; v <= s; v++) off[v] = (long long)before;
+        } else if constexpr (kMode == kStartsLow) {
+          if (before > 0)  // starts[] is cleared: the groups up to the first need no store
+            for (long long v = (long long)ps[q] + 1; v <= s; v++) starts[v] = before;
+        } else if constexpr (kMode == kEmitUpper) {
+          adj[before + look0[q]] = (int)lo_f;
+          for (long long v = (long long)ps[q] + 1; v <= s; v++) off[v] = (long long)before;
+        } else {
+          adj[look0[q] + before] = (int)hi_f;
+        }
       }
-      // the last valid key (unique or a repeat) closes the offsets above its source
-      if ((closing >> q) & 1u) {
+      // the last valid key (unique or a repeat) closes the groups above its own
+      if (kMode != kEmitLower && ((closing >> q) & 1u)) {
         const long long m_val = (long long)before + (u ? 1 : 0);
-        for (long long v = s + 1; v <= n; v++) off[v] = m_val;
-        *m_out = m_val;
+        if constexpr (kMode == kEmitAll) {
+          for (long long v = s + 1; v <= n; v++) off[v] = m_val;
+          *m_out = m_val;
+        } else {
+          // the groups above the last one are filled by csr_fill_tail
+          tail[0] = s;
+          tail[1] = m_val;
+          if constexpr (kMode == kEmitUpper) *m_out = 2 * m_val;
+        }
       }
     }
     running += tile_total;
   }
+}
+
+// starts[v] = m for the groups above the last valid key's group s = tail[0]
+// (m = tail[1] unique keys in all), in parallel; every group at or below s was
+// written by csr_emit<kStartsLow>.
+__global__ void csr_fill_starts(const long long* __restrict__ tail, long long n,
+                                unsigned long long* __restrict__ starts) {
+  const long long s = tail[0], m_val = tail[1];
+  for (long long v = s + 1 + blockIdx.x * (long long)blockDim.x + threadIdx.x; v <= n;
+       v += (long long)gridDim.x * blockDim.x)
+    starts[v] = (unsigned long long)m_val;
+}
+
+// offsets[v] = (A's unique keys with smaller endpoint below v) + starts[v]:
+// csr_emit<kEmitUpper> wrote the first term for v up to the last valid key's
+// group tail[0]; above it the term is tail[1], A's unique keys in all.
+__global__ void csr_finish_offsets(const long long* __restrict__ tail, long long n, long long* __restrict__ off,
+                                   const unsigned long long* __restrict__ starts) {
+  const long long s = tail[0], m_val = tail[1];
+  for (long long v = blockIdx.x * (long long)blockDim.x + threadIdx.x; v <= n; v += (long long)gridDim.x * blockDim.x)
+    off[v] = (v > s ? m_val : off[v]) + (long long)starts[v];
 }
 
 // ------------------------------------------------------------------ host side
@@ -470,20 +595,22 @@ CsrLayout csr_layout(long long n, long long E, int sms, long long max_graph_n) {
   CsrLayout L{};
   long long N = 2 * E;
   // five CTAs per SM, each sorting 2,048-key tiles with the next tile copied
-  // into shared memory while the current one is ranked (44 KB of shared
-  // memory, which admits five; 40 registers, held to six CTAs' worth by the
-  // kernel's launch bounds): the scatter is latency bound, so resident warps and
-  // loads in flight count. Measured on R-MAT 24 (ms per build): 2 CTAs x
+  // into shared memory while the current one is ranked (43 KB of shared
+  // memory, which admits five; registers held to five CTAs' worth by the
+  // kernels' launch bounds): resident warps and loads in flight count. Measured on R-MAT 24 (ms per build): 2 CTAs x
   // 4,096-key tiles 56.8, 4 x 4,096 37.7, 6 x 2,048 35.6, 7 x 2,048 38.2,
   // 8 x 1,536 37.3; with the asynchronous copy 5 x 2,048 31.0, 4 x 2,048 31.8
   long long G = (long long)sms * 5;
   long long tiles = (N + kTile - 1) / kTile;
   if (tiles < G) G = tiles < 1 ? 1 : tiles;
   L.grid = (int)G;
-  long long chunk = (N + G - 1) / G;
-  chunk = (chunk + kTile - 1) / kTile * kTile;
-  if (chunk < kTile) chunk = kTile;
-  L.chunk = chunk;
+  auto chunk_of = [&](long long keys) {
+    long long c = (keys + G - 1) / G;
+    c = (c + kTile - 1) / kTile * kTile;
+    return c < kTile ? (long long)kTile : c;
+  };
+  L.chunk = chunk_of(N);
+  L.chunk1 = chunk_of(E);
   L.N = N;
   L.Bs = bits_for(n);
   // batched: one spare code so that no valid (local) target has all bits set
@@ -493,16 +620,21 @@ CsrLayout csr_layout(long long n, long long E, int sms, long long max_graph_n) {
   auto al = [](size_t x) { return (x + 255) / 256 * 256; };
   L.status = off;
   off = al(off + 256);
+  // two spare keys per buffer: a single graph's build keeps two sequences of
+  // E keys per buffer, the second from an even index, and a 16-byte copy may
+  // read the key after a sequence's last
   L.keys0 = off;
-  off = al(off + 8 * (size_t)(N > 0 ? N : 1));
+  off = al(off + 8 * (size_t)(N + 2));
   L.keys1 = off;
-  off = al(off + 8 * (size_t)(N > 0 ? N : 1));
+  off = al(off + 8 * (size_t)(N + 2));
   L.hist = off;
   off = al(off + 4 * 256 * (size_t)G);
   L.offs = off;
   off = al(off + 8 * 256 * (size_t)G);
   L.rowtot = off;
   off = al(off + 8 * 256);
+  L.starts = off;  // a single graph's build: starts of the lower-neighbour lists
+  off = al(off + (max_graph_n > 0 ? 8 : 8 * (size_t)(n + 1)));
   L.total = off;
   return L;
 }
@@ -521,33 +653,76 @@ cudaError_t csr_build_launch(const CsrLayout& L, char* ws, long long n, long lon
   if ((e = cudaMemsetAsync(off_out, 0, 8 * (size_t)(n + 1), stream)) != cudaSuccess) return e;
   if ((e = cudaMemsetAsync(m_out, 0, 8, stream)) != cudaSuccess) return e;
   if (E == 0) return cudaSuccess;
-  const long long N = L.N;
   const int G = L.grid;
   const EdgeList es{src, dst, n, L.B, gv, eoff, ngraphs, status};
-  const bool narrow = N <= (1ll << 32);  // output positions fit in 32 bits
+  // one radix pass: upsweep, row scans, downsweep (32-bit positions when the
+  // keys number at most 2^32)
+  auto pass = [&](int src_kind, const unsigned long long* in, unsigned long long* out, long long N, long long chunk,
+                  int shift, int dmask) {
+    if (src_kind == kKeys) rs_upsweep<kKeys><<<G, kCsrBlock, 0, stream>>>(in, es, N, chunk, shift, dmask, hist);
+    else if (src_kind == kArcs) rs_upsweep<kArcs><<<G, kCsrBlock, 0, stream>>>(in, es, N, chunk, shift, dmask, hist);
+    else rs_upsweep<kCanon><<<G, kCsrBlock, 0, stream>>>(in, es, N, chunk, shift, dmask, hist);
+    scan_u32_to_u64<<<256, 1024, 0, stream>>>(hist, offs, G, rowtot);
+    const bool narrow = N <= (1ll << 32);
+#define KC_DOWN(S, P) rs_downsweep<S, P><<<G, kCsrBlock, 0, stream>>>(in, es, out, N, chunk, shift, dmask, offs, rowtot)
+    if (src_kind == kKeys) narrow ? KC_DOWN(kKeys, unsigned) : KC_DOWN(kKeys, unsigned long long);
+    else if (src_kind == kArcs) narrow ? KC_DOWN(kArcs, unsigned) : KC_DOWN(kArcs, unsigned long long);
+    else narrow ? KC_DOWN(kCanon, unsigned) : KC_DOWN(kCanon, unsigned long long);
+#undef KC_DOWN
+  };
+  if (!gv) {
+    // a single graph: A = the E edge keys sorted by (min, max); B = A stably
+    // sorted by max. A ping-pongs between the first halves of the two key
+    // buffers, B between their second halves (from an even index: 16-byte
+    // copies stay aligned)
+    const long long off2 = (E + 1) / 2 * 2;
+    unsigned long long *a0 = k0, *a1 = k1, *b0 = k0 + off2, *b1 = k1 + off2;
+    const int passes_a = (2 * L.B + 7) / 8;
+    for (int p = 0; p < passes_a; p++) {
+      pass(p == 0 ? kCanon : kKeys, a0, a1, E, L.chunk1, 8 * p, 0xff);
+      std::swap(a0, a1);
+    }
+    const unsigned long long* A = a0;
+    const int passes_b = (L.B + 7) / 8;
+    for (int p = 0; p < passes_b; p++) {
+      const int bits = std::min(8, L.B - 8 * p);
+      pass(kKeys, p == 0 ? A : b0, b1, E, L.chunk1, 8 * p, (1 << bits) - 1);
+      std::swap(b0, b1);
+    }
+    const unsigned long long* Bq = b0;
+    unsigned long long* starts = (unsigned long long*)(ws + L.starts);
+    unsigned long long* base_b = offs;      // B's unique keys before each chunk
+    unsigned long long* base_a = offs + G;  // A's
+    // the last valid key's group and the unique count (0, 0 when no key is
+    // valid: the tail fill then writes what the cleared arrays hold)
+    long long* tail = (long long*)(ws + L.status + 64);
+    const int fill_grid = (int)std::min<long long>((n + kCsrBlock) / kCsrBlock, 4 * (long long)G);
+    if ((e = cudaMemsetAsync(starts, 0, 8 * (size_t)(n + 1), stream)) != cudaSuccess) return e;
+    csr_count_unique<<<G, kCsrBlock, 0, stream>>>(Bq, E, L.chunk1, hist);
+    scan_u32_to_u64<<<1, 1024, 0, stream>>>(hist, base_b, G, nullptr);
+    csr_emit<kStartsLow><<<G, kCsrBlock, 0, stream>>>(Bq, E, L.chunk1, L.B, n, base_b, adj_out, off_out, m_out,
+                                                     starts, tail);
+    csr_fill_starts<<<fill_grid, kCsrBlock, 0, stream>>>(tail, n, starts);
+    csr_count_unique<<<G, kCsrBlock, 0, stream>>>(A, E, L.chunk1, hist);
+    scan_u32_to_u64<<<1, 1024, 0, stream>>>(hist, base_a, G, nullptr);
+    csr_emit<kEmitUpper><<<G, kCsrBlock, 0, stream>>>(A, E, L.chunk1, L.B, n, base_a, adj_out, off_out, m_out,
+                                                     starts, tail);
+    csr_finish_offsets<<<fill_grid, kCsrBlock, 0, stream>>>(tail, n, off_out, starts);
+    csr_emit<kEmitLower><<<G, kCsrBlock, 0, stream>>>(Bq, E, L.chunk1, L.B, n, base_b, adj_out, off_out, m_out,
+                                                     starts, nullptr);
+    return cudaGetLastError();
+  }
+  // a batch: two arcs per edge, sorted by (global source, local target)
+  const long long N = L.N;
   const int passes = (L.Bs + L.B + 7) / 8;
   for (int p = 0; p < passes; p++) {
-    int shift = 8 * p;
-    if (p == 0) rs_upsweep<true><<<G, kCsrBlock, 0, stream>>>(nullptr, es, N, L.chunk, shift, hist);
-    else rs_upsweep<false><<<G, kCsrBlock, 0, stream>>>(k0, es, N, L.chunk, shift, hist);
-    scan_u32_to_u64<<<256, 1024, 0, stream>>>(hist, offs, G, rowtot);
-    if (p == 0 && narrow)
-      rs_downsweep<true, unsigned><<<G, kCsrBlock, 0, stream>>>(nullptr, es, k1, N, L.chunk, shift, offs, rowtot);
-    else if (p == 0)
-      rs_downsweep<true, unsigned long long><<<G, kCsrBlock, 0, stream>>>(nullptr, es, k1, N, L.chunk, shift, offs,
-                                                                        rowtot);
-    else if (narrow)
-      rs_downsweep<false, unsigned><<<G, kCsrBlock, 0, stream>>>(k0, es, k1, N, L.chunk, shift, offs, rowtot);
-    else
-      rs_downsweep<false, unsigned long long><<<G, kCsrBlock, 0, stream>>>(k0, es, k1, N, L.chunk, shift, offs,
-                                                                         rowtot);
-    unsigned long long* t = k0;
-    k0 = k1;
-    k1 = t;
+    pass(p == 0 ? kArcs : kKeys, k0, k1, N, L.chunk, 8 * p, 0xff);
+    std::swap(k0, k1);
   }
   csr_count_unique<<<G, kCsrBlock, 0, stream>>>(k0, N, L.chunk, hist);
   scan_u32_to_u64<<<1, 1024, 0, stream>>>(hist, offs, G, nullptr);
-  csr_emit<<<G, kCsrBlock, 0, stream>>>(k0, N, L.chunk, L.B, n, offs, adj_out, off_out, m_out);
+  csr_emit<kEmitAll><<<G, kCsrBlock, 0, stream>>>(k0, N, L.chunk, L.B, n, offs, adj_out, off_out, m_out, nullptr,
+                                                  nullptr);
   return cudaGetLastError();
 }
 

@@ -8,9 +8,10 @@
 namespace kc {
 
 struct CsrLayout {
-  size_t status, keys0, keys1, hist, offs, rowtot, total;
+  size_t status, keys0, keys1, hist, offs, rowtot, starts, total;
   long long N;      // keys = 2 * edges
-  long long chunk;  // keys per CTA (multiple of the 2,048-key tile)
+  long long chunk;  // keys per CTA (multiple of the 2,048-key tile), for 2 * edges keys
+  long long chunk1; // the same for edges keys (a single graph's build)
   int grid;
   int B;            // bits of the target (local) id in a key
   int Bs;           // bits of the source (global) id in a key
