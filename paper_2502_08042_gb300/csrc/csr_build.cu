@@ -29,9 +29,10 @@
 // lower neighbours in order (B). A vertex's list is its lower neighbours
 // followed by its upper ones, both ascending, so emission writes the CSR from
 // A and B directly: 2B + B digit passes over E keys instead of 2B over 2E.
-// Repeats stay in both sequences as adjacent equal keys and are dropped on
-// emission (a repeat cannot become the sentinel: in B it would sort among the
-// keys whose larger endpoint has all B bits set).
+// Repeats stay in A as adjacent equal keys and are dropped on emission; the
+// first pass of B's sort drops them (and the sentinels), and the rest of B's
+// buffer holds sentinels written beforehand, which every stable pass keeps
+// behind the real keys.
 //
 // Lists come out ascending and duplicate-free, the canonical form of the CPU
 // builder, so the two are comparable bit for bit.
@@ -99,9 +100,11 @@ __device__ __forceinline__ unsigned long long edge_canon(const EdgeList& es, int
 }
 
 // Where a pass's keys come from: a key array, the edge list as two arcs per
-// edge (the first pass of the general build), or the edge list as one key per
-// edge (the first pass of a single graph's build).
-enum KeySrc : int { kKeys = 0, kArcs = 1, kCanon = 2 };
+// edge (the first pass of the general build), the edge list as one key per
+// edge (the first pass of a single graph's build), or a sorted key array
+// without its sentinels and without keys equal to their predecessor (the
+// first pass of B's sort).
+enum KeySrc : int { kKeys = 0, kArcs = 1, kCanon = 2, kKeysDrop = 3 };
 
 // digit of a pass: bits [shift, shift + 8) of the key, masked by dmask (the
 // last pass over a field narrower than a multiple of 8 bits keeps only its bits)
@@ -155,6 +158,11 @@ __global__ void __launch_bounds__(kCsrBlock) rs_upsweep(const unsigned long long
           atomicAdd(&cnt[warp][digit_of(k1, shift, dmask)], 1u);
         }
       }
+    }
+  } else if constexpr (kSrc == kKeysDrop) {
+    for (long long i = lo + tid; i < hi; i += kCsrBlock) {
+      const unsigned long long x = keys[i], p = i > 0 ? keys[i - 1] : kSentinel;
+      if (x != kSentinel && x != p) atomicAdd(&cnt[warp][digit_of(x, shift, dmask)], 1u);
     }
   } else {
     for (long long i = lo + tid; i < hi; i += kCsrBlock) atomicAdd(&cnt[warp][digit_of(keys[i], shift, dmask)], 1u);
@@ -220,6 +228,7 @@ __global__ void __launch_bounds__(kCsrBlock, 5) rs_downsweep(const unsigned long
   __shared__ Pos dstb[256];  // output position of the tile's first key of digit d, minus its tile offset
   __shared__ unsigned long long part64[kCsrBlock / 32];
   __shared__ unsigned part[kCsrBlock / 32];
+  __shared__ unsigned tile_keys;  // keys of the tile that are written (all but kKeysDrop's dropped ones)
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   const int G = gridDim.x;
   const unsigned lt = lanemask_lt();
@@ -247,7 +256,7 @@ __global__ void __launch_bounds__(kCsrBlock, 5) rs_downsweep(const unsigned long
       ((reinterpret_cast<unsigned long long>(es.src) | reinterpret_cast<unsigned long long>(es.dst)) & 15) == 0;
   auto prefetch = [&](long long t0) {
     const long long tn = min((long long)kTile, hi - t0);
-    if constexpr (kSrc != kKeys) {
+    if constexpr (kSrc == kArcs || kSrc == kCanon) {
       constexpr int kE = kSrc == kArcs ? kTile / 2 : kTile;  // edges per tile
       constexpr unsigned kHalf = 4u * kE;                     // bytes of one array's share
       const long long e0 = kSrc == kArcs ? t0 / 2 : t0, ne = kSrc == kArcs ? tn / 2 : tn;
@@ -283,8 +292,12 @@ __global__ void __launch_bounds__(kCsrBlock, 5) rs_downsweep(const unsigned long
     // the tile's edge el_of(it); kCanon: edge j_of(it)); 256 is the digit of no key
     auto j_of = [&](int it) { return warp * (kKeysPerThread * 32) + it * 32 + lane; };
     auto el_of = [&](int it) { return warp * (kKeysPerThread * 16) + (it >> 1) * 32 + lane; };
-    auto valid = [&](int it) { return kSrc == kArcs ? el_of(it) < tn / 2 : j_of(it) < tn; };
+    unsigned dropped = 0;  // kKeysDrop: bit it set for a dropped key
+    auto valid = [&](int it) {
+      return kSrc == kArcs ? el_of(it) < tn / 2 : (j_of(it) < tn && !((dropped >> it) & 1u));
+    };
     auto dg_of = [&](int it) { return valid(it) ? digit_of(k[it], shift, dmask) : 256; };
+    const unsigned long long pre = kSrc == kKeysDrop && tid == 0 && ts > 0 ? in[ts - 1] : kSentinel;
     asm volatile("cp.async.wait_all;" ::: "memory");
     __syncthreads();
     if constexpr (kSrc == kCanon) {
@@ -302,6 +315,14 @@ __global__ void __launch_bounds__(kCsrBlock, 5) rs_downsweep(const unsigned long
     } else {
 #pragma unroll
       for (int it = 0; it < kKeysPerThread; it++) k[it] = j_of(it) < tn ? stage[j_of(it)] : 0;
+      if constexpr (kSrc == kKeysDrop) {
+#pragma unroll
+        for (int it = 0; it < kKeysPerThread; it++) {
+          const int j = j_of(it);
+          const unsigned long long p = j > 0 ? stage[j - 1] : pre;
+          if (j < tn && (k[it] == kSentinel || k[it] == p)) dropped |= 1u << it;
+        }
+      }
     }
     __syncthreads();  // the stage is read: copy the next tile into it
     if (ts + kTile < hi) prefetch(ts + kTile);
@@ -342,6 +363,7 @@ __global__ void __launch_bounds__(kCsrBlock, 5) rs_downsweep(const unsigned long
     }
     dstb[tid] = (Pos)(run - lo_d);  // modulo 2^64 (2^32): adding a tile offset of digit tid lands at or after run
     run += tc;
+    if (tid == 255) tile_keys = lo_d + tc;
     __syncthreads();
 #pragma unroll
     for (int it = 0; it < kKeysPerThread; it++) {
@@ -350,7 +372,8 @@ __global__ void __launch_bounds__(kCsrBlock, 5) rs_downsweep(const unsigned long
     }
     __syncthreads();
     for (int w = 0; w < kCsrBlock / 32; w++) wcnt[w][tid] = 0;  // for the next tile
-    for (int j = tid; j < tn; j += kCsrBlock) {
+    const int tk = (int)tile_keys;
+    for (int j = tid; j < tk; j += kCsrBlock) {
       const unsigned long long key = buf[j];
       out[(unsigned long long)(Pos)(dstb[digit_of(key, shift, dmask)] + (Pos)j)] = key;
     }
@@ -438,20 +461,15 @@ __global__ void __launch_bounds__(kCsrBlock, 5) csr_count_unique(const unsigned 
 // unique keys ahead of it) is the chunk's base, plus the unique keys of
 // earlier rows and of earlier warps in its row (one warp scans the tile's rows
 // x warps counts), plus those of lower lanes (a ballot). A key's group is its
-// high field (source) in kEmitAll and kEmitUpper, its low B bits (the larger
-// endpoint) in kStartsLow and kEmitLower.
+// high field (the source, or the smaller endpoint).
 //   kEmitAll: adj[pos] = low B bits; the first arc of each source fixes
 //     offsets[] for that source and every source without arcs just below it;
 //     the last arc fills the offsets of the sources above it.
-//   kStartsLow (sequence B): starts[x] = unique keys of B whose larger
-//     endpoint is below x, for x in [0, n].
 //   kEmitUpper (sequence A): vertex u's upper neighbours go after its lower
 //     ones: adj[pos + starts[u + 1]] = larger endpoint, and offsets[x] = A's
 //     unique keys with smaller endpoint below x (csr_finish_offsets adds
 //     starts[x]); m = twice A's unique keys.
-//   kEmitLower (sequence B): vertex v's lower neighbours open its list:
-//     adj[offsets[v] + pos - starts[v]] = smaller endpoint.
-enum EmitMode : int { kEmitAll = 0, kStartsLow = 1, kEmitUpper = 2, kEmitLower = 3 };
+enum EmitMode : int { kEmitAll = 0, kEmitUpper = 2 };
 template <int kMode>
 __global__ void __launch_bounds__(kCsrBlock, 5) csr_emit(const unsigned long long* __restrict__ k, long long N,
                                                       long long chunk, int B, long long n,
@@ -495,8 +513,7 @@ __global__ void __launch_bounds__(kCsrBlock, 5) csr_emit(const unsigned long lon
       const unsigned long long sk = succ_key(edges, x[q], q, lane, warp, post);  // every lane: a shuffle
       const unsigned long long nx = i + 1 < N ? sk : kSentinel;
       const bool valid = i < hi && x[q] != kSentinel;
-      const bool low = kMode == kStartsLow || kMode == kEmitLower;
-      ps[q] = (i == 0 || p == kSentinel) ? -1 : (int)(low ? (p & mask) : (p >> B));
+      ps[q] = (i == 0 || p == kSentinel) ? -1 : (int)(p >> B);
       if (valid && nx == kSentinel) closing |= 1u << q;
       bal[q] = __ballot_sync(kFull, valid && (i == 0 || p != x[q]));
       if (lane == q) mine = __popc(bal[q]);
@@ -518,9 +535,6 @@ __global__ void __launch_bounds__(kCsrBlock, 5) csr_emit(const unsigned long lon
         if constexpr (kMode == kEmitUpper) {
           const long long u = (long long)(x[q] >> B);
           look0[q] = starts[u + 1];  // the lower neighbours of u come first
-        } else if constexpr (kMode == kEmitLower) {
-          const long long v = (long long)(x[q] & mask);
-          look0[q] = (unsigned long long)off[v] - starts[v];  // where v's lower neighbours start, minus B's offset
         }
       }
     }
@@ -530,32 +544,27 @@ __global__ void __launch_bounds__(kCsrBlock, 5) csr_emit(const unsigned long lon
       const bool u = (bal[q] >> lane) & 1u;
       const unsigned long long before = running + cnt[q * kW + warp] + __popc(bal[q] & lt);
       const long long hi_f = (long long)(x[q] >> B), lo_f = (long long)(x[q] & mask);
-      const long long s = (kMode == kStartsLow || kMode == kEmitLower) ? lo_f : hi_f;  // the key's group
+      const long long s = hi_f;  // the key's group
       if (u) {
         if constexpr (kMode == kEmitAll) {
           adj[before] = (int)lo_f;
           for (long long v = (long long)ps[q] + 1; v <= s; v++) off[v] = (long long)before;
-        } else if constexpr (kMode == kStartsLow) {
-          if (before > 0)  // starts[] is cleared: the groups up to the first need no store
-            for (long long v = (long long)ps[q] + 1; v <= s; v++) starts[v] = before;
-        } else if constexpr (kMode == kEmitUpper) {
+        } else {
           adj[before + look0[q]] = (int)lo_f;
           for (long long v = (long long)ps[q] + 1; v <= s; v++) off[v] = (long long)before;
-        } else {
-          adj[look0[q] + before] = (int)hi_f;
         }
       }
       // the last valid key (unique or a repeat) closes the groups above its own
-      if (kMode != kEmitLower && ((closing >> q) & 1u)) {
+      if ((closing >> q) & 1u) {
         const long long m_val = (long long)before + (u ? 1 : 0);
         if constexpr (kMode == kEmitAll) {
           for (long long v = s + 1; v <= n; v++) off[v] = m_val;
           *m_out = m_val;
         } else {
-          // the groups above the last one are filled by csr_fill_tail
+          // the groups above the last one are finished by csr_finish_offsets
           tail[0] = s;
           tail[1] = m_val;
-          if constexpr (kMode == kEmitUpper) *m_out = 2 * m_val;
+          *m_out = 2 * m_val;
         }
       }
     }
@@ -563,15 +572,74 @@ __global__ void __launch_bounds__(kCsrBlock, 5) csr_emit(const unsigned long lon
   }
 }
 
-// starts[v] = m for the groups above the last valid key's group s = tail[0]
-// (m = tail[1] unique keys in all), in parallel; every group at or below s was
-// written by csr_emit<kStartsLow>.
+// Sequence B: its E' = tail[1] keys, unique and ordered by (larger, smaller)
+// endpoint, then sentinels. starts[x] = keys of B whose larger endpoint is
+// below x, for x in [0, n] (cleared beforehand: the groups up to the first key's
+// need no store; the last key records its group in tail[0] and E' in tail[1]).
+__global__ void csr_lower_starts(const unsigned long long* __restrict__ Bq, long long E, int B, long long n,
+                                 unsigned long long* __restrict__ starts, long long* __restrict__ tail) {
+  constexpr int kU = 4;  // keys per thread per step, all loaded first
+  const unsigned long long mask = (1ull << B) - 1;
+  const long long stride = (long long)gridDim.x * blockDim.x;
+  for (long long i0 = blockIdx.x * (long long)blockDim.x + threadIdx.x; i0 < E; i0 += kU * stride) {
+    unsigned long long x[kU], xp[kU], xn[kU];
+#pragma unroll
+    for (int u = 0; u < kU; u++) {
+      const long long i = i0 + u * stride;
+      x[u] = i < E ? __ldcs(Bq + i) : kSentinel;
+      xp[u] = i < E && i > 0 ? __ldg(Bq + i - 1) : kSentinel;
+      xn[u] = i + 1 < E ? __ldg(Bq + i + 1) : kSentinel;
+    }
+#pragma unroll
+    for (int u = 0; u < kU; u++) {
+      const long long i = i0 + u * stride;
+      if (x[u] == kSentinel) continue;
+      const long long g = (long long)(x[u] & mask);
+      if (i > 0) {
+        const long long gp = (long long)(xp[u] & mask);  // a key: sentinels only follow the keys
+        for (long long v = gp + 1; v <= g; v++) starts[v] = (unsigned long long)i;
+      }
+      if (xn[u] == kSentinel) {
+        tail[0] = g;
+        tail[1] = i + 1;
+      }
+    }
+  }
+}
+
+// starts[v] = E' for the groups above the last key's group s = tail[0], in parallel.
 __global__ void csr_fill_starts(const long long* __restrict__ tail, long long n,
                                 unsigned long long* __restrict__ starts) {
   const long long s = tail[0], m_val = tail[1];
   for (long long v = s + 1 + blockIdx.x * (long long)blockDim.x + threadIdx.x; v <= n;
        v += (long long)gridDim.x * blockDim.x)
     starts[v] = (unsigned long long)m_val;
+}
+
+// The lower neighbours: B's key i (u, v) is v's (i - starts[v])-th lower
+// neighbour, and v's list opens with them.
+__global__ void csr_lower_emit(const unsigned long long* __restrict__ Bq, long long E, int B,
+                               const long long* __restrict__ off, const unsigned long long* __restrict__ starts,
+                               int* __restrict__ adj) {
+  constexpr int kU = 4;  // keys per thread per step, all loaded first, then all their lookups
+  const unsigned long long mask = (1ull << B) - 1;
+  const long long stride = (long long)gridDim.x * blockDim.x;
+  for (long long i0 = blockIdx.x * (long long)blockDim.x + threadIdx.x; i0 < E; i0 += kU * stride) {
+    unsigned long long x[kU], at[kU];
+#pragma unroll
+    for (int u = 0; u < kU; u++) {
+      const long long i = i0 + u * stride;
+      x[u] = i < E ? __ldcs(Bq + i) : kSentinel;
+    }
+#pragma unroll
+    for (int u = 0; u < kU; u++) {
+      const long long v = (long long)(x[u] & mask);
+      at[u] = x[u] != kSentinel ? (unsigned long long)__ldg(off + v) - __ldg(starts + v) : 0;
+    }
+#pragma unroll
+    for (int u = 0; u < kU; u++)
+      if (x[u] != kSentinel) adj[at[u] + (unsigned long long)(i0 + u * stride)] = (int)(x[u] >> B);
+  }
 }
 
 // offsets[v] = (A's unique keys with smaller endpoint below v) + starts[v]:
@@ -659,15 +727,23 @@ cudaError_t csr_build_launch(const CsrLayout& L, char* ws, long long n, long lon
   // keys number at most 2^32)
   auto pass = [&](int src_kind, const unsigned long long* in, unsigned long long* out, long long N, long long chunk,
                   int shift, int dmask) {
-    if (src_kind == kKeys) rs_upsweep<kKeys><<<G, kCsrBlock, 0, stream>>>(in, es, N, chunk, shift, dmask, hist);
-    else if (src_kind == kArcs) rs_upsweep<kArcs><<<G, kCsrBlock, 0, stream>>>(in, es, N, chunk, shift, dmask, hist);
-    else rs_upsweep<kCanon><<<G, kCsrBlock, 0, stream>>>(in, es, N, chunk, shift, dmask, hist);
+#define KC_UP(S) rs_upsweep<S><<<G, kCsrBlock, 0, stream>>>(in, es, N, chunk, shift, dmask, hist)
+    switch (src_kind) {
+      case kKeys: KC_UP(kKeys); break;
+      case kArcs: KC_UP(kArcs); break;
+      case kCanon: KC_UP(kCanon); break;
+      default: KC_UP(kKeysDrop); break;
+    }
+#undef KC_UP
     scan_u32_to_u64<<<256, 1024, 0, stream>>>(hist, offs, G, rowtot);
     const bool narrow = N <= (1ll << 32);
 #define KC_DOWN(S, P) rs_downsweep<S, P><<<G, kCsrBlock, 0, stream>>>(in, es, out, N, chunk, shift, dmask, offs, rowtot)
-    if (src_kind == kKeys) narrow ? KC_DOWN(kKeys, unsigned) : KC_DOWN(kKeys, unsigned long long);
-    else if (src_kind == kArcs) narrow ? KC_DOWN(kArcs, unsigned) : KC_DOWN(kArcs, unsigned long long);
-    else narrow ? KC_DOWN(kCanon, unsigned) : KC_DOWN(kCanon, unsigned long long);
+    switch (src_kind) {
+      case kKeys: narrow ? KC_DOWN(kKeys, unsigned) : KC_DOWN(kKeys, unsigned long long); break;
+      case kArcs: narrow ? KC_DOWN(kArcs, unsigned) : KC_DOWN(kArcs, unsigned long long); break;
+      case kCanon: narrow ? KC_DOWN(kCanon, unsigned) : KC_DOWN(kCanon, unsigned long long); break;
+      default: narrow ? KC_DOWN(kKeysDrop, unsigned) : KC_DOWN(kKeysDrop, unsigned long long); break;
+    }
 #undef KC_DOWN
   };
   if (!gv) {
@@ -683,33 +759,31 @@ cudaError_t csr_build_launch(const CsrLayout& L, char* ws, long long n, long lon
       std::swap(a0, a1);
     }
     const unsigned long long* A = a0;
+    // B: A without sentinels and repeats, stably by the larger endpoint; the
+    // first pass writes E' <= E keys over a buffer of sentinels
+    if ((e = cudaMemsetAsync(b1, 0xff, 8 * (size_t)E, stream)) != cudaSuccess) return e;
     const int passes_b = (L.B + 7) / 8;
     for (int p = 0; p < passes_b; p++) {
       const int bits = std::min(8, L.B - 8 * p);
-      pass(kKeys, p == 0 ? A : b0, b1, E, L.chunk1, 8 * p, (1 << bits) - 1);
+      pass(p == 0 ? kKeysDrop : kKeys, p == 0 ? A : b0, b1, E, L.chunk1, 8 * p, (1 << bits) - 1);
       std::swap(b0, b1);
     }
     const unsigned long long* Bq = b0;
     unsigned long long* starts = (unsigned long long*)(ws + L.starts);
-    unsigned long long* base_b = offs;      // B's unique keys before each chunk
-    unsigned long long* base_a = offs + G;  // A's
-    // the last valid key's group and the unique count (0, 0 when no key is
-    // valid: the tail fill then writes what the cleared arrays hold)
+    // B's last key's group and E' (0, 0 when no key is valid: the fills then
+    // write what the cleared arrays hold)
     long long* tail = (long long*)(ws + L.status + 64);
     const int fill_grid = (int)std::min<long long>((n + kCsrBlock) / kCsrBlock, 4 * (long long)G);
+    const int key_grid = (int)std::min<long long>((E + 4 * kCsrBlock - 1) / (4 * kCsrBlock), 8 * (long long)G);
     if ((e = cudaMemsetAsync(starts, 0, 8 * (size_t)(n + 1), stream)) != cudaSuccess) return e;
-    csr_count_unique<<<G, kCsrBlock, 0, stream>>>(Bq, E, L.chunk1, hist);
-    scan_u32_to_u64<<<1, 1024, 0, stream>>>(hist, base_b, G, nullptr);
-    csr_emit<kStartsLow><<<G, kCsrBlock, 0, stream>>>(Bq, E, L.chunk1, L.B, n, base_b, adj_out, off_out, m_out,
-                                                     starts, tail);
+    csr_lower_starts<<<key_grid, kCsrBlock, 0, stream>>>(Bq, E, L.B, n, starts, tail);
     csr_fill_starts<<<fill_grid, kCsrBlock, 0, stream>>>(tail, n, starts);
     csr_count_unique<<<G, kCsrBlock, 0, stream>>>(A, E, L.chunk1, hist);
-    scan_u32_to_u64<<<1, 1024, 0, stream>>>(hist, base_a, G, nullptr);
-    csr_emit<kEmitUpper><<<G, kCsrBlock, 0, stream>>>(A, E, L.chunk1, L.B, n, base_a, adj_out, off_out, m_out,
+    scan_u32_to_u64<<<1, 1024, 0, stream>>>(hist, offs, G, nullptr);
+    csr_emit<kEmitUpper><<<G, kCsrBlock, 0, stream>>>(A, E, L.chunk1, L.B, n, offs, adj_out, off_out, m_out,
                                                      starts, tail);
     csr_finish_offsets<<<fill_grid, kCsrBlock, 0, stream>>>(tail, n, off_out, starts);
-    csr_emit<kEmitLower><<<G, kCsrBlock, 0, stream>>>(Bq, E, L.chunk1, L.B, n, base_b, adj_out, off_out, m_out,
-                                                     starts, nullptr);
+    csr_lower_emit<<<key_grid, kCsrBlock, 0, stream>>>(Bq, E, L.B, off_out, starts, adj_out);
     return cudaGetLastError();
   }
   // a batch: two arcs per edge, sorted by (global source, local target)
