@@ -116,3 +116,30 @@ def test_edge_arrays_not_16_byte_aligned(kc, shift):
     want_off, want_adj = oracle.build_csr(n, s, d)
     np.testing.assert_array_equal(off.cpu().numpy(), want_off)
     np.testing.assert_array_equal(adj.cpu().numpy(), want_adj)
+
+
+@pytest.mark.parametrize("n", [256, 1 << 16])
+def test_top_vertex_with_repeats_and_loops(kc, n):
+    """n a power of two, so the top vertex n - 1 has every id bit set, like
+    the sentinel that marks self-loops: many edges to it, each repeated and
+    reversed, with self-loops on it and elsewhere, over several tiles."""
+    rng = np.random.default_rng(n)
+    top = n - 1
+    x = rng.integers(0, n, 5000).astype(np.int32)
+    s = np.concatenate([x, np.full(5000, top, np.int32), x[:2000], np.full(300, top, np.int32),
+                        rng.integers(0, n, 4000).astype(np.int32)])
+    d = np.concatenate([np.full(5000, top, np.int32), x, np.full(2000, top, np.int32),
+                        np.full(300, top, np.int32), rng.integers(0, n, 4000).astype(np.int32)])
+    perm = rng.permutation(s.size)
+    check_same(kc, n, s[perm], d[perm])
+
+
+def test_long_runs_of_one_repeated_edge(kc):
+    """One edge repeated 9,000 times (its copies span several 2,048-key tiles
+    and CTA chunks of both sorted sequences) among a random graph."""
+    rng = np.random.default_rng(5)
+    n = 3000
+    s = np.concatenate([np.full(9000, 17, np.int32), rng.integers(0, n, 20000).astype(np.int32)])
+    d = np.concatenate([np.full(9000, 2999, np.int32), rng.integers(0, n, 20000).astype(np.int32)])
+    perm = rng.permutation(s.size)
+    check_same(kc, n, s[perm], d[perm])
