@@ -503,7 +503,7 @@ def run_gpu(args):
                    "graphs_per_s": G_total / (bms / 1e3), "ms_per_batch": bms, "steps": 5, "warmup": 3,
                    "arcs": r["M"], "plain_loop_graphs_per_s": G_total / (r["loop_ms"] / 1e3),
                    "speedup_vs_plain_loop": r["loop_ms"] / bms, "identical_output": r["same"],
-                   "autotuned": {key: r["tuning"][key] for key in ("block", "ctas_per_sm", "smem_vertices")},
+                   "autotuned": {key: r["tuning"][key] for key in ("block", "ctas_per_sm", "smem_vertices", "cluster")},
                    "note": "CUDA events around each batched launch; the plain loop is one kcore_decompose per "
                            "graph on the same stream"}
     served = None

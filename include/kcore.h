@@ -141,9 +141,17 @@ typedef enum {
   KCORE_OPT_TAIL_ENTRIES = 25,        /* a scan of at most this many active-list entries runs on one
                                          CTA (0 .. 2^31 - 2; 0 = never) */
   KCORE_OPT_PARK_SLEEP_NS = 26,       /* nanosleep of a parked CTA between polls (0 .. 100000) */
-  KCORE_OPT_SCAN_ENTRIES = 27         /* modes 1 and 2: a scan gives each CTA at least this many active-list
+  KCORE_OPT_SCAN_ENTRIES = 27,        /* modes 1 and 2: a scan gives each CTA at least this many active-list
                                          entries (256 .. 2^20; default 512), so short lists are
                                          scanned by fewer CTAs */
+  KCORE_OPT_BATCH_CLUSTER = 28,       /* batched peel: 0 (default) = one CTA per graph; 2, 4 or 8 = a
+                                         graph with at least KCORE_OPT_BATCH_BIG_ARCS arcs is peeled
+                                         by a thread-block cluster of that many CTAs (512 or 1024
+                                         threads per CTA), so a batch's largest graphs no longer
+                                         hold it up; smaller graphs still take one CTA each */
+  KCORE_OPT_BATCH_BIG_ARCS = 29       /* batched peel with clusters: the arcs from which a graph takes a
+                                         cluster (0 = the batch's arcs divided by its CTAs, default;
+                                         else 1 .. 2^40) */
 } kcore_option;
 
 /* Counters of the last decomposition, or of the last CSR check (the three
@@ -175,6 +183,7 @@ typedef struct {
                               and 2 the offending offset value instead */
   int64_t tail_phases;     /* mode 2: phases run by one CTA in tail mode (not counted in barriers) */
   int64_t tail_episodes;   /* mode 2: times the grid parked while one CTA ran tail phases */
+  int64_t batch_cluster;   /* batched calls: CTAs per cluster for the large graphs (0: none) */
 } kcore_stats;
 
 /* Creates a handle on `device` (CUDA ordinal). The handle owns a workspace
@@ -322,16 +331,18 @@ typedef struct {
   int32_t smem_vertices; /* largest graph kept in shared memory under that shape */
   int32_t candidates;    /* launch shapes timed */
   double ms;             /* best time of one batched call with the chosen shape */
+  int32_t cluster;       /* CTAs per cluster for the large graphs chosen (KCORE_OPT_BATCH_CLUSTER) */
 } kcore_batch_tuning;
 
 /* Autotuner of the batched peel (not in the paper: the launch shape of the
  * batched form). Times each candidate launch shape -- 1024, 512 or 256
  * threads per CTA with 1..8 resident CTAs per SM, the shared-memory threshold
- * following the shape -- on the caller's own batch (the arguments of
+ * following the shape, and the clustered form with clusters of 2, 4 or 8 CTAs
+ * of 1024 threads or 4 of 512 -- on the caller's own batch (the arguments of
  * kcore_decompose_batched), best of `repeats` (1..100) calls after one
- * warm-up each, with CUDA events on `stream`. It then sets the handle's three
- * batch options to the fastest shape, runs the batch once more with it and
- * fills *best_out. Synchronous; the outputs hold that last, exact result.
+ * warm-up each, with CUDA events on `stream`. It then sets the handle's batch
+ * options (KCORE_OPT_BATCH_BIG_ARCS back to 0) to the fastest shape, runs the
+ * batch once more with it and fills *best_out. Synchronous; the outputs hold that last, exact result.
  * Errors: KCORE_ERR_INVALID (bad arguments; options unchanged), the first
  * input or memory error any call reports (KCORE_ERR_NOT_SIMPLE, _OOM;
  * options restored), KCORE_ERR_CUDA if no shape could run. */

@@ -102,7 +102,7 @@ class Stats(ctypes.Structure):
                                            "sample_vertices", "sample_recounts", "sample_bag",
                                            "sample_failed_validations", "sample_heads", "sample_reruns",
                                            "sample_miss_round", "invalid_check", "invalid_vertex", "invalid_arc",
-                                           "tail_phases", "tail_episodes")]
+                                           "tail_phases", "tail_episodes", "batch_cluster")]
 
 
 class Tuning(ctypes.Structure):
@@ -115,7 +115,7 @@ class Tuning(ctypes.Structure):
 class BatchTuning(ctypes.Structure):
     _fields_ = [("block", ctypes.c_int32), ("ctas_per_sm", ctypes.c_int32),
                 ("smem_vertices", ctypes.c_int32), ("candidates", ctypes.c_int32),
-                ("ms", ctypes.c_double)]
+                ("ms", ctypes.c_double), ("cluster", ctypes.c_int32)]
 
 
 # Every exported symbol of include/kcore.h with its ctypes signature.

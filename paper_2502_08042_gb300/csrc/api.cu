@@ -26,7 +26,7 @@ struct kcore_ctx {
                                   kc::kPollSleepDefault, 1024, -1, 0, kc::kLocalBatchesDefault, 0, 1,
                                   0, 0, -1, 1, 1, 0, kc::kPrecheckDefault, kc::kTailItemsDefault,
                                   kc::kTailEntriesDefault, kc::kParkSleepDefault,
-                                  kc::kScanMin};  // indexed by kcore_option
+                                  kc::kScanMin, 0, 0};  // indexed by kcore_option
   cudaStream_t last_stream = nullptr;
   bool pending = false;
   kc::PeelCtl* last_ctl = nullptr;
@@ -34,7 +34,7 @@ struct kcore_ctx {
   int* last_csr_status = nullptr;  // device status word of the last CSR build
   int* last_batch_status = nullptr;  // device status word of the last batched call
   int* last_validate_status = nullptr;  // device status words of the last CSR check
-  int last_batch_block = 0, last_batch_grid = 0, last_batch_smem_vertices = 0;
+  int last_batch_block = 0, last_batch_grid = 0, last_batch_smem_vertices = 0, last_batch_cluster = 0;
   unsigned long long* last_trace = nullptr;
   bool last_trace_phases = false;  // the trace holds one record per phase
   int last_max_rounds = 0;
@@ -262,6 +262,13 @@ kcore_status kcore_set_option(kcore_handle h, kcore_option opt, int64_t value) {
       break;
     case KCORE_OPT_BATCH_CTAS_PER_SM:
       if (value < 0 || value > 8) return fail(h, KCORE_ERR_INVALID, "batch CTAs per SM in [0, 8]");
+      break;
+    case KCORE_OPT_BATCH_CLUSTER:
+      if (value != 0 && value != 2 && value != 4 && value != 8)
+        return fail(h, KCORE_ERR_INVALID, "batch cluster must be 0, 2, 4 or 8");
+      break;
+    case KCORE_OPT_BATCH_BIG_ARCS:
+      if (value < 0 || value > ((int64_t)1 << 40)) return fail(h, KCORE_ERR_INVALID, "big arcs in [0, 2^40]");
       break;
     case KCORE_OPT_LOCAL_BATCHES:
       if (value < 0 || value > (1 << 20)) return fail(h, KCORE_ERR_INVALID, "local batches in [0, 2^20]");
@@ -708,10 +715,16 @@ kcore_status kcore_decompose_batched(kcore_handle h, int64_t num_graphs, int64_t
   a.next_graph = (int*)(ws + L.ctl);
   a.status = (int*)(ws + L.ctl) + 32;
   a.smem_deg_max = sv;
+  const int cluster = (int)h->opt[KCORE_OPT_BATCH_CLUSTER];
+  if (cluster > 1 && block != 512 && block != 1024)
+    return fail(h, KCORE_ERR_INVALID, "a clustered batch needs 512 or 1024 threads per CTA");
+  long long big_arcs = (long long)h->opt[KCORE_OPT_BATCH_BIG_ARCS];
+  if (big_arcs == 0) big_arcs = std::max<long long>(1, total_arcs / std::max(grid, 1));
   cudaError_t e;
   if ((e = cudaMemsetAsync(ws + L.ctl, 0, 256, stream)) != cudaSuccess) return cuda_fail(h, e, "memset");
-  if ((e = kc::batch_launch(a, block, grid, smem, sort_graphs, stream)) != cudaSuccess)
+  if ((e = kc::batch_launch(a, block, grid, smem, sort_graphs, stream, cluster, big_arcs)) != cudaSuccess)
     return cuda_fail(h, e, "batched launch");
+  h->last_batch_cluster = cluster > 1 ? cluster : 0;
   h->last_batch_status = a.status;
   h->last_batch_block = block;
   h->last_batch_grid = grid;
@@ -768,6 +781,7 @@ kcore_status kcore_sync_status(kcore_handle h) {
     h->stats.grid = h->last_batch_grid;
     h->stats.batch_block = h->last_batch_block;
     h->stats.batch_smem_vertices = h->last_batch_smem_vertices;
+    h->stats.batch_cluster = h->last_batch_cluster;
     if (bs[0] == kc::ST_NOT_SIMPLE) {
       long long val = (long long)(unsigned)bs[2] | ((long long)bs[3] << 32);
       return fail(h, KCORE_ERR_NOT_SIMPLE,

@@ -19,6 +19,18 @@
 // Persistent CTAs take graphs from a device counter in descending order of
 // arcs (longest-processing-time first), so the largest graphs start first.
 // Nothing waits on another CTA: the kernel has no spin-waits.
+//
+// A small batch is bound by its largest graphs, each walked by one CTA while
+// the others run out of work. The clustered form (batch_peel_cl) gives every
+// graph with more arcs than a threshold (by default the batch's arcs per CTA)
+// to a thread-block cluster of C CTAs: the cluster splits each list pass and
+// each subround's frontier arcs among its CTAs, keeps the induced degrees in
+// L2 and its counters in the first CTA's shared memory (reached through
+// distributed shared memory), and closes every phase with the hardware cluster
+// barrier. Once a cluster draws a graph below the threshold (the order is by
+// arcs, so every later one is too), its CTAs go back to one graph each.
+#include <cooperative_groups.h>
+
 #include <climits>
 
 #include "kcore_batched.h"
@@ -39,6 +51,7 @@ struct BatchShared {
   int g;
   int total;
   int bad;  // this graph failed a bounds check: stop peeling it
+  int base;  // clustered peel: this CTA's output position for the current tile
 };
 
 // Records a failed bounds check (first one wins: code, graph-local value) and
@@ -368,6 +381,302 @@ __device__ void peel_one_graph(const GraphDesc& gd, int smem_deg_max, int* statu
   __syncthreads();
 }
 
+// ------------------------------------------------------------------ clustered form
+namespace cg = cooperative_groups;
+
+// Counters of a cluster, kept in its first CTA. Each phase (the work between
+// two cluster barriers) accumulates into slot[phase % 3] -- [0] and [1]
+// counts, [2] a minimum, [3] a maximum -- which every CTA reads after the
+// barrier that ends the phase; the first CTA clears the slot of the next phase
+// at the start of each phase (its last readers passed a barrier since).
+struct ClusterCtl {
+  int g;    // graph drawn for the cluster
+  int bad;  // the graph failed a bounds check
+  int slot[3][4];
+};
+
+template <int BLOCK, int C>
+struct ClusterPeel {
+  cg::cluster_group cl;
+  ClusterCtl* lc;  // the first CTA's counters
+  BatchShared<BLOCK>& sh;
+  int* status;
+  int r;       // this CTA's rank in the cluster
+  int ph = 0;  // phase index (the same in every CTA)
+
+  __device__ ClusterPeel(ClusterCtl* lead, BatchShared<BLOCK>& s, int* st)
+      : cl(cg::this_cluster()), lc(lead), sh(s), status(st), r((int)cg::this_cluster().block_rank()) {}
+
+  __device__ int* slot(int p) const { return lc->slot[p % 3]; }
+  __device__ void clear(int p) const {
+    int* x = slot(p);
+    x[0] = 0;
+    x[1] = 0;
+    x[2] = INT_MAX;
+    x[3] = 0;
+  }
+  __device__ bool first() const { return r == 0 && threadIdx.x == 0; }
+  // ends a phase: this CTA's bounds-check failure goes to the cluster flag,
+  // then the cluster barrier (release / acquire: the phase's stores, global
+  // and distributed shared, are seen by every CTA after it)
+  __device__ void next_phase() {
+    if (threadIdx.x == 0 && sh.bad) atomicOr(&lc->bad, 1);
+    cl.sync();
+    ph++;
+    if (first()) clear(ph + 1);
+  }
+  // this CTA's part [lo, hi) of a range of len entries
+  __device__ long long part_lo(long long len) const { return len * r / C; }
+  __device__ long long part_hi(long long len) const { return len * (r + 1) / C; }
+
+  // entries of A with D == k go to F (count in this phase's slot[0])
+  __device__ void select(const int* A, int la, int n, int* F, const DegStore& D, int k) {
+    const int lo = (int)part_lo(la), hi = (int)part_hi(la);
+    for (int base = lo; base < hi; base += BLOCK * kScanItems) {
+      int v[kScanItems];
+      unsigned take = 0;
+#pragma unroll
+      for (int q = 0; q < kScanItems; q++) {
+        const int i = base + q * BLOCK + threadIdx.x;
+        v[q] = -1;
+        if (i < hi) {
+          const int x = __ldcg(A + i);  // written by other CTAs of the cluster
+          v[q] = (unsigned)x < (unsigned)n ? x : -1;
+        }
+      }
+#pragma unroll
+      for (int q = 0; q < kScanItems; q++)
+        if (v[q] >= 0 && D.get(v[q]) == k) take |= 1u << q;
+      int tot;
+      const int pos = block_excl_scan(__popc(take), sh, &tot);
+      if (threadIdx.x == 0) sh.base = tot ? atomicAdd(&slot(ph)[0], tot) : 0;
+      __syncthreads();
+      int p = sh.base + pos;
+#pragma unroll
+      for (int q = 0; q < kScanItems; q++)
+        if ((take >> q) & 1u) F[p++] = v[q];
+      __syncthreads();  // sh.base is reused by the next tile
+    }
+  }
+
+  // entries of A with D > k survive into out (count slot[0], minimum slot[2]);
+  // those at k + 1 also go to F (count slot[1])
+  __device__ void compact(const int* A, int la, int n, int* out, int* F, const DegStore& D, int k) {
+    const int lo = (int)part_lo(la), hi = (int)part_hi(la);
+    int lmin = INT_MAX;
+    for (int base = lo; base < hi; base += BLOCK * kScanItems) {
+      int v[kScanItems];
+      unsigned keep = 0, front = 0;
+#pragma unroll
+      for (int q = 0; q < kScanItems; q++) {
+        const int i = base + q * BLOCK + threadIdx.x;
+        v[q] = -1;
+        if (i < hi) {
+          const int x = __ldcg(A + i);
+          v[q] = (unsigned)x < (unsigned)n ? x : -1;
+        }
+      }
+#pragma unroll
+      for (int q = 0; q < kScanItems; q++) {
+        if (v[q] >= 0) {
+          const int d = D.get(v[q]);
+          if (d > k) {
+            keep |= 1u << q;
+            lmin = min(lmin, d);
+            if (d == k + 1) front |= 1u << q;
+          }
+        }
+      }
+      int tot;
+      const int pos = block_excl_scan(__popc(keep) | (__popc(front) << 16), sh, &tot);
+      if (threadIdx.x == 0) {
+        const int bk = (tot & 0xffff) ? atomicAdd(&slot(ph)[0], tot & 0xffff) : 0;
+        const int bf = (tot >> 16) ? atomicAdd(&slot(ph)[1], tot >> 16) : 0;
+        sh.base = bk;
+        sh.cnt = bf;
+      }
+      __syncthreads();
+      int pk = sh.base + (pos & 0xffff), pf = sh.cnt + (pos >> 16);
+#pragma unroll
+      for (int q = 0; q < kScanItems; q++) {
+        if ((keep >> q) & 1u) out[pk++] = v[q];
+        if ((front >> q) & 1u) F[pf++] = v[q];
+      }
+      __syncthreads();
+    }
+    const int m = block_min(lmin, sh);
+    if (threadIdx.x == 0 && m != INT_MAX) atomicMin(&slot(ph)[2], m);
+  }
+
+  // Peels one graph with the whole cluster (Algorithm 1's levels and
+  // subrounds, the online Peel of Algorithm 3, as peel_one_graph does in one CTA).
+  __device__ void peel(const GraphDesc& gd) {
+    const int tid = threadIdx.x, lane = tid & 31;
+    if (first()) {
+      lc->bad = 0;
+      clear(0);
+      clear(1);
+      clear(2);
+    }
+    if (tid == 0) sh.bad = 0;
+    ph = 0;
+    cl.sync();
+    const int n = (int)gd.n;
+    const long long* O = gd.off;
+    // phase: degrees (least and largest)
+    int lmin = INT_MAX, lmax = 0;
+    for (long long v = (long long)r * BLOCK + tid; v < n; v += (long long)C * BLOCK) {
+      long long o0 = O[v], o1 = O[v + 1];
+      if (o0 < 0 || o1 < o0 || o1 > gd.m || o1 - o0 >= n) {
+        flag_bad(status, 1, v, &sh.bad);
+        o1 = o0;
+      }
+      lmin = min(lmin, (int)(o1 - o0));
+      lmax = max(lmax, (int)(o1 - o0));
+    }
+    lmin = block_min(lmin, sh);
+    lmax = -block_min(-lmax, sh);
+    if (tid == 0) {
+      atomicMin(&slot(ph)[2], lmin);
+      atomicMax(&slot(ph)[3], lmax);
+    }
+    next_phase();
+    int k = slot(ph - 1)[2];
+    const int dmax = slot(ph - 1)[3];
+    if (lc->bad) {  // malformed offsets: leave this graph (its outputs are undefined)
+      if (first()) *gd.kmax = -1;
+      return;
+    }
+    const bool narrow = dmax < 65536;
+    const DegStore D{gd.deg, false, narrow, l2_evict_last_policy()};
+    // phase: initial induced degrees, the identity active list
+    const int nw = narrow ? (n + 1) / 2 : n;
+    for (long long i = (long long)r * BLOCK + tid; i < nw; i += (long long)C * BLOCK) {
+      const int v0 = narrow ? 2 * (int)i : (int)i;
+      const int d0 = (int)(O[v0 + 1] - O[v0]);
+      const int d1 = narrow && v0 + 1 < n ? (int)(O[v0 + 2] - O[v0 + 1]) : 0;
+      D.put_word((int)i, d0, d1);
+    }
+    for (long long v = (long long)r * BLOCK + tid; v < n; v += (long long)C * BLOCK) gd.A0[v] = (int)v;
+    next_phase();
+    int* A = gd.A0;
+    int* An = gd.A1;
+    int la = n, kmax = 0;
+    select(A, la, n, gd.F0, D, k);
+    next_phase();
+    int nf = slot(ph - 1)[0];
+    for (;;) {
+      int* Fc = gd.F0;
+      int* Fn = gd.F1;
+      while (nf > 0) {
+        for (long long i = (long long)r * BLOCK + tid; i < nf; i += (long long)C * BLOCK) {
+          const int v = __ldcg(Fc + i);
+          if ((unsigned)v < (unsigned)n) gd.core[v] = k;
+          else flag_bad(status, 6, v, &sh.bad);
+        }
+        // a large frontier: the CTAs take whole chunks of BLOCK frontier
+        // vertices in turn; a small one: every CTA walks every chunk and takes
+        // its share of the chunk's arcs
+        const bool whole = nf >= 2 * C * BLOCK;
+        for (int c0 = whole ? r * BLOCK : 0; c0 < nf; c0 += whole ? C * BLOCK : BLOCK) {
+          const int cnum = min(BLOCK, nf - c0);
+          int len = 0;
+          long long st = 0;
+          if (tid < cnum) {
+            const int v = __ldcg(Fc + c0 + tid);
+            if ((unsigned)v < (unsigned)n) {
+              st = O[v];
+              const long long e = O[v + 1];
+              if (st < 0 || e < st || e > gd.m || e - st >= n) flag_bad(status, 2, v, &sh.bad);
+              else len = (int)(e - st);
+            } else {
+              flag_bad(status, 3, v, &sh.bad);
+            }
+          }
+          int total;
+          const int ex = block_excl_scan(len, sh, &total);
+          sh.pre[tid] = ex;
+          sh.start[tid] = st;
+          __syncthreads();
+          const int jlo = whole ? 0 : (int)part_lo(total), jhi = whole ? total : (int)part_hi(total);
+          for (int j0 = jlo; j0 < jhi; j0 += BLOCK * kBatchIlp) {
+            int u[kBatchIlp];
+#pragma unroll
+            for (int q = 0; q < kBatchIlp; q++) {
+              const int j = j0 + q * BLOCK + tid;
+              u[q] = -1;
+              if (j < jhi) {
+                int lo = 0, hi = cnum;
+                while (lo < hi) {
+                  const int mid = (lo + hi) >> 1;
+                  if (sh.pre[mid] <= j) lo = mid + 1;
+                  else hi = mid;
+                }
+                const int idx = lo - 1;
+                const long long arc = idx >= 0 ? sh.start[idx] + (j - sh.pre[idx]) : -1;
+                if (idx < 0 || arc < 0 || arc >= gd.m) {
+                  flag_bad(status, 4, arc, &sh.bad);
+                } else {
+                  u[q] = ld_stream_s32(gd.adj + arc);
+                  if ((unsigned)u[q] >= (unsigned)n) {
+                    flag_bad(status, 5, u[q], &sh.bad);
+                    u[q] = -1;
+                  }
+                }
+              }
+            }
+#pragma unroll
+            for (int q = 0; q < kBatchIlp; q++) {
+              // d~ lives in L2: the decrement goes unread (a vertex at or
+              // below k never returns k + 1)
+              const bool cross = u[q] >= 0 && D.dec(u[q]) == k + 1;
+              const unsigned m = __ballot_sync(kFull, cross);
+              if (m) {
+                int base = 0;
+                if (lane == __ffs(m) - 1) base = atomicAdd(&slot(ph)[0], __popc(m));
+                base = __shfl_sync(kFull, base, __ffs(m) - 1);
+                const int pos = base + __popc(m & lanemask_lt());
+                if (cross) {
+                  if (pos < n) Fn[pos] = u[q];
+                  else flag_bad(status, 7, pos, &sh.bad);
+                }
+              }
+            }
+          }
+          __syncthreads();  // sh.pre / sh.start are reused by the next chunk
+        }
+        next_phase();
+        nf = slot(ph - 1)[0];
+        if (nf > n) nf = 0;  // cannot happen: every vertex lands on k at most once per level
+        if (lc->bad) {
+          if (first()) *gd.kmax = -1;
+          return;
+        }
+        int* t = Fc;
+        Fc = Fn;
+        Fn = t;
+      }
+      kmax = k;
+      compact(A, la, n, An, gd.F0, D, k);
+      next_phase();
+      la = slot(ph - 1)[0];
+      nf = slot(ph - 1)[1];
+      const int dmin = slot(ph - 1)[2];
+      int* t = A;
+      A = An;
+      An = t;
+      if (la == 0) break;
+      if (dmin != k + 1) {
+        select(A, la, n, gd.F0, D, dmin);
+        next_phase();
+        nf = slot(ph - 1)[0];
+      }
+      k = dmin;
+    }
+    if (first()) *gd.kmax = kmax;
+  }
+};
+
 template <int BLOCK>
 __global__ void __launch_bounds__(BLOCK, (BLOCK >= 1024 ? 1 : 2048 / BLOCK / 2)) batch_peel(BatchArgs a) {
   extern __shared__ int sdeg[];
@@ -403,6 +712,71 @@ __global__ void __launch_bounds__(BLOCK, (BLOCK >= 1024 ? 1 : 2048 / BLOCK / 2))
     gd.A1 = a.A1 + v0;
     gd.F0 = a.F0 + v0;
     gd.F1 = a.F1 + v0;
+    peel_one_graph<BLOCK>(gd, a.smem_deg_max, a.status, sdeg, sh);
+  }
+}
+
+// The batched peel with clusters of C CTAs for the graphs of at least big_arcs
+// arcs (see the file comment). A cluster draws graphs together while they are
+// big; from the first graph below the threshold on, its CTAs draw one each.
+template <int BLOCK, int C>
+__global__ void __cluster_dims__(C, 1, 1) __launch_bounds__(BLOCK, (BLOCK >= 1024 ? 1 : 2048 / BLOCK / 2))
+    batch_peel_cl(BatchArgs a, long long big_arcs) {
+  extern __shared__ int sdeg[];
+  __shared__ BatchShared<BLOCK> sh;
+  __shared__ ClusterCtl ctl;
+  cg::cluster_group cl = cg::this_cluster();
+  ClusterCtl* lc = cl.map_shared_rank(&ctl, 0);
+  const bool lead = cl.block_rank() == 0;
+  bool together = true;
+  for (;;) {
+    long long gi;
+    if (together) {
+      if (lead && threadIdx.x == 0) ctl.g = atomicAdd(a.next_graph, 1);
+      cl.sync();
+      gi = lc->g;
+      cl.sync();  // every CTA has read the draw before the next one
+    } else {
+      if (threadIdx.x == 0) sh.g = atomicAdd(a.next_graph, 1);
+      __syncthreads();
+      gi = sh.g;
+      __syncthreads();
+    }
+    if (gi >= a.G) break;
+    const long long g = a.order ? a.order[gi] : gi;
+    if (g < 0 || g >= a.G) {
+      if (threadIdx.x == 0) flag_bad(a.status, 8, g, &sh.bad);
+      continue;
+    }
+    GraphDesc gd;
+    const long long v0 = a.gv[g];
+    gd.n = a.gv[g + 1] - v0;
+    if (v0 < 0 || gd.n < 0 || v0 + gd.n > a.N) {
+      if (threadIdx.x == 0 && (!together || lead)) {
+        flag_bad(a.status, 9, g, &sh.bad);
+        a.kmax[g] = -1;
+      }
+      continue;
+    }
+    gd.m = a.m;
+    gd.off = a.off + v0;
+    gd.adj = a.adj;
+    gd.core = a.core + v0;
+    gd.kmax = a.kmax + g;
+    gd.deg = a.deg + v0;
+    gd.A0 = a.A0 + v0;
+    gd.A1 = a.A1 + v0;
+    gd.F0 = a.F0 + v0;
+    gd.F1 = a.F1 + v0;
+    if (together && gd.n > 0 && gd.n < INT_MAX && gd.off[gd.n] - gd.off[0] >= big_arcs) {
+      ClusterPeel<BLOCK, C> cp(lc, sh, a.status);
+      cp.peel(gd);
+      continue;
+    }
+    if (together) {
+      together = false;  // the first CTA peels this graph, the others draw their own
+      if (!lead) continue;
+    }
     peel_one_graph<BLOCK>(gd, a.smem_deg_max, a.status, sdeg, sh);
   }
 }
@@ -473,6 +847,16 @@ cudaError_t launch_block(const BatchArgs& a, int grid, size_t smem, cudaStream_t
   batch_peel<BLOCK><<<grid, BLOCK, smem, stream>>>(a);
   return cudaGetLastError();
 }
+template <int BLOCK, int C>
+cudaError_t launch_cluster(const BatchArgs& a, int grid, size_t smem, long long big_arcs, cudaStream_t stream) {
+  cudaError_t e = cudaFuncSetAttribute(batch_peel_cl<BLOCK, C>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       (int)smem);
+  if (e != cudaSuccess) return e;
+  grid = grid / C * C;
+  if (grid < C) grid = C;
+  batch_peel_cl<BLOCK, C><<<grid, BLOCK, smem, stream>>>(a, big_arcs);
+  return cudaGetLastError();
+}
 template <int BLOCK>
 int occupancy_block(size_t smem) {
   int nb = 0;
@@ -515,7 +899,7 @@ size_t batch_static_smem(int block) {
 }
 
 cudaError_t batch_launch(const BatchArgs& a, int block, int grid, size_t smem, bool sort_graphs,
-                         cudaStream_t stream) {
+                         cudaStream_t stream, int cluster, long long big_arcs) {
   if (sort_graphs && a.order) {
     int P = 1;
     while (P < a.G) P <<= 1;
@@ -524,6 +908,18 @@ cudaError_t batch_launch(const BatchArgs& a, int block, int grid, size_t smem, b
     if (e != cudaSuccess) return e;
     batch_order<<<1, 1024, ss, stream>>>(a.gv, a.off, a.G, (int*)a.order);
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
+  }
+  if (cluster > 1) {
+    const int key = block * 16 + cluster;
+    switch (key) {
+      case 512 * 16 + 2: return launch_cluster<512, 2>(a, grid, smem, big_arcs, stream);
+      case 512 * 16 + 4: return launch_cluster<512, 4>(a, grid, smem, big_arcs, stream);
+      case 512 * 16 + 8: return launch_cluster<512, 8>(a, grid, smem, big_arcs, stream);
+      case 1024 * 16 + 2: return launch_cluster<1024, 2>(a, grid, smem, big_arcs, stream);
+      case 1024 * 16 + 4: return launch_cluster<1024, 4>(a, grid, smem, big_arcs, stream);
+      case 1024 * 16 + 8: return launch_cluster<1024, 8>(a, grid, smem, big_arcs, stream);
+    }
+    return cudaErrorInvalidValue;
   }
   switch (block) {
     case 256: return launch_block<256>(a, grid, smem, stream);

@@ -58,7 +58,9 @@ cudaError_t desc_launch(const GraphDesc* table, const SlotList& list, int* next,
 size_t desc_static_smem();
 int batch_occupancy(int block, size_t smem);
 size_t batch_static_smem(int block);
+// cluster > 1 (512 or 1024 threads, 2, 4 or 8 CTAs): the clustered form, for
+// graphs with at least big_arcs arcs
 cudaError_t batch_launch(const BatchArgs& a, int block, int grid, size_t smem, bool sort_graphs,
-                         cudaStream_t stream);
+                         cudaStream_t stream, int cluster = 0, long long big_arcs = 0);
 
 }  // namespace kc

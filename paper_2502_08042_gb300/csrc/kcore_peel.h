@@ -13,7 +13,7 @@ constexpr int kHandoff = 8;  // words of loop state CTA 0 hands the parked CTAs 
 // Options of a handle (kcore_option values 0 .. kNumOptions - 1) and the
 // tail-mode defaults: off, because every threshold measured on GB300 was
 // slower on R-MAT scale 24 and the kNN workload (kcore_autotune tries it).
-constexpr int kNumOptions = 28;
+constexpr int kNumOptions = 30;
 constexpr long long kTailItemsDefault = 0;
 constexpr long long kTailEntriesDefault = 0;
 constexpr long long kParkSleepDefault = 256;

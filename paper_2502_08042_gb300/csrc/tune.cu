@@ -13,7 +13,7 @@
 namespace {
 
 struct Shape {
-  int block, ctas_per_sm;
+  int block, ctas_per_sm, cluster;
 };
 
 // Candidate shapes: threads per CTA x resident CTAs per SM, within one SM's
@@ -21,24 +21,31 @@ struct Shape {
 // vertices as fit with that many CTAs per SM).
 std::vector<Shape> candidates() {
   std::vector<Shape> c;
-  for (int cps : {1, 2}) c.push_back({1024, cps});
-  for (int cps : {1, 2, 3, 4}) c.push_back({512, cps});
-  for (int cps : {2, 4, 6, 8}) c.push_back({256, cps});
+  for (int cps : {1, 2}) c.push_back({1024, cps, 0});
+  for (int cps : {1, 2, 3, 4}) c.push_back({512, cps, 0});
+  for (int cps : {2, 4, 6, 8}) c.push_back({256, cps, 0});
+  // the clustered form for the batch's largest graphs
+  for (int cl : {2, 4, 8}) c.push_back({1024, 2, cl});
+  c.push_back({512, 2, 4});
   return c;
 }
 
 struct OptionSnapshot {
   kcore_handle h;
-  int64_t block = 0, sv = 0, cps = 0;
+  int64_t block = 0, sv = 0, cps = 0, cluster = 0, big = 0;
   explicit OptionSnapshot(kcore_handle hh) : h(hh) {
     kcore_get_option(h, KCORE_OPT_BATCH_BLOCK, &block);
     kcore_get_option(h, KCORE_OPT_BATCH_SMEM_VERTICES, &sv);
     kcore_get_option(h, KCORE_OPT_BATCH_CTAS_PER_SM, &cps);
+    kcore_get_option(h, KCORE_OPT_BATCH_CLUSTER, &cluster);
+    kcore_get_option(h, KCORE_OPT_BATCH_BIG_ARCS, &big);
   }
   void restore() const {
     kcore_set_option(h, KCORE_OPT_BATCH_BLOCK, block);
     kcore_set_option(h, KCORE_OPT_BATCH_SMEM_VERTICES, sv);
     kcore_set_option(h, KCORE_OPT_BATCH_CTAS_PER_SM, cps);
+    kcore_set_option(h, KCORE_OPT_BATCH_CLUSTER, cluster);
+    kcore_set_option(h, KCORE_OPT_BATCH_BIG_ARCS, big);
   }
 };
 
@@ -46,6 +53,8 @@ kcore_status apply(kcore_handle h, const Shape& s) {
   kcore_status st = kcore_set_option(h, KCORE_OPT_BATCH_BLOCK, s.block);
   if (st == KCORE_OK) st = kcore_set_option(h, KCORE_OPT_BATCH_SMEM_VERTICES, -1);
   if (st == KCORE_OK) st = kcore_set_option(h, KCORE_OPT_BATCH_CTAS_PER_SM, s.ctas_per_sm);
+  if (st == KCORE_OK) st = kcore_set_option(h, KCORE_OPT_BATCH_CLUSTER, s.cluster);
+  if (st == KCORE_OK) st = kcore_set_option(h, KCORE_OPT_BATCH_BIG_ARCS, 0);
   return st;
 }
 
@@ -66,7 +75,7 @@ extern "C" kcore_status kcore_autotune_batched(kcore_handle h, int64_t num_graph
     cudaGetLastError();
     return KCORE_ERR_CUDA;
   }
-  Shape best{0, 0};
+  Shape best{0, 0, 0};
   double best_ms = 0;
   int timed = 0;
   kcore_status result = KCORE_OK;
@@ -116,6 +125,7 @@ extern "C" kcore_status kcore_autotune_batched(kcore_handle h, int64_t num_graph
   kcore_get_stats(h, &stats);
   best_out->block = best.block;
   best_out->ctas_per_sm = best.ctas_per_sm;
+  best_out->cluster = best.cluster;
   best_out->smem_vertices = (int32_t)stats.batch_smem_vertices;
   best_out->candidates = timed;
   best_out->ms = best_ms;

@@ -20,7 +20,8 @@ OPTIONS = {"sync_mode": 0, "ctas_per_sm": 1, "slice_arcs": 2, "local_queue": 3, 
            "batch_smem_vertices": 12, "batch_ctas_per_sm": 13, "local_batches": 14, "level_window": 15,
            "batch_update": 16, "sampling": 17, "sample_mu": 18, "sample_threshold": 19, "sample_seed": 20,
            "sample_check": 21, "warp_combine": 22, "precheck_items": 23, "tail_items": 24,
-           "tail_entries": 25, "park_sleep_ns": 26, "scan_entries": 27}
+           "tail_entries": 25, "park_sleep_ns": 26, "scan_entries": 27, "batch_cluster": 28,
+           "batch_big_arcs": 29}
 TRACE_FIELDS = ("t_start", "t_scanned", "t_done", "level", "scanned", "found", "queued", "scan_ctas",
                 "arcs", "decrements", "max_cta_scan_ns", "max_cta_start_delay_ns", "busy_ns",
                 "batches")
