@@ -506,6 +506,7 @@ def run_gpu(args):
                    "autotuned": {key: r["tuning"][key] for key in ("block", "ctas_per_sm", "smem_vertices", "cluster")},
                    "note": "CUDA events around each batched launch; the plain loop is one kcore_decompose per "
                            "graph on the same stream"}
+        batched["small_batch"] = small_batch_measure(local)
     served = None
     if args.workload == "rmat24" and ws == 1 and not args.no_served:
         R = WORKLOADS["served"]["requests"]
@@ -639,8 +640,60 @@ def gather_batch_results(core_local, kmax_local, own, gv_global, ws: int, rank: 
     return core, kmax
 
 
+def small_batch_measure(local: int, G: int = 512, steps: int = 5, warmup: int = 2):
+    """The first G graphs of the batched workload, a batch bound by its largest
+    graphs: one batched call with the default launch shape (one CTA per graph)
+    against the shape the library's autotuner keeps (which may give the largest
+    graphs thread-block clusters), both timed with CUDA events, identical
+    output checked."""
+    import torch
+
+    from paper_2502_08042_gb300 import KCore
+
+    dev = torch.device("cuda", local)
+    spec, gv, eoff, s, d = _batch_inputs(G)
+    N = int(gv[-1])
+    k = KCore(local)
+    gvd = torch.from_numpy(gv).to(dev)
+    off, adj_buf, m_t = k.build_csr_batched(gvd, torch.from_numpy(eoff).to(dev), torch.from_numpy(s).to(dev),
+                                            torch.from_numpy(d).to(dev), int(spec[:, 0].max()), sync=False)
+    k.sync()
+    M = int(m_t.item())
+    adj = adj_buf[:M].clone()
+    del adj_buf
+    torch.cuda.empty_cache()
+    core = torch.empty(N, dtype=torch.int32, device=dev)
+    kmax = torch.empty(G, dtype=torch.int32, device=dev)
+
+    def timed():
+        for _ in range(warmup):
+            k.decompose_batched(gvd, off, adj, core, kmax)
+        ts = []
+        for _ in range(steps):
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record()
+            k.decompose_batched(gvd, off, adj, core, kmax, sync=False)
+            e1.record()
+            k.sync()
+            torch.cuda.synchronize()
+            ts.append(e0.elapsed_time(e1))
+        return sum(ts) / len(ts)
+
+    plain_ms = timed()
+    ref = core.clone()
+    _, _, tuning = k.autotune_batched(gvd, off, adj, core, kmax, repeats=2)
+    tuned_ms = timed()
+    same = bool(torch.equal(core, ref))
+    k.close()
+    return {"workload": f"the first {G} graphs of the batched workload", "graphs": G, "arcs": M,
+            "ms_one_cta_per_graph": plain_ms, "ms_autotuned": tuned_ms,
+            "speedup": plain_ms / tuned_ms, "identical_output": same,
+            "autotuned": {key: tuning[key] for key in ("block", "ctas_per_sm", "smem_vertices", "cluster")},
+            "note": f"mean of {steps} calls after {warmup} each; one CTA per graph is the default shape"}
+
+
 def batched_measure(local: int, steps: int, warmup: int, G_total: int, ws: int = 1, rank: int = 0,
-                    e2e: bool = True):
+                    e2e: bool = True, cluster: int = -1):
     """The batched workload on one GPU: generation, segmented CSR build, the
     library's autotuner (untimed), `steps` timed batched launches after
     `warmup`, then a loop of plain single-graph launches over the same graphs
@@ -683,10 +736,15 @@ def batched_measure(local: int, steps: int, warmup: int, G_total: int, ws: int =
     core = torch.empty(N, dtype=torch.int32, device=dev)
     kmax = torch.empty(G, dtype=torch.int32, device=dev)
     flush = torch.empty(2 * L2_BYTES // 4, dtype=torch.int32, device=dev)
-    # launch shape picked by the library's autotuner on this batch (untimed)
-    t_tune = time.perf_counter()
-    _, _, tuning = k.autotune_batched(gvd, off, adj, core, kmax, repeats=2)
-    tuning["tune_s"] = time.perf_counter() - t_tune
+    if cluster < 0:
+        # launch shape picked by the library's autotuner on this batch (untimed)
+        t_tune = time.perf_counter()
+        _, _, tuning = k.autotune_batched(gvd, off, adj, core, kmax, repeats=2)
+        tuning["tune_s"] = time.perf_counter() - t_tune
+    else:
+        # a fixed shape: the default one, with clusters of `cluster` CTAs for the largest graphs
+        k.set_option("batch_cluster", cluster)
+        tuning = {"fixed": True, "cluster": cluster}
     for _ in range(warmup):
         k.decompose_batched(gvd, off, adj, core, kmax)
     evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
@@ -782,7 +840,7 @@ def run_batched(args):
     torch.cuda.set_device(local)
     dev = torch.device("cuda", local)
     G_total = args.graphs or WORKLOADS["batched"]["G"]
-    r = batched_measure(local, args.steps, args.warmup, G_total, ws, rank)
+    r = batched_measure(local, args.steps, args.warmup, G_total, ws, rank, cluster=args.batch_cluster)
     ms = max_over_ranks(r["total_ms"], ws, dev) / args.steps
     e2e_best = max_over_ranks(min(r["e2e_ms"][1:]), ws, dev)
     if rank != 0:
@@ -1019,6 +1077,9 @@ def main():
                     help="single-graph workloads: warp-aggregated decrements (mode 2)")
     ap.add_argument("--sync-mode", type=int, default=0, choices=[0, 1, 2, 3],
                     help="single-graph schedule (0: the library's default)")
+    ap.add_argument("--batch-cluster", type=int, default=-1, choices=[-1, 0, 2, 4, 8],
+                    help="batched workloads: skip the autotuner and run the default shape with clusters of "
+                         "this many CTAs for the largest graphs (0: one CTA per graph)")
     ap.add_argument("--graphs", type=int, default=0,
                     help="batched workload: first G graphs of the distribution (default 4096; "
                          "smaller batches are for profiling)")
