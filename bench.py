@@ -919,12 +919,14 @@ SERIAL_NOTE = ("serial plain launches (kcore_decompose_host per request): each s
                "previous one finishes); arrivals are not replayed")
 
 
-def served_measure(local: int, R: int):
+def served_measure(local: int, R: int, batch_cluster: int = 0):
     """The served workload on one GPU: R requests (95% drawn from 256 graphs of
     the batch distribution, 5% from one R-MAT graph per scale 20..24) through a
     KCoreServer, all at once (saturation) and as Poisson arrivals at 0.5x and
     0.8x the saturation rate; then serial plain launches over the same
-    requests. Returns (runs, serial, h2d bytes, d2h bytes)."""
+    requests. batch_cluster: the server's clusters for the largest graphs of a
+    batched launch (0: its default; 1: one CTA per graph). Returns (runs,
+    serial, h2d bytes, d2h bytes)."""
     import torch
 
     import graphgen as gg
@@ -963,7 +965,7 @@ def served_measure(local: int, R: int):
         gaps = rng.exponential(1.0 / rate, R) if np.isfinite(rate) else np.zeros(R)
         arrive = np.cumsum(gaps)
         done_t = np.zeros(R)
-        with KCoreServer(local, pool_bytes=48 << 30) as srv:
+        with KCoreServer(local, pool_bytes=48 << 30, batch_cluster=batch_cluster) as srv:
             tick = {}
             nxt = 0
             t0 = time.perf_counter()
@@ -1029,7 +1031,9 @@ def run_served(args):
     ws, rank, local = dist_env()
     torch.cuda.set_device(local)
     R = WORKLOADS["served"]["requests"]
-    runs, serial, h2d, d2h = served_measure(local, R)
+    # --batch-cluster: 0 = one CTA per graph (the server's 1), C = clusters of C, unset = the server's default
+    cluster = 0 if args.batch_cluster < 0 else (1 if args.batch_cluster == 0 else args.batch_cluster)
+    runs, serial, h2d, d2h = served_measure(local, R, cluster)
     sat = runs[0]
     out = {
         "metric": METRIC, "value": sat["graphs_per_s"], "unit": "graphs/s", "n_gpus": 1,
@@ -1078,8 +1082,9 @@ def main():
     ap.add_argument("--sync-mode", type=int, default=0, choices=[0, 1, 2, 3],
                     help="single-graph schedule (0: the library's default)")
     ap.add_argument("--batch-cluster", type=int, default=-1, choices=[-1, 0, 2, 4, 8],
-                    help="batched workloads: skip the autotuner and run the default shape with clusters of "
-                         "this many CTAs for the largest graphs (0: one CTA per graph)")
+                    help="batched workload: skip the autotuner and run the default shape with clusters of "
+                         "this many CTAs for the largest graphs (0: one CTA per graph); served workload: the "
+                         "server's clusters for its batched launches (0: one CTA per graph)")
     ap.add_argument("--graphs", type=int, default=0,
                     help="batched workload: first G graphs of the distribution (default 4096; "
                          "smaller batches are for profiling)")

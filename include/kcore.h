@@ -391,7 +391,8 @@ kcore_status kcore_autotune(kcore_handle h, int64_t n, int64_t m, const int64_t*
  * coreness and the peel state kept resident while it is in flight) fits and a
  * slot is free. kcore_server_poll moves requests through copy-in, launch,
  * copy-out without blocking on the device: the small requests that became
- * ready together run as one batched launch (one CTA per graph) on one of
+ * ready together run as one batched launch (one CTA per graph, or a cluster
+ * of CTAs for each of its largest graphs, listed first) on one of
  * several streams, so requests admitted while others are on the GPU overlap
  * with them; large requests run the whole-GPU peel on their own stream.
  * One host thread drives a server (not thread-safe). */
@@ -403,6 +404,11 @@ typedef struct {
   int streams;            /* launch streams for batched launches (0: 4, at most 32) */
   int64_t large_vertices; /* requests with more vertices use the whole-GPU peel (0: 2^20) */
   int64_t large_arcs;     /* ... or more arcs (0: 2^25) */
+  int batch_cluster;      /* batched launches: the graphs with at least batch_big_arcs arcs are peeled
+                             by a thread-block cluster of this many CTAs (2, 4 or 8), the others by
+                             one CTA each; 1 = one CTA per graph; 0 = the default (4) */
+  int64_t batch_big_arcs; /* batched launches with clusters: the arcs from which a graph takes a
+                             cluster (0: the launch's arcs divided by its CTAs) */
 } kcore_server_config;
 
 /* cfg may be NULL (defaults). Errors: INVALID, OOM (pool or pinned buffers). */

@@ -158,7 +158,8 @@ SIGNATURES = {
 
 class ServerConfig(ctypes.Structure):
     _fields_ = [("pool_bytes", c_sz), ("max_requests", ctypes.c_int), ("streams", ctypes.c_int),
-                ("large_vertices", c_i64), ("large_arcs", c_i64)]
+                ("large_vertices", c_i64), ("large_arcs", c_i64), ("batch_cluster", ctypes.c_int),
+                ("batch_big_arcs", c_i64)]
 
 
 def _declare(L):

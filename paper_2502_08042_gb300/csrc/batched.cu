@@ -800,6 +800,47 @@ __global__ void __launch_bounds__(BLOCK, (BLOCK >= 1024 ? 1 : 2048 / BLOCK / 2))
   }
 }
 
+// The descriptor-driven peel with clusters of C CTAs for the graphs of at
+// least big_arcs arcs (the launch lists the slots largest first).
+template <int BLOCK, int C>
+__global__ void __cluster_dims__(C, 1, 1) __launch_bounds__(BLOCK, (BLOCK >= 1024 ? 1 : 2048 / BLOCK / 2))
+    desc_peel_cl(const GraphDesc* table, SlotList list, int* next, int smem_deg_max, int* status,
+                 long long big_arcs) {
+  extern __shared__ int sdeg[];
+  __shared__ BatchShared<BLOCK> sh;
+  __shared__ ClusterCtl ctl;
+  cg::cluster_group cl = cg::this_cluster();
+  ClusterCtl* lc = cl.map_shared_rank(&ctl, 0);
+  const bool lead = cl.block_rank() == 0;
+  bool together = true;
+  for (;;) {
+    int gi;
+    if (together) {
+      if (lead && threadIdx.x == 0) ctl.g = atomicAdd(next, 1);
+      cl.sync();
+      gi = lc->g;
+      cl.sync();  // every CTA has read the draw before the next one
+    } else {
+      if (threadIdx.x == 0) sh.g = atomicAdd(next, 1);
+      __syncthreads();
+      gi = sh.g;
+      __syncthreads();
+    }
+    if (gi >= list.count) break;
+    const GraphDesc gd = table[list.slot[gi]];
+    if (together && gd.n > 0 && gd.n < INT_MAX && gd.off[gd.n] - gd.off[0] >= big_arcs) {
+      ClusterPeel<BLOCK, C> cp(lc, sh, status);
+      cp.peel(gd);
+      continue;
+    }
+    if (together) {
+      together = false;  // the first CTA peels this graph, the others draw their own
+      if (!lead) continue;
+    }
+    peel_one_graph<BLOCK>(gd, smem_deg_max, status, sdeg, sh);
+  }
+}
+
 // Order of graphs: descending number of arcs (ties by index). One CTA sorts
 // keys (~arcs << 24 | g) bitonically in shared memory; batches larger than
 // kMaxSortGraphs keep their given order.
@@ -869,8 +910,26 @@ int occupancy_block(size_t smem) {
 }
 }  // namespace
 
+namespace {
+template <int C>
+cudaError_t desc_launch_cl(const GraphDesc* table, const SlotList& list, int* next, int smem_deg_max, int* status,
+                           int grid, size_t smem, long long big_arcs, cudaStream_t stream) {
+  cudaError_t e = cudaFuncSetAttribute(desc_peel_cl<1024, C>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       (int)smem);
+  if (e != cudaSuccess) return e;
+  grid = std::max(C, grid / C * C);
+  desc_peel_cl<1024, C><<<grid, 1024, smem, stream>>>(table, list, next, smem_deg_max, status, big_arcs);
+  return cudaGetLastError();
+}
+}  // namespace
+
 cudaError_t desc_launch(const GraphDesc* table, const SlotList& list, int* next, int smem_deg_max,
-                        int* status, int grid, size_t smem, cudaStream_t stream) {
+                        int* status, int grid, size_t smem, cudaStream_t stream, int cluster, long long big_arcs) {
+  switch (cluster) {
+    case 2: return desc_launch_cl<2>(table, list, next, smem_deg_max, status, grid, smem, big_arcs, stream);
+    case 4: return desc_launch_cl<4>(table, list, next, smem_deg_max, status, grid, smem, big_arcs, stream);
+    case 8: return desc_launch_cl<8>(table, list, next, smem_deg_max, status, grid, smem, big_arcs, stream);
+  }
   cudaError_t e = cudaFuncSetAttribute(desc_peel<1024>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                        (int)smem);
   if (e != cudaSuccess) return e;

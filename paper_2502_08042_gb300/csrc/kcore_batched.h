@@ -53,8 +53,11 @@ struct SlotList {
   int slot[kMaxSlotsPerLaunch];
 };
 
+// cluster 2, 4 or 8: clusters of that many CTAs for the listed graphs of at
+// least big_arcs arcs (list them largest first)
 cudaError_t desc_launch(const GraphDesc* table, const SlotList& list, int* next, int smem_deg_max,
-                        int* status, int grid, size_t smem, cudaStream_t stream);
+                        int* status, int grid, size_t smem, cudaStream_t stream, int cluster = 0,
+                        long long big_arcs = 0);
 size_t desc_static_smem();
 int batch_occupancy(int block, size_t smem);
 size_t batch_static_smem(int block);

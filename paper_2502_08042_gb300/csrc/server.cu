@@ -11,7 +11,8 @@
 //   copying  - its graph is being copied to the pool (copy stream)
 //   ready    - copies done; waiting for the next launch
 //   running  - small requests that became ready together run as one
-//              descriptor-driven batched peel (one CTA per graph) on one of
+//              descriptor-driven batched peel (one CTA per graph; a cluster of
+//              CTAs for each of the largest, which are listed first) on one of
 //              several launch streams, so a batch admitted while others are on
 //              the GPU overlaps with them; a large request (many vertices or
 //              arcs) runs the whole-GPU single-graph peel on its own stream
@@ -210,7 +211,20 @@ kcore_status kcore_server_create(kcore_server* out, int device, const kcore_serv
   c.streams = 4;
   c.large_vertices = (int64_t)1 << 20;
   c.large_arcs = (int64_t)1 << 25;
+  c.batch_cluster = 4;
+  c.batch_big_arcs = 0;
   if (cfg) {
+    if (cfg->batch_cluster != 0 && cfg->batch_cluster != 1 && cfg->batch_cluster != 2 &&
+        cfg->batch_cluster != 4 && cfg->batch_cluster != 8) {
+      delete s;
+      return KCORE_ERR_INVALID;
+    }
+    if (cfg->batch_cluster > 0) c.batch_cluster = cfg->batch_cluster;
+    if (cfg->batch_big_arcs < 0) {
+      delete s;
+      return KCORE_ERR_INVALID;
+    }
+    c.batch_big_arcs = cfg->batch_big_arcs;
     if (cfg->pool_bytes) c.pool_bytes = cfg->pool_bytes;
     if (cfg->max_requests > 0) c.max_requests = cfg->max_requests;
     if (cfg->streams > 0) c.streams = std::min(cfg->streams, 32);
@@ -365,8 +379,17 @@ kcore_status kcore_server_poll(kcore_server s, int64_t* tickets_out, int32_t* km
     b.d_status = ctr + 1;
     kc::SlotList list;
     list.count = cnt;
+    // largest first: with clusters the cluster-sized graphs lead the list
+    std::vector<std::pair<long long, int64_t>> by_arcs;
+    long long launch_arcs = 0;
     for (int i = 0; i < cnt; i++) {
-      Request& r = s->reqs[small_ready[first + i]];
+      const Request& r = s->reqs[small_ready[first + i]];
+      by_arcs.push_back({-(long long)r.m, small_ready[first + i]});
+      launch_arcs += (long long)r.m;
+    }
+    std::sort(by_arcs.begin(), by_arcs.end());
+    for (int i = 0; i < cnt; i++) {
+      Request& r = s->reqs[by_arcs[i].second];
       list.slot[i] = r.slot;
       r.state = RS_RUNNING;
       r.batch = s->next_batch;
@@ -374,11 +397,14 @@ kcore_status kcore_server_poll(kcore_server s, int64_t* tickets_out, int32_t* km
     }
     cudaStream_t st = s->launch[s->next_launch];
     s->next_launch = (s->next_launch + 1) % (int)s->launch.size();
-    int grid = std::min(cnt, s->desc_grid_cap);
+    const int cl = s->cfg.batch_cluster > 1 ? s->cfg.batch_cluster : 0;
+    int grid = std::min(cl ? cnt * cl : cnt, s->desc_grid_cap);
+    long long big = s->cfg.batch_big_arcs > 0 ? (long long)s->cfg.batch_big_arcs
+                                              : std::max<long long>(1, launch_arcs / std::max(grid, 1));
     e = cudaMemsetAsync(ctr, 0, 2 * sizeof(int), st);
     if (e == cudaSuccess)
       e = kc::desc_launch(s->d_table, list, ctr, (int)s->smem_vertices, b.d_status, grid,
-                          s->smem_vertices * 4, st);
+                          s->smem_vertices * 4, st, cl, big);
     if (e == cudaSuccess) e = cudaEventCreateWithFlags(&b.done, cudaEventDisableTiming);
     if (e == cudaSuccess) e = cudaEventRecord(b.done, st);
     if (e != cudaSuccess) {

@@ -327,9 +327,10 @@ class KCoreServer:
     to submit() must stay alive until their ticket comes back from poll()."""
 
     def __init__(self, device: int = 0, pool_bytes: int = 0, max_requests: int = 0, streams: int = 0,
-                 large_vertices: int = 0, large_arcs: int = 0):
+                 large_vertices: int = 0, large_arcs: int = 0, batch_cluster: int = 0, batch_big_arcs: int = 0):
         self._L = _native.lib()
-        cfg = _native.ServerConfig(pool_bytes, max_requests, streams, large_vertices, large_arcs)
+        cfg = _native.ServerConfig(pool_bytes, max_requests, streams, large_vertices, large_arcs, batch_cluster,
+                                   batch_big_arcs)
         h = ctypes.c_void_p()
         st = self._L.kcore_server_create(ctypes.byref(h), device, ctypes.byref(cfg))
         if st != 0:

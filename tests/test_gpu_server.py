@@ -87,3 +87,32 @@ def test_server_admission_defers_without_loss():
         assert srv.info()["in_flight"] == 0
     for i, w in enumerate(want):
         np.testing.assert_array_equal(res[i][0], w)
+
+
+@pytest.mark.parametrize("cluster", [1, 2, 8])
+def test_server_cluster_settings_match_oracle(cluster):
+    """Batched launches with one CTA per graph (1) or clusters of 2 or 8 CTAs
+    for their largest graphs (listed first): the same exact results, with the
+    R-MAT request kept on the batched path (large_vertices above it) and the
+    threshold forcing clusters onto every graph with arcs (big arcs 1)."""
+    reqs = make_requests()
+    want = [oracle.bz(len(o) - 1, o, a) for o, a in reqs]
+    for big in (0, 1):
+        with KCoreServer(0, pool_bytes=1 << 30, large_vertices=1 << 20, batch_cluster=cluster,
+                         batch_big_arcs=big) as srv:
+            rng = np.random.default_rng(cluster + big)
+            res = run_all(srv, reqs, list(rng.permutation(len(reqs))), 8)
+        for i, w in enumerate(want):
+            core, km, st = res[i]
+            assert st == 0
+            np.testing.assert_array_equal(core, w)
+            assert km == (int(w.max()) if len(w) else 0)
+
+
+def test_server_rejects_bad_cluster_settings():
+    from paper_2502_08042_gb300 import KCoreError
+    for bad in (3, 16, -2):
+        with pytest.raises(KCoreError):
+            KCoreServer(0, pool_bytes=1 << 26, batch_cluster=bad)
+    with pytest.raises(KCoreError):
+        KCoreServer(0, pool_bytes=1 << 26, batch_big_arcs=-1)
