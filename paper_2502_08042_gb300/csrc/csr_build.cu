@@ -63,19 +63,37 @@ struct EdgeList {
   int* status;
 };
 
-// the arcs of edge i = (a, b): keys 2i (a -> b) and 2i + 1 (b -> a)
+// a batch: the last graph g in [glo, ghi) with eoff[g] <= i
+__device__ __forceinline__ long long graph_of(const EdgeList& es, long long i, long long glo, long long ghi) {
+  long long lo = glo, hi = ghi;
+  while (hi - lo > 1) {
+    const long long mid = (lo + hi) >> 1;
+    if (es.eoff[mid] <= i) lo = mid;
+    else hi = mid;
+  }
+  return lo;
+}
+
+// a batch: the graphs [*glo, *ghi) that hold edges [e0, e1) (a CTA's chunk;
+// one binary search each for its first and last edge, by thread 0, shared
+// through *glo / *ghi in shared memory; the caller synchronises)
+__device__ __forceinline__ void chunk_graphs(const EdgeList& es, long long e0, long long e1, long long* glo,
+                                             long long* ghi) {
+  if (threadIdx.x == 0) {
+    *glo = es.gv && e0 < e1 ? graph_of(es, e0, 0, es.G) : 0;
+    *ghi = es.gv && e0 < e1 ? graph_of(es, e1 - 1, *glo, es.G) + 1 : es.G;
+  }
+}
+
+// the arcs of edge i = (a, b): keys 2i (a -> b) and 2i + 1 (b -> a); a batch's
+// edge i lies in one of the graphs [glo, ghi)
 __device__ __forceinline__ void edge_keys(const EdgeList& es, long long i, int a, int b, unsigned long long& k0,
-                                          unsigned long long& k1) {
+                                          unsigned long long& k1, long long glo = 0, long long ghi = 0) {
   long long base = 0, lim = es.n;
   if (es.gv) {
-    long long lo = 0, hi = es.G;  // last g with eoff[g] <= i
-    while (hi - lo > 1) {
-      long long mid = (lo + hi) >> 1;
-      if (es.eoff[mid] <= i) lo = mid;
-      else hi = mid;
-    }
-    base = es.gv[lo];
-    lim = es.gv[lo + 1] - base;
+    const long long g = ghi - glo == 1 ? glo : graph_of(es, i, glo, ghi > glo ? ghi : es.G);
+    base = es.gv[g];
+    lim = es.gv[g + 1] - base;
   }
   k0 = k1 = kSentinel;
   if ((unsigned long long)(unsigned)a >= (unsigned long long)lim ||
@@ -139,6 +157,10 @@ __global__ void __launch_bounds__(kCsrBlock) rs_upsweep(const unsigned long long
         if (e0 + u * kCsrBlock < hi) atomicAdd(&cnt[warp][digit_of(edge_canon(es, a[u], b[u]), shift, dmask)], 1u);
     }
   } else if constexpr (kSrc == kArcs) {
+    __shared__ long long cg_lo, cg_hi;
+    chunk_graphs(es, lo / 2, hi > lo ? hi / 2 : lo / 2, &cg_lo, &cg_hi);
+    __syncthreads();
+    const long long glo = cg_lo, ghi = cg_hi;
     constexpr int kU = 4;  // edges per thread per step, loaded before any count
     for (long long e0 = lo / 2 + tid; e0 < hi / 2; e0 += kU * kCsrBlock) {
       int a[kU], b[kU];
@@ -153,7 +175,7 @@ __global__ void __launch_bounds__(kCsrBlock) rs_upsweep(const unsigned long long
         const long long e = e0 + u * kCsrBlock;
         if (e < hi / 2) {
           unsigned long long k0, k1;
-          edge_keys(es, e, a[u], b[u], k0, k1);
+          edge_keys(es, e, a[u], b[u], k0, k1, glo, ghi);
           atomicAdd(&cnt[warp][digit_of(k0, shift, dmask)], 1u);
           atomicAdd(&cnt[warp][digit_of(k1, shift, dmask)], 1u);
         }
@@ -245,6 +267,11 @@ __global__ void __launch_bounds__(kCsrBlock, 5) rs_downsweep(const unsigned long
     run = before + incl - rt + offs[(long long)tid * G + blockIdx.x];
   }
   long long lo = (long long)blockIdx.x * chunk, hi = min(N, lo + chunk);
+  __shared__ long long cg_lo, cg_hi;  // kArcs, a batch: the graphs of this chunk's edges
+  if constexpr (kSrc == kArcs) {
+    chunk_graphs(es, lo / 2, hi > lo ? hi / 2 : lo / 2, &cg_lo, &cg_hi);
+    __syncthreads();
+  }
   // 16-byte asynchronous copies of a tile's keys into `stage` (pairs of keys;
   // a last odd key is copied with its neighbour, which lies inside the
   // key buffer and is not used). kArcs / kCanon: the tile's sources and
@@ -310,7 +337,8 @@ __global__ void __launch_bounds__(kCsrBlock, 5) rs_downsweep(const unsigned long
 #pragma unroll
       for (int it = 0; it < kKeysPerThread; it += 2) {
         k[it] = k[it + 1] = 0;
-        if (valid(it)) edge_keys(es, ts / 2 + el_of(it), sa[el_of(it)], sa[1024 + el_of(it)], k[it], k[it + 1]);
+        if (valid(it))
+          edge_keys(es, ts / 2 + el_of(it), sa[el_of(it)], sa[1024 + el_of(it)], k[it], k[it + 1], cg_lo, cg_hi);
       }
     } else {
 #pragma unroll
