@@ -63,7 +63,14 @@ typedef enum {
                                   3 the offline peel of Algorithm 2 on the same kernel: each subround
                                   counts the frontier's decrements per neighbour (histogram), then
                                   applies them in one step per vertex, so every crossing is decided
-                                  by one owner; no local queues (its subrounds are Algorithm 1's) */
+                                  by one owner; no local queues (its subrounds are Algorithm 1's);
+                                  4 the whole graph on one CTA of 1024 threads (CTA barriers only,
+                                  induced degrees in shared memory when they fit), or on one
+                                  thread-block cluster of KCORE_OPT_BATCH_CLUSTER CTAs (the
+                                  hardware cluster barrier): the batched peel's kernel on a batch
+                                  of one, for small deep graphs whose many phases cost more in
+                                  grid barriers than one SM's work; not for the k'-core query,
+                                  which runs mode 2; trace and sampling options do not apply */
   KCORE_OPT_CTAS_PER_SM = 1,   /* CTAs per SM of the persistent kernel (0 = occupancy maximum) */
   KCORE_OPT_SLICE_ARCS = 2,    /* arcs per work item (16 .. 2^20; 0 = auto: 32 in modes 2 and 3,
                                   512 in mode 1): longer lists are split in slices */
@@ -148,7 +155,8 @@ typedef enum {
                                          graph with at least KCORE_OPT_BATCH_BIG_ARCS arcs is peeled
                                          by a thread-block cluster of that many CTAs (512 or 1024
                                          threads per CTA), so a batch's largest graphs no longer
-                                         hold it up; smaller graphs still take one CTA each */
+                                         hold it up; smaller graphs still take one CTA each. Sync
+                                         mode 4 of a single graph: the cluster size (0 = one CTA) */
   KCORE_OPT_BATCH_BIG_ARCS = 29       /* batched peel with clusters: the arcs from which a graph takes a
                                          cluster (0 = the batch's arcs divided by its CTAs, default;
                                          else 1 .. 2^40) */
@@ -364,6 +372,7 @@ typedef struct {
   int64_t local_batches;  /* KCORE_OPT_LOCAL_BATCHES */
   int32_t candidates;     /* schedules timed */
   double ms;              /* best time of one decomposition with the chosen schedule */
+  int32_t cluster;        /* KCORE_OPT_BATCH_CLUSTER (used by sync mode 4) */
 } kcore_tuning;
 
 /* Autotuner of the single-graph peel's schedule (Algorithm 1's subround and
@@ -371,8 +380,8 @@ typedef struct {
  * are paid). Times each candidate schedule -- the bulk-synchronous default;
  * tail mode at a few thresholds, including the whole peel on one CTA; no
  * batch update; d~ read first in shorter subrounds; shorter local chains;
- * warp aggregation; one CTA per SM; the asynchronous schedule -- on the
- * caller's own graph (the arguments of kcore_decompose), best of `repeats`
+ * warp aggregation; one CTA per SM; the asynchronous schedule; mode 4 on one
+ * CTA and on a cluster of 8 -- on the caller's own graph (the arguments of kcore_decompose), best of `repeats`
  * (1..100) calls after one warm-up each, with CUDA events on `stream`. It then
  * sets the handle's options to the fastest schedule, decomposes once more
  * with it and fills *best_out. Tracing is off while it times. Synchronous; the

@@ -109,7 +109,8 @@ class Tuning(ctypes.Structure):
     _fields_ = [("sync_mode", ctypes.c_int32), ("batch_update", ctypes.c_int32),
                 ("warp_combine", ctypes.c_int32), ("ctas_per_sm", ctypes.c_int32),
                 ("tail_items", c_i64), ("tail_entries", c_i64), ("precheck_items", c_i64),
-                ("local_batches", c_i64), ("candidates", ctypes.c_int32), ("ms", ctypes.c_double)]
+                ("local_batches", c_i64), ("candidates", ctypes.c_int32), ("ms", ctypes.c_double),
+                ("cluster", ctypes.c_int32)]
 
 
 class BatchTuning(ctypes.Structure):

@@ -35,6 +35,7 @@ struct kcore_ctx {
   int* last_batch_status = nullptr;  // device status word of the last batched call
   int* last_validate_status = nullptr;  // device status words of the last CSR check
   int last_batch_block = 0, last_batch_grid = 0, last_batch_smem_vertices = 0, last_batch_cluster = 0;
+  bool last_batch_single = false;  // the batched kernel ran one graph of a single-graph call (mode 4)
   unsigned long long* last_trace = nullptr;
   bool last_trace_phases = false;  // the trace holds one record per phase
   int last_max_rounds = 0;
@@ -153,8 +154,12 @@ PeelLayout peel_layout(long long n, long long m, int slice, bool offline = false
 // Schedule and slice length a call on this handle uses (option value 0 = auto).
 int effective_mode(const kcore_ctx* h) {
   const int64_t m = h->opt[KCORE_OPT_SYNC_MODE];
-  return m == 1 ? 1 : (m == 3 ? 3 : 2);
+  return m == 1 ? 1 : (m == 3 ? 3 : (m == 4 ? 4 : 2));
 }
+// mode 4: the batched peel's kernel on a batch of one graph (defined with the batched entry points)
+size_t single_batched_bytes(int64_t n);
+kcore_status single_batched_call(kcore_ctx* h, int64_t n, int64_t m, const int64_t* offsets, const int32_t* adj,
+                                 int32_t* out, int32_t* kmax_out, cudaStream_t stream);
 // Sampling runs in the bulk-synchronous mode, without the level window and
 // not for the k'-core query.
 bool sampling_on(const kcore_ctx* h, bool threshold) {
@@ -307,7 +312,7 @@ kcore_status kcore_set_option(kcore_handle h, kcore_option opt, int64_t value) {
       if (value < 0 || value > 1) return fail(h, KCORE_ERR_INVALID, "test stall must be 0 or 1");
       break;
     case KCORE_OPT_SYNC_MODE:
-      if (value < 0 || value > 3) return fail(h, KCORE_ERR_INVALID, "sync mode must be 0, 1, 2 or 3");
+      if (value < 0 || value > 4) return fail(h, KCORE_ERR_INVALID, "sync mode must be 0, 1, 2, 3 or 4");
       break;
     case KCORE_OPT_CTAS_PER_SM:
       if (value < 0 || value > h->max_ctas_per_sm)
@@ -343,6 +348,10 @@ kcore_status kcore_get_option(kcore_handle h, kcore_option opt, int64_t* value) 
 
 kcore_status kcore_workspace_size(kcore_handle h, int64_t n, int64_t m, size_t* bytes) {
   if (!h || !bytes || n < 0 || m < 0 || n > INT32_MAX - 1) return KCORE_ERR_INVALID;
+  if (effective_mode(h) == 4) {
+    *bytes = single_batched_bytes(n);
+    return KCORE_OK;
+  }
   *bytes = peel_layout(n, m, effective_slice(h),
                        effective_mode(h) == 3 || (effective_mode(h) == 2 && h->opt[KCORE_OPT_BATCH_UPDATE]),
                        sampling_on(h, false))
@@ -390,6 +399,7 @@ kcore_status peel_call(kcore_ctx* h, int64_t n, int64_t m, const int64_t* offset
     if (e != cudaSuccess) return cuda_fail(h, e, "cudaMemsetAsync");
     return KCORE_OK;
   }
+  if (!threshold && effective_mode(h) == 4) return single_batched_call(h, n, m, offsets, adj, out, kmax_out, stream);
   const int mode = threshold ? 2 : effective_mode(h);
   const int slice =
       h->opt[KCORE_OPT_SLICE_ARCS] > 0 ? (int)h->opt[KCORE_OPT_SLICE_ARCS] : (mode == 1 ? 512 : kc::kSliceDefault);
@@ -656,7 +666,67 @@ void batch_shape(kcore_ctx* h, int* block, int* smem_vertices, int* grid, size_t
   *grid = h->sms * occ;
   *smem = sm;
 }
+
 }  // namespace
+extern "C++" {
+namespace {
+size_t single_batched_bytes(int64_t n) { return batch_layout(1, n).total + 256; }
+
+// Mode 4: the whole graph on one CTA of 1,024 threads (induced degrees in
+// shared memory when they fit in one SM's), or on one thread-block cluster of
+// KCORE_OPT_BATCH_CLUSTER CTAs: the batched peel's kernel on a batch of one.
+kcore_status single_batched_call(kcore_ctx* h, int64_t n, int64_t m, const int64_t* offsets, const int32_t* adj,
+                                 int32_t* out, int32_t* kmax_out, cudaStream_t stream) {
+  const BatchLayout L = batch_layout(1, n);
+  kcore_status st = ensure_ws(h, L.total + 256);
+  if (st != KCORE_OK) return st;
+  char* ws = (char*)h->ws;
+  int dev_smem = 0, sm_total = 0;
+  cudaDeviceGetAttribute(&dev_smem, cudaDevAttrMaxSharedMemoryPerBlockOptin, h->device);
+  cudaDeviceGetAttribute(&sm_total, cudaDevAttrMaxSharedMemoryPerMultiprocessor, h->device);
+  const long long stat = (long long)kc::batch_static_smem(1024) + 256;  // + the cluster counters
+  const long long per = std::min<long long>((long long)sm_total - stat - 2048, (long long)dev_smem - stat - 1024);
+  // shared memory only as large as the graph's induced degrees (32 bits, or 16
+  // when every degree is below 2^16, which the kernel finds out); none when
+  // even 16 bits do not fit, so the SM keeps its L1 for the global accesses
+  const long long cap = std::max<long long>(0, per / 4);
+  const int sv = (int)(n <= cap ? n : ((n + 1) / 2 <= cap ? (n + 1) / 2 : 0));
+  const int cluster = h->opt[KCORE_OPT_BATCH_CLUSTER] > 1 ? (int)h->opt[KCORE_OPT_BATCH_CLUSTER] : 0;
+  kc::BatchArgs a{};
+  a.G = 1;
+  a.N = n;
+  a.m = m;
+  a.gv = (const long long*)(ws + L.total);
+  a.off = (const long long*)offsets;
+  a.adj = adj;
+  a.core = out;
+  a.kmax = kmax_out;
+  a.deg = (int*)(ws + L.deg);
+  a.A0 = (int*)(ws + L.a0);
+  a.A1 = (int*)(ws + L.a1);
+  a.F0 = (int*)(ws + L.f0);
+  a.F1 = (int*)(ws + L.f1);
+  a.order = nullptr;
+  a.next_graph = (int*)(ws + L.ctl);
+  a.status = (int*)(ws + L.ctl) + 32;
+  a.smem_deg_max = sv;
+  cudaError_t e;
+  if ((e = cudaMemsetAsync(ws + L.ctl, 0, 256, stream)) != cudaSuccess) return cuda_fail(h, e, "memset");
+  if ((e = kc::batch_single_gv((long long*)(ws + L.total), n, stream)) != cudaSuccess)
+    return cuda_fail(h, e, "graph offsets");
+  if ((e = kc::batch_launch(a, 1024, cluster ? cluster : 1, (size_t)sv * 4, false, stream, cluster, 1)) !=
+      cudaSuccess)
+    return cuda_fail(h, e, "single-graph launch on the batched kernel");
+  h->last_batch_status = a.status;
+  h->last_batch_block = 1024;
+  h->last_batch_grid = cluster ? cluster : 1;
+  h->last_batch_smem_vertices = sv;
+  h->last_batch_cluster = cluster;
+  h->last_batch_single = true;
+  return KCORE_OK;
+}
+}  // namespace
+}  // extern "C++"
 
 kcore_status kcore_batched_workspace_size(kcore_handle h, int64_t num_graphs, int64_t total_vertices,
                                           size_t* bytes) {
@@ -725,6 +795,7 @@ kcore_status kcore_decompose_batched(kcore_handle h, int64_t num_graphs, int64_t
   if ((e = kc::batch_launch(a, block, grid, smem, sort_graphs, stream, cluster, big_arcs)) != cudaSuccess)
     return cuda_fail(h, e, "batched launch");
   h->last_batch_cluster = cluster > 1 ? cluster : 0;
+  h->last_batch_single = false;
   h->last_batch_status = a.status;
   h->last_batch_block = block;
   h->last_batch_grid = grid;
@@ -782,8 +853,13 @@ kcore_status kcore_sync_status(kcore_handle h) {
     h->stats.batch_block = h->last_batch_block;
     h->stats.batch_smem_vertices = h->last_batch_smem_vertices;
     h->stats.batch_cluster = h->last_batch_cluster;
+    if (h->last_batch_single) h->stats.sync_mode = 4;
     if (bs[0] == kc::ST_NOT_SIMPLE) {
       long long val = (long long)(unsigned)bs[2] | ((long long)bs[3] << 32);
+      if (h->last_batch_single)
+        return fail(h, KCORE_ERR_NOT_SIMPLE,
+                    "malformed CSR detected on the device (check " + std::to_string(bs[1]) + ", value " +
+                        std::to_string(val) + "); k_max is -1");
       return fail(h, KCORE_ERR_NOT_SIMPLE,
                   "malformed segmented CSR detected on the device (check " + std::to_string(bs[1]) +
                       ", value " + std::to_string(val) + "); the graphs concerned report k_max -1");

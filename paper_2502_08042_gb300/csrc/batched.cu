@@ -939,6 +939,16 @@ cudaError_t desc_launch(const GraphDesc* table, const SlotList& list, int* next,
 
 size_t desc_static_smem() { return sizeof(BatchShared<1024>); }
 
+__global__ void batch_single_gv_kernel(long long* gv, long long n) {
+  gv[0] = 0;
+  gv[1] = n;
+}
+
+cudaError_t batch_single_gv(long long* gv, long long n, cudaStream_t stream) {
+  batch_single_gv_kernel<<<1, 1, 0, stream>>>(gv, n);
+  return cudaGetLastError();
+}
+
 int batch_occupancy(int block, size_t smem) {
   switch (block) {
     case 256: return occupancy_block<256>(smem);

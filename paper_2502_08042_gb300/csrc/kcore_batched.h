@@ -59,6 +59,8 @@ cudaError_t desc_launch(const GraphDesc* table, const SlotList& list, int* next,
                         int* status, int grid, size_t smem, cudaStream_t stream, int cluster = 0,
                         long long big_arcs = 0);
 size_t desc_static_smem();
+// gv = {0, n} on `stream`: the vertex offsets of a batch of one graph
+cudaError_t batch_single_gv(long long* gv, long long n, cudaStream_t stream);
 int batch_occupancy(int block, size_t smem);
 size_t batch_static_smem(int block);
 // cluster > 1 (512 or 1024 threads, 2, 4 or 8 CTAs): the clustered form, for

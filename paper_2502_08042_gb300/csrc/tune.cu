@@ -141,48 +141,53 @@ constexpr int64_t kHuge = (int64_t)1 << 30;
 // One candidate schedule: every option the single-graph tuner sets.
 struct Schedule {
   int64_t sync_mode, batch_update, warp_combine, ctas_per_sm, tail_items, tail_entries, precheck_items,
-      local_batches;
+      local_batches, cluster;
 };
 
 // Candidates: the default bulk-synchronous schedule; tail mode at small,
 // medium and unbounded thresholds (the last runs the whole peel on one CTA,
 // which suits small graphs); without batch update; reading d~ first in
 // shorter subrounds; shorter local chains; warp aggregation; one CTA per SM;
-// and the asynchronous schedule.
+// the asynchronous schedule; and the whole graph on one CTA or on one cluster
+// of 8 CTAs (mode 4).
 std::vector<Schedule> schedule_candidates() {
   return {
-      {2, 1, 0, 0, 0, 0, 64, 32},
-      {2, 1, 0, 0, 8, 0, 64, 32},
-      {2, 1, 0, 0, 64, 4096, 64, 32},
-      {2, 1, 0, 0, kHuge, kHuge, 64, 32},
-      {2, 0, 0, 0, 0, 0, 64, 32},
-      {2, 1, 0, 0, 0, 0, 16, 32},
-      {2, 1, 0, 0, 0, 0, 64, 8},
-      {2, 1, 1, 0, 0, 0, 64, 32},
-      {2, 1, 0, 1, 0, 0, 64, 32},
-      {1, 1, 0, 0, 0, 0, 64, 32},
+      {2, 1, 0, 0, 0, 0, 64, 32, 0},
+      {2, 1, 0, 0, 8, 0, 64, 32, 0},
+      {2, 1, 0, 0, 64, 4096, 64, 32, 0},
+      {2, 1, 0, 0, kHuge, kHuge, 64, 32, 0},
+      {2, 0, 0, 0, 0, 0, 64, 32, 0},
+      {2, 1, 0, 0, 0, 0, 16, 32, 0},
+      {2, 1, 0, 0, 0, 0, 64, 8, 0},
+      {2, 1, 1, 0, 0, 0, 64, 32, 0},
+      {2, 1, 0, 1, 0, 0, 64, 32, 0},
+      {1, 1, 0, 0, 0, 0, 64, 32, 0},
+      {4, 1, 0, 0, 0, 0, 64, 32, 0},
+      {4, 1, 0, 0, 0, 0, 64, 32, 8},
   };
 }
 
 constexpr kcore_option kScheduleOptions[] = {KCORE_OPT_SYNC_MODE,      KCORE_OPT_BATCH_UPDATE,
                                              KCORE_OPT_WARP_COMBINE,   KCORE_OPT_CTAS_PER_SM,
                                              KCORE_OPT_TAIL_ITEMS,     KCORE_OPT_TAIL_ENTRIES,
-                                             KCORE_OPT_PRECHECK_ITEMS, KCORE_OPT_LOCAL_BATCHES};
+                                             KCORE_OPT_PRECHECK_ITEMS, KCORE_OPT_LOCAL_BATCHES,
+                                             KCORE_OPT_BATCH_CLUSTER};
+constexpr int kScheduleFields = 9;
 
 int64_t* field(Schedule& s, int i) {
-  int64_t* f[] = {&s.sync_mode,    &s.batch_update, &s.warp_combine,   &s.ctas_per_sm,
-                  &s.tail_items,   &s.tail_entries, &s.precheck_items, &s.local_batches};
+  int64_t* f[] = {&s.sync_mode,    &s.batch_update, &s.warp_combine,   &s.ctas_per_sm,  &s.tail_items,
+                  &s.tail_entries, &s.precheck_items, &s.local_batches, &s.cluster};
   return f[i];
 }
 
 Schedule read_schedule(kcore_handle h) {
   Schedule s{};
-  for (int i = 0; i < 8; i++) kcore_get_option(h, kScheduleOptions[i], field(s, i));
+  for (int i = 0; i < kScheduleFields; i++) kcore_get_option(h, kScheduleOptions[i], field(s, i));
   return s;
 }
 
 kcore_status apply_schedule(kcore_handle h, Schedule s) {
-  for (int i = 0; i < 8; i++) {
+  for (int i = 0; i < kScheduleFields; i++) {
     const kcore_status st = kcore_set_option(h, kScheduleOptions[i], *field(s, i));
     if (st != KCORE_OK) return st;
   }
@@ -258,6 +263,7 @@ extern "C" kcore_status kcore_autotune(kcore_handle h, int64_t n, int64_t m, con
   best_out->ctas_per_sm = (int32_t)best.ctas_per_sm;
   best_out->tail_items = best.tail_items;
   best_out->tail_entries = best.tail_entries;
+  best_out->cluster = (int32_t)best.cluster;
   best_out->precheck_items = best.precheck_items;
   best_out->local_batches = best.local_batches;
   best_out->candidates = timed;
