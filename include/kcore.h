@@ -297,7 +297,9 @@ kcore_status kcore_build_csr_workspace_size(kcore_handle h, int64_t n, int64_t n
  *   coreness_out          device int32[N]: coreness of every vertex in its graph
  *   kmax_out              device int32[G]: largest coreness of each graph (0 if empty)
  * Asynchronous; one persistent kernel (each graph peeled by one CTA, induced
- * degrees in shared memory when the graph fits, largest graphs first). Uses
+ * degrees in shared memory when the graph fits, largest graphs first; with
+ * KCORE_OPT_BATCH_CLUSTER, the graphs above KCORE_OPT_BATCH_BIG_ARCS arcs by a
+ * thread-block cluster each, induced degrees in L2). Uses
  * kcore_batched_workspace_size bytes of workspace (20 bytes per vertex).
  * Malformed offsets or ids are reported as KCORE_ERR_NOT_SIMPLE by
  * kcore_sync_status. */
