@@ -347,7 +347,8 @@ typedef struct {
 /* Autotuner of the batched peel (not in the paper: the launch shape of the
  * batched form). Times each candidate launch shape -- 1024, 512 or 256
  * threads per CTA with 1..8 resident CTAs per SM, the shared-memory threshold
- * following the shape, and the clustered form with clusters of 2, 4 or 8 CTAs
+ * following the shape, 512 threads x 3 CTAs with thresholds of 8,000 and
+ * 2,000 vertices, and the clustered form with clusters of 2, 4 or 8 CTAs
  * of 1024 threads or 4 of 512 -- on the caller's own batch (the arguments of
  * kcore_decompose_batched), best of `repeats` (1..100) calls after one
  * warm-up each, with CUDA events on `stream`. It then sets the handle's batch

@@ -678,7 +678,7 @@ struct ClusterPeel {
 };
 
 template <int BLOCK>
-__global__ void __launch_bounds__(BLOCK, (BLOCK >= 1024 ? 1 : 2048 / BLOCK / 2)) batch_peel(BatchArgs a) {
+__global__ void __launch_bounds__(BLOCK, (BLOCK >= 1024 ? 1 : 2048 / BLOCK * 3 / 4)) batch_peel(BatchArgs a) {
   extern __shared__ int sdeg[];
   __shared__ BatchShared<BLOCK> sh;
   for (;;) {

@@ -13,7 +13,7 @@
 namespace {
 
 struct Shape {
-  int block, ctas_per_sm, cluster;
+  int block, ctas_per_sm, cluster, smem_vertices;  // smem_vertices -1: as many as fit
 };
 
 // Candidate shapes: threads per CTA x resident CTAs per SM, within one SM's
@@ -21,12 +21,15 @@ struct Shape {
 // vertices as fit with that many CTAs per SM).
 std::vector<Shape> candidates() {
   std::vector<Shape> c;
-  for (int cps : {1, 2}) c.push_back({1024, cps, 0});
-  for (int cps : {1, 2, 3, 4}) c.push_back({512, cps, 0});
-  for (int cps : {2, 4, 6, 8}) c.push_back({256, cps, 0});
+  for (int cps : {1, 2}) c.push_back({1024, cps, 0, -1});
+  for (int cps : {1, 2, 3, 4}) c.push_back({512, cps, 0, -1});
+  for (int cps : {2, 4, 6, 8}) c.push_back({256, cps, 0, -1});
+  // more resident CTAs with less shared memory each: the SM keeps more L1 for
+  // the global accesses of the graphs that do not fit
+  for (int sv : {8000, 2000}) c.push_back({512, 3, 0, sv});
   // the clustered form for the batch's largest graphs
-  for (int cl : {2, 4, 8}) c.push_back({1024, 2, cl});
-  c.push_back({512, 2, 4});
+  for (int cl : {2, 4, 8}) c.push_back({1024, 2, cl, -1});
+  c.push_back({512, 2, 4, -1});
   return c;
 }
 
@@ -51,7 +54,7 @@ struct OptionSnapshot {
 
 kcore_status apply(kcore_handle h, const Shape& s) {
   kcore_status st = kcore_set_option(h, KCORE_OPT_BATCH_BLOCK, s.block);
-  if (st == KCORE_OK) st = kcore_set_option(h, KCORE_OPT_BATCH_SMEM_VERTICES, -1);
+  if (st == KCORE_OK) st = kcore_set_option(h, KCORE_OPT_BATCH_SMEM_VERTICES, s.smem_vertices);
   if (st == KCORE_OK) st = kcore_set_option(h, KCORE_OPT_BATCH_CTAS_PER_SM, s.ctas_per_sm);
   if (st == KCORE_OK) st = kcore_set_option(h, KCORE_OPT_BATCH_CLUSTER, s.cluster);
   if (st == KCORE_OK) st = kcore_set_option(h, KCORE_OPT_BATCH_BIG_ARCS, 0);
@@ -75,7 +78,7 @@ extern "C" kcore_status kcore_autotune_batched(kcore_handle h, int64_t num_graph
     cudaGetLastError();
     return KCORE_ERR_CUDA;
   }
-  Shape best{0, 0, 0};
+  Shape best{0, 0, 0, -1};
   double best_ms = 0;
   int timed = 0;
   kcore_status result = KCORE_OK;
