@@ -420,6 +420,7 @@ struct ClusterPeel {
   // then the cluster barrier (release / acquire: the phase's stores, global
   // and distributed shared, are seen by every CTA after it)
   __device__ void next_phase() {
+    __syncthreads();  // every thread's flag_bad of this phase is seen by thread 0
     if (threadIdx.x == 0 && sh.bad) atomicOr(&lc->bad, 1);
     cl.sync();
     ph++;
