@@ -324,7 +324,11 @@ class KCore:
 
 class KCoreServer:
     """Request loop with continuous batching (kcore_server_*). Host arrays given
-    to submit() must stay alive until their ticket comes back from poll()."""
+    to submit() must stay alive until their ticket comes back from poll().
+    The arguments mirror kcore_server_config (0 = its default): batch_cluster
+    is the cluster size for the largest graphs of a batched launch (2, 4 or 8;
+    1 = one CTA per graph; default 4), batch_big_arcs the arcs from which a
+    graph takes a cluster (default: the launch's arcs per CTA)."""
 
     def __init__(self, device: int = 0, pool_bytes: int = 0, max_requests: int = 0, streams: int = 0,
                  large_vertices: int = 0, large_arcs: int = 0, batch_cluster: int = 0, batch_big_arcs: int = 0):
